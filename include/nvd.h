@@ -1,0 +1,238 @@
+/*
+ * nvd.h -- C ABI of the GB300 Generalized-Euclidean node-vector distance library.
+ *
+ * The library computes, for node vectors x and y on a weighted undirected graph,
+ *
+ *     d(x, y)^2 = (x - y)^T L^+ (x - y)                 (Section 3.1, GE equation)
+ *
+ * where L = D - W is the graph Laplacian and L^+ its Moore-Penrose pseudoinverse,
+ * without ever forming L^+: it solves L z = x - y with a Laplacian solver
+ * (Section 3.2) -- here a Jacobi-preconditioned conjugate gradient (the "CG"
+ * solver of Table 1) built from hand-written sm_103a kernels -- and returns
+ * (x - y)^T z.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an nvd_status (0 = NVD_OK) and never throws or aborts.
+ *    nvd_last_error() gives a one-line description of the most recent failure on
+ *    the calling thread.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work is ordered on that stream.  Unless a flag below
+ *    says otherwise, a call returns after its results are available to the
+ *    caller (it synchronises the stream once at the end).
+ *  - Node vectors use the layout [k][n]: k pairs, one contiguous row of n values
+ *    per pair, node order of the CSR given to nvd_graph_create.
+ *  - One handle may be used by one thread at a time; distinct handles are
+ *    independent.  A handle lives on the CUDA device that was current when it
+ *    was created; calls on it make that device current for their duration.
+ *  - Sizes: n < 2^31 nodes, nnz < 2^62 stored entries, k < 2^31 pairs.
+ */
+#ifndef NVD_H_
+#define NVD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nvd_graph_s *nvd_graph_t; /* opaque graph handle */
+typedef void *nvd_stream_t;              /* cudaStream_t */
+
+typedef enum { NVD_F32 = 0, NVD_F64 = 1 } nvd_dtype;
+
+typedef enum {
+    NVD_OK = 0,
+    NVD_ERR_INVALID_ARG = 1,   /* bad pointer, size, dtype, flag or CSR layout */
+    NVD_ERR_NOT_SYMMETRIC = 2, /* CSR is not a symmetric matrix (structure or values) */
+    NVD_ERR_BAD_WEIGHT = 3,    /* a weight is <= 0, NaN or infinite (Section 3.1 needs w > 0) */
+    NVD_ERR_OOM = 4,           /* device or host allocation failed */
+    NVD_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    NVD_ERR_NOT_CONVERGED = 6, /* some pair did not reach the tolerance (results still written) */
+    NVD_ERR_NUMERIC = 7,       /* NaN/Inf or loss of positivity inside the solver */
+    NVD_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up (grid barrier) */
+    NVD_ERR_UNSUPPORTED = 9    /* valid request the build does not handle */
+} nvd_status;
+
+/* ------------------------------------------------------------------ graphs */
+
+#define NVD_GRAPH_DEVICE_PTRS 1u    /* rowptr/colidx/w are device pointers (else host) */
+#define NVD_GRAPH_SKIP_SYM_CHECK 2u /* trust the caller: skip the symmetry check */
+
+/*
+ * nvd_graph_create -- build a graph handle from a CSR adjacency (Section 3.1:
+ * undirected graph, positive weights; L = D - W).
+ *
+ *   n        number of nodes (>= 1).
+ *   nnz      number of stored entries (>= 0); rowptr[n] must equal nnz.
+ *   rowptr   int64 [n+1], non-decreasing, rowptr[0] = 0.
+ *   colidx   int32 [nnz], column of each entry, 0 <= colidx < n.
+ *   w        [nnz] weights, float (NVD_F32) or double (NVD_F64) per wdtype;
+ *            NULL means every weight is 1.
+ *   flags    NVD_GRAPH_* bits.  Without NVD_GRAPH_DEVICE_PTRS the three arrays
+ *            are host memory.
+ *
+ * The matrix must be symmetric (entry (u,v,w) present iff (v,u,w) is); both
+ * directions of every edge are stored.  Self-loops are dropped (they do not
+ * change L); repeated (u,v) entries are summed (parallel conductances); columns
+ * need not be sorted.  The library copies everything it needs: the caller may
+ * free its arrays when the call returns.  Connected components are found here;
+ * the solver works on each component separately (L^+ annihilates constants on
+ * every component, so delta is projected mean-zero per component).
+ *
+ * Errors: NVD_ERR_INVALID_ARG (n < 1, nnz < 0, NULL pointers, rowptr not
+ * monotone or not ending at nnz, column out of range), NVD_ERR_NOT_SYMMETRIC,
+ * NVD_ERR_BAD_WEIGHT, NVD_ERR_OOM, NVD_ERR_CUDA.  On failure *out is NULL.
+ */
+int nvd_graph_create(nvd_graph_t *out, int64_t n, int64_t nnz, const int64_t *rowptr,
+                     const int32_t *colidx, const void *w, int32_t wdtype, uint32_t flags,
+                     nvd_stream_t stream);
+
+/* nvd_graph_destroy -- release a handle and all its device memory.  NULL is a no-op. */
+int nvd_graph_destroy(nvd_graph_t g);
+
+/*
+ * nvd_graph_info -- sizes of a handle.  Any output pointer may be NULL.
+ *   n, nnz        nodes and stored entries after cleaning (self-loops dropped,
+ *                 repeated entries merged);
+ *   ncomp         connected components (isolated nodes count as components);
+ *   device_bytes  device memory currently held by the handle (graph + workspace).
+ */
+int nvd_graph_info(nvd_graph_t g, int64_t *n, int64_t *nnz, int32_t *ncomp,
+                   int64_t *device_bytes);
+
+/* ------------------------------------------------------------------ solving */
+
+typedef enum {
+    NVD_MODE_FP64 = 0,  /* FP64 vectors, FP64 arithmetic throughout */
+    NVD_MODE_FP32 = 1,  /* FP32 vectors and SpMV/SpMM, FP64 inner products and scalars */
+    NVD_MODE_MIXED = 2  /* FP32 block-PCG inside an FP64 iterative-refinement loop */
+} nvd_mode;
+
+#define NVD_SOLVE_SINGLE_RHS 1u   /* solve the k pairs one right-hand side at a time */
+#define NVD_SOLVE_D2_DEVICE 2u    /* d2_out is a device pointer (default: host) */
+#define NVD_SOLVE_HOST_INPUTS 4u  /* x, y (and z_out) are host pointers; copies are done here */
+#define NVD_SOLVE_PERSISTENT 8u   /* run each PCG solve inside one persistent cooperative kernel */
+#define NVD_SOLVE_NO_SYNC 16u     /* with NVD_SOLVE_D2_DEVICE and no stats: return without a final sync */
+
+typedef struct {
+    int32_t mode;        /* nvd_mode */
+    int32_t max_iter;    /* CG iteration limit per solve (MIXED: per inner solve) */
+    double rtol;         /* FP64/FP32: stop when ||delta - L z||_2 <= rtol ||delta||_2 per pair
+                            (recursive residual); MIXED: tolerance of each inner FP32 solve */
+    double d2_rtol;      /* MIXED: stop refining when the relative change of d^2 <= d2_rtol */
+    int32_t max_refine;  /* MIXED: limit on outer refinement steps */
+    int32_t check_every; /* iterations between host convergence polls (host-driven loop) */
+    int32_t kt;          /* right-hand sides per tile: 0 = automatic, else 1, 4, 8, 16 or 32 */
+    uint32_t flags;      /* NVD_SOLVE_* bits */
+} nvd_solve_opts;
+
+typedef struct {
+    int32_t iters;        /* CG iterations used (MIXED: summed over inner solves) */
+    int32_t refine_steps; /* MIXED: outer steps; 0 otherwise */
+    double rel_resid;     /* final relative residual ||delta - L z|| / ||delta|| (recursive;
+                             MIXED: the true FP64 residual of the last refinement step) */
+    int32_t status;       /* nvd_status of this pair */
+    int32_t reserved;
+} nvd_solve_stats;
+
+/* nvd_solve_opts_default -- FP64 mode, rtol 1e-10, max_iter 10000, d2_rtol 1e-8,
+ * max_refine 8, check_every 8, kt automatic, no flags. */
+void nvd_solve_opts_default(nvd_solve_opts *o);
+
+/*
+ * nvd_ge_distance -- d^2 = (x_j - y_j)^T L^+ (x_j - y_j) for j < k (Section 3.1,
+ * GE equation), by PCG on L z = P(x_j - y_j) (Section 3.2), P the per-component
+ * mean-zero projector.  d = sqrt(max(d^2, 0)) is left to the caller.
+ *
+ *   x, y    [k][n] device arrays (host with NVD_SOLVE_HOST_INPUTS) of xdtype.
+ *   d2_out  [k] double, host unless NVD_SOLVE_D2_DEVICE.
+ *   z_out   optional [k][n] of xdtype: z_j = L^+ (x_j - y_j), mean-zero on every
+ *           component (what nvd_ge_grad consumes).  NULL to skip.
+ *   stats   optional [k] host array.
+ *
+ * FP64 mode returns d^2 = delta^T z at the converged z; MIXED mode returns the
+ * variational estimate 2 delta^T z - z^T L z from the FP64 residual (error
+ * quadratic in the error of z).  Non-convergence still writes every output and
+ * returns NVD_ERR_NOT_CONVERGED; per-pair status is in stats.
+ */
+int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdtype,
+                    const nvd_solve_opts *opts, double *d2_out, void *z_out,
+                    nvd_solve_stats *stats, nvd_stream_t stream);
+
+/*
+ * nvd_ge_distance_batched -- many graphs in one solve: the G graphs are treated as
+ * the diagonal blocks of one block-diagonal Laplacian and every (graph, pair)
+ * keeps its own CG scalars and convergence test, so the result equals G
+ * independent nvd_ge_distance calls.  The PCG loop runs inside one persistent
+ * cooperative kernel captured in a CUDA graph (replayed when the same arguments
+ * come again).
+ *
+ *   graphs  [G] handles (same device).
+ *   k_per   [G] pairs per graph.
+ *   x, y    [G] device pointers, x[g] and y[g] of shape [k_per[g]][n_g].
+ *   d2_out  [sum k_per] host doubles, graph after graph.
+ *   stats   optional [sum k_per].
+ */
+int nvd_ge_distance_batched(const nvd_graph_t *graphs, int32_t G, const int32_t *k_per,
+                            const void *const *x, const void *const *y, int32_t xdtype,
+                            const nvd_solve_opts *opts, double *d2_out, nvd_solve_stats *stats,
+                            nvd_stream_t stream);
+
+/*
+ * nvd_ge_grad -- adjoint of d^2 (no new solve; reuses z from nvd_ge_distance).
+ * With upstream weights gbar_j = dLoss/d(d_j^2):
+ *
+ *   grad_x[j] =  2 gbar_j z_j,   grad_y[j] = -2 gbar_j z_j        (L^+ symmetric)
+ *   grad_w[e] = -1/2 sum_j gbar_j (z_j[u] - z_j[v])^2             per stored entry e = (u, v)
+ *
+ * The weight gradient follows from dL^+ = -L^+ dL L^+ with the operator built
+ * from W_sym = (W + W^T)/2, so the two stored entries of an undirected edge
+ * together receive -(z_u - z_v)^2 -- the derivative with respect to the edge
+ * weight.  Self-loop entries receive 0.
+ *
+ *   z       [k][n] device array of zdtype (z_out of nvd_ge_distance).
+ *   gbar    [k] device doubles.
+ *   grad_w  [nnz] device array in the entry order given to nvd_graph_create, of
+ *           the graph's weight dtype, or NULL.
+ *   grad_x, grad_y  [k][n] device arrays of zdtype, or NULL.
+ */
+int nvd_ge_grad(nvd_graph_t g, int32_t k, const void *z, int32_t zdtype, const double *gbar,
+                void *grad_w, void *grad_x, void *grad_y, nvd_stream_t stream);
+
+/*
+ * nvd_laplacian_apply -- y_j = L x_j for j < k ([k][n] device arrays of dtype),
+ * the operator the solver uses (exposed for testing and benchmarking; FP64
+ * arithmetic for NVD_F64, FP32 for NVD_F32).
+ */
+int nvd_laplacian_apply(nvd_graph_t g, int32_t k, const void *x, void *y, int32_t dtype,
+                        nvd_stream_t stream);
+
+/* ------------------------------------------------------------------ diagnostics */
+
+/* nvd_status_string -- static name of a status code. */
+const char *nvd_status_string(int status);
+
+/* nvd_last_error -- detail of the last failure on this thread ("" if none). */
+const char *nvd_last_error(void);
+
+/*
+ * Kernel timing.  While enabled, every launch of the Laplacian SpMV/SpMM kernel
+ * made by nvd_ge_distance is bracketed by CUDA events on its stream;
+ * nvd_profile_read returns the launch count, summed event time in ms and summed
+ * algorithmic bytes of those launches since the last read (and resets them).
+ * Class 0 = the SpMV/SpMM kernel.  Enabling forces the host-driven loop (no
+ * persistent kernel) so launches can be bracketed.
+ */
+int nvd_profile_enable(int32_t on);
+int nvd_profile_read(int32_t kernel_class, int64_t *launches, double *total_ms,
+                     double *bytes);
+
+/* nvd_version -- library version string. */
+const char *nvd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NVD_H_ */

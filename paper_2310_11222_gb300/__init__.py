@@ -1,0 +1,422 @@
+"""GB300-native Generalized-Euclidean (GE) node-vector distance.
+
+    d(x, y)^2 = (x - y)^T L^+ (x - y)            (Section 3.1 of the paper, GE equation)
+
+computed without forming L^+: the CUDA library (``_build/libnvd.so``, C ABI in
+``include/nvd.h``) solves L z = x - y with a Jacobi-preconditioned conjugate
+gradient (Section 3.2, the "CG" Laplacian solver) whose SpMV/SpMM, fused
+update/inner-product passes, preconditioner and per-component projection are
+hand-written sm_103a kernels.
+
+This module only marshals arguments to the C ABI (ctypes); every step of the
+computation runs in the library's kernels.  There is no CPU fallback: if the
+library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "Graph", "SolveOpts", "SolveStats", "ge_distance", "ge_distance_batched", "ge_grad",
+    "laplacian_apply", "GEDistance", "ge_distance_autograd", "profile_enable", "profile_read",
+    "library_path", "load_library", "NvdError", "MODE_FP64", "MODE_FP32", "MODE_MIXED",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libnvd.so")
+
+F32, F64 = 0, 1
+MODE_FP64, MODE_FP32, MODE_MIXED = 0, 1, 2
+SOLVE_SINGLE_RHS = 1
+SOLVE_D2_DEVICE = 2
+SOLVE_HOST_INPUTS = 4
+SOLVE_PERSISTENT = 8
+SOLVE_NO_SYNC = 16
+GRAPH_DEVICE_PTRS = 1
+GRAPH_SKIP_SYM_CHECK = 2
+
+STATUS = {0: "NVD_OK", 1: "NVD_ERR_INVALID_ARG", 2: "NVD_ERR_NOT_SYMMETRIC", 3: "NVD_ERR_BAD_WEIGHT",
+          4: "NVD_ERR_OOM", 5: "NVD_ERR_CUDA", 6: "NVD_ERR_NOT_CONVERGED", 7: "NVD_ERR_NUMERIC",
+          8: "NVD_ERR_TIMEOUT", 9: "NVD_ERR_UNSUPPORTED"}
+
+
+class NvdError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class SolveOpts(ctypes.Structure):
+    """Mirror of ``nvd_solve_opts``."""
+    _fields_ = [("mode", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("d2_rtol", ctypes.c_double), ("max_refine", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("kt", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class SolveStats(ctypes.Structure):
+    """Mirror of ``nvd_solve_stats``."""
+    _fields_ = [("iters", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("rel_resid", ctypes.c_double), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "nvd_graph_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_uint32, ctypes.c_void_p]),
+    "nvd_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "nvd_graph_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "nvd_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+    "nvd_ge_distance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "nvd_ge_distance_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.POINTER(SolveOpts), ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
+    "nvd_ge_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    "nvd_laplacian_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p]),
+    "nvd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "nvd_last_error": (ctypes.c_char_p, []),
+    "nvd_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
+    "nvd_profile_read": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "nvd_version": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load ``libnvd.so`` (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {_LIB_PATH} is missing "
+                                   "(run __graft_entry__.build() or paper_2310_11222_gb300/build.py)")
+            lib = ctypes.CDLL(_LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, where: str, allow=(0,)):
+    if rc not in allow:
+        detail = load_library().nvd_last_error()
+        raise NvdError(rc, where, detail.decode() if detail else "")
+    return rc
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(device=None):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def default_opts(mode: int = MODE_FP64, **kw) -> SolveOpts:
+    o = SolveOpts()
+    load_library().nvd_solve_opts_default(ctypes.byref(o))
+    o.mode = mode
+    if mode == MODE_MIXED:
+        o.rtol = 1e-4
+    elif mode == MODE_FP32:
+        o.rtol = 1e-5
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """Handle on a graph held in device memory (``nvd_graph_create``).
+
+    ``rowptr`` int64 [n+1], ``colidx`` int32 [nnz], ``w`` float32/float64 [nnz] (or None
+    for unit weights) describe a symmetric CSR adjacency.  numpy arrays are copied
+    from the host; torch CUDA tensors are read on the device.
+    """
+
+    def __init__(self, rowptr, colidx, w=None, *, skip_sym_check: bool = False, device=None):
+        torch = _torch()
+        lib = load_library()
+        self._lib = lib
+        self.handle = ctypes.c_void_p(None)
+        flags = GRAPH_SKIP_SYM_CHECK if skip_sym_check else 0
+        keep = []
+        if isinstance(rowptr, np.ndarray):
+            rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+            ci = np.ascontiguousarray(colidx, dtype=np.int32)
+            wv = None if w is None else np.ascontiguousarray(w)
+            if wv is not None and wv.dtype not in (np.float32, np.float64):
+                wv = wv.astype(np.float64)
+            wdt = F64 if (wv is None or wv.dtype == np.float64) else F32
+            keep = [rp, ci, wv]
+            p_rp, p_ci = rp.ctypes.data, ci.ctypes.data
+            p_w = None if wv is None else wv.ctypes.data
+            n = rp.shape[0] - 1
+            nnz = ci.shape[0]
+            dev = device if device is not None else torch.cuda.current_device()
+        else:
+            rp = rowptr.contiguous()
+            ci = colidx.contiguous()
+            wv = None if w is None else w.contiguous()
+            if rp.dtype != torch.int64 or ci.dtype != torch.int32:
+                raise TypeError("rowptr must be int64 and colidx int32")
+            wdt = F64 if wv is None else _dtype_code(wv)
+            keep = [rp, ci, wv]
+            if rp.is_cuda:
+                flags |= GRAPH_DEVICE_PTRS
+                dev = rp.device.index
+            else:
+                dev = device if device is not None else torch.cuda.current_device()
+            p_rp, p_ci = rp.data_ptr(), ci.data_ptr()
+            p_w = None if wv is None else wv.data_ptr()
+            n = rp.shape[0] - 1
+            nnz = ci.shape[0]
+        self.device = torch.device("cuda", dev)
+        self.wdtype = wdt
+        self.n_user = int(n)
+        self.nnz_user = int(nnz)
+        with torch.cuda.device(self.device):
+            rc = lib.nvd_graph_create(ctypes.byref(self.handle), int(n), int(nnz), p_rp, p_ci, p_w, wdt,
+                                      flags, _stream_ptr(self.device))
+        del keep
+        _check(rc, "nvd_graph_create")
+
+    @classmethod
+    def from_csr(cls, g, **kw):
+        """From an object with ``rowptr``, ``colidx``, ``w`` numpy attributes."""
+        return cls(g.rowptr, g.colidx, g.w, **kw)
+
+    def info(self):
+        n, nnz, nc, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        _check(self._lib.nvd_graph_info(self.handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc),
+                                        ctypes.byref(nb)), "nvd_graph_info")
+        return {"n": n.value, "nnz": nnz.value, "ncomp": nc.value, "device_bytes": nb.value}
+
+    @property
+    def n(self) -> int:
+        return self.n_user
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.nvd_graph_destroy(self.handle)
+            self.handle = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
+                d2_rtol: float = 1e-8, max_iter: int = 10000, max_refine: int = 8, kt: int = 0,
+                check_every: int = 8, single_rhs: bool = False, persistent: bool = False,
+                return_z: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
+    """Squared GE distances d^2 for the k pairs (rows) of x, y ([k, n] or [n]).
+
+    CUDA tensors run on the device (d^2 returned as a CUDA float64 tensor); CPU
+    tensors / numpy arrays go through the host-buffer path of the C ABI (copies
+    inside the call) and d^2 comes back on the host.
+    """
+    torch = _torch()
+    lib = load_library()
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(x)
+    if isinstance(y, np.ndarray):
+        y = torch.from_numpy(y)
+    one = x.dim() == 1
+    X = (x[None] if one else x).contiguous()
+    Y = (y[None] if one else y).contiguous()
+    if X.shape != Y.shape or X.dtype != Y.dtype or X.shape[1] != graph.n:
+        raise ValueError("x and y must both be [k, n] of the same dtype")
+    k = X.shape[0]
+    o = default_opts(mode, d2_rtol=d2_rtol, max_iter=max_iter, max_refine=max_refine, kt=kt,
+                     check_every=check_every)
+    if rtol is not None:
+        o.rtol = rtol
+    if single_rhs:
+        o.flags |= SOLVE_SINGLE_RHS
+    if persistent:
+        o.flags |= SOLVE_PERSISTENT
+    xdt = _dtype_code(X)
+    stats = (SolveStats * max(k, 1))()
+    if X.is_cuda:
+        d2 = torch.empty(k, dtype=torch.float64, device=X.device)
+        Z = torch.empty_like(X) if return_z else None
+        o.flags |= SOLVE_D2_DEVICE
+        with torch.cuda.device(X.device):
+            rc = lib.nvd_ge_distance(graph.handle, k, X.data_ptr(), Y.data_ptr(), xdt, ctypes.byref(o),
+                                     d2.data_ptr(), None if Z is None else Z.data_ptr(), stats,
+                                     _stream_ptr(X.device))
+    else:
+        d2 = torch.empty(k, dtype=torch.float64)
+        Z = torch.empty_like(X) if return_z else None
+        o.flags |= SOLVE_HOST_INPUTS
+        with torch.cuda.device(graph.device):
+            rc = lib.nvd_ge_distance(graph.handle, k, X.data_ptr(), Y.data_ptr(), xdt, ctypes.byref(o),
+                                     d2.data_ptr(), None if Z is None else Z.data_ptr(), stats,
+                                     _stream_ptr(graph.device))
+    _check(rc, "nvd_ge_distance", allow=(0, 6) if allow_not_converged else (0,))
+    out = [d2[0] if one else d2]
+    if return_z:
+        out.append(Z[0] if one else Z)
+    if return_stats:
+        out.append([{"iters": s.iters, "refine_steps": s.refine_steps, "rel_resid": s.rel_resid,
+                     "status": s.status} for s in stats[:k]])
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def ge_distance_batched(graphs: Sequence[Graph], xs, ys, *, mode: int = MODE_FP32,
+                        rtol: Optional[float] = None, max_iter: int = 10000, return_stats: bool = False):
+    """d^2 for many graphs in one persistent launch; xs[g], ys[g] are CUDA [k_g, n_g]."""
+    torch = _torch()
+    lib = load_library()
+    G = len(graphs)
+    hs = (ctypes.c_void_p * G)(*[g.handle.value for g in graphs])
+    ks = (ctypes.c_int32 * G)(*[int(x.shape[0]) for x in xs])
+    xs = [x.contiguous() for x in xs]
+    ys = [y.contiguous() for y in ys]
+    px = (ctypes.c_void_p * G)(*[x.data_ptr() for x in xs])
+    py = (ctypes.c_void_p * G)(*[y.data_ptr() for y in ys])
+    total = sum(int(x.shape[0]) for x in xs)
+    o = default_opts(mode, max_iter=max_iter)
+    if rtol is not None:
+        o.rtol = rtol
+    d2 = torch.empty(total, dtype=torch.float64)
+    stats = (SolveStats * max(total, 1))()
+    dev = xs[0].device
+    with torch.cuda.device(dev):
+        rc = lib.nvd_ge_distance_batched(hs, G, ks, px, py, _dtype_code(xs[0]), ctypes.byref(o),
+                                         d2.data_ptr(), stats, _stream_ptr(dev))
+    _check(rc, "nvd_ge_distance_batched")
+    if return_stats:
+        return d2, [{"iters": s.iters, "rel_resid": s.rel_resid, "status": s.status} for s in stats[:total]]
+    return d2
+
+
+def ge_grad(graph: Graph, z, gbar, *, want_w: bool = True, want_x: bool = True):
+    """Adjoint of d^2: (grad_w [nnz], grad_x [k, n], grad_y [k, n]) from z and gbar = dL/d(d^2)."""
+    torch = _torch()
+    lib = load_library()
+    Z = z.contiguous()
+    gb = gbar.to(device=Z.device, dtype=torch.float64).contiguous()
+    wdt = torch.float64 if graph.wdtype == F64 else torch.float32
+    gw = torch.empty(graph.nnz_user, dtype=wdt, device=Z.device) if want_w else None
+    gx = torch.empty_like(Z) if want_x else None
+    gy = torch.empty_like(Z) if want_x else None
+    with torch.cuda.device(Z.device):
+        rc = lib.nvd_ge_grad(graph.handle, Z.shape[0], Z.data_ptr(), _dtype_code(Z), gb.data_ptr(),
+                             None if gw is None else gw.data_ptr(), None if gx is None else gx.data_ptr(),
+                             None if gy is None else gy.data_ptr(), _stream_ptr(Z.device))
+    _check(rc, "nvd_ge_grad")
+    return gw, gx, gy
+
+
+def laplacian_apply(graph: Graph, x):
+    """y = L x for each row of x ([k, n] CUDA tensor)."""
+    torch = _torch()
+    lib = load_library()
+    X = (x[None] if x.dim() == 1 else x).contiguous()
+    Yt = torch.empty_like(X)
+    with torch.cuda.device(X.device):
+        rc = lib.nvd_laplacian_apply(graph.handle, X.shape[0], X.data_ptr(), Yt.data_ptr(), _dtype_code(X),
+                                     _stream_ptr(X.device))
+    _check(rc, "nvd_laplacian_apply")
+    return Yt[0] if x.dim() == 1 else Yt
+
+
+def profile_enable(on: bool = True):
+    _check(load_library().nvd_profile_enable(1 if on else 0), "nvd_profile_enable")
+
+
+def profile_read():
+    """(launches, total_ms, algorithmic_bytes) of the SpMV/SpMM kernel since the last read."""
+    n, ms, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(load_library().nvd_profile_read(0, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)),
+           "nvd_profile_read")
+    return n.value, ms.value, b.value
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class GEDistance(torch.autograd.Function):
+        """d^2 = (x - y)^T L^+ (x - y) with gradients for x, y and the CSR weights.
+
+        forward(x, y, w, graph, opts) -> d^2 [k]; ``w`` must be the weight tensor the
+        graph was built from (its values are read at graph creation; pass it here so
+        autograd tracks it).  Backward reuses the forward z = L^+ delta (no new
+        solve) through ``nvd_ge_grad``.
+        """
+
+        @staticmethod
+        def forward(ctx, x, y, w, graph, opts):
+            d2, z = ge_distance(graph, x, y, return_z=True, **(opts or {}))
+            ctx.graph = graph
+            ctx.save_for_backward(z)
+            ctx.want_w = w is not None
+            return d2
+
+        @staticmethod
+        def backward(ctx, gd2):
+            (z,) = ctx.saved_tensors
+            one = z.dim() == 1
+            Z = z[None] if one else z
+            g = gd2.reshape(-1)
+            gw, gx, gy = ge_grad(ctx.graph, Z, g, want_w=ctx.want_w,
+                                 want_x=ctx.needs_input_grad[0] or ctx.needs_input_grad[1])
+            if gx is not None and one:
+                gx, gy = gx[0], gy[0]
+            return gx, gy, gw, None, None
+
+    return GEDistance
+
+
+class _Lazy:
+    def __init__(self):
+        self._cls = None
+
+    def __getattr__(self, item):
+        if self._cls is None:
+            self._cls = _make_autograd()
+        return getattr(self._cls, item)
+
+
+GEDistance = _Lazy()
+
+
+def ge_distance_autograd(graph: Graph, x, y, w=None, **opts):
+    """Differentiable d^2 (see ``GEDistance``)."""
+    return GEDistance.apply(x, y, w, graph, opts)

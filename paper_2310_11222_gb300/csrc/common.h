@@ -1,0 +1,114 @@
+// Shared host/device definitions of the GE-distance library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nvd {
+
+constexpr int NT = 256;          // threads per CTA for every work kernel
+constexpr int NWARP = NT / 32;
+
+// Sub-item budgets of the SpMV/SpMM for KT right-hand sides with vector/accumulator
+// element sizes szv/sza (shared by the host planner and the kernels).
+//   rows per sub-item: the row accumulators (rows x KT x sza) fit 8 KB, at most NT;
+//   entries per sub-item: KT = 1 stages 1024 products in shared memory, KT > 1
+//   gathers about 32 KB of neighbour rows.  Longer rows are split into chunks.
+constexpr int sp_rows_budget(int KT, int sza) {
+    return (8192 / (KT * sza)) > NT ? NT : (8192 / (KT * sza));
+}
+constexpr int sp_nnz_budget(int KT, int szv) { return KT == 1 ? 1024 : 32768 / (KT * szv); }
+// doubles of reduction scratch per CTA
+constexpr int red_doubles(int KT) { return (NWARP * 4 * KT) > 256 ? NWARP * 4 * KT : 256; }
+constexpr int vec_smem_bytes(int KT) { return (red_doubles(KT) + 4 * KT) * 8; }
+
+// Sub-item of the Laplacian SpMV/SpMM.
+//   kind 0: rows [r0, r1) of one segment whose entries fit one CTA pass.
+//   kind 1: entries [e0, e1) of a long row r0 split over several sub-items
+//           (merge-path style row splitting); this is chunk `hchunk` of `nchunk`;
+//           its partial row sum goes to hsum[hbase + hchunk] and the chunk that
+//           finishes last (counter hcount[hrow]) adds the chunks in chunk order,
+//           applies the row epilogue and owns partial slot (n_blocks + hrow).
+struct SpItem {
+    int32_t r0, r1, kind, hrow;
+    int64_t e0, e1;
+    int32_t hbase, hchunk, nchunk, pad;
+};
+static_assert(sizeof(SpItem) == 48, "SpItem layout");
+
+// A CTA block: a contiguous run of work inside one segment.
+//   SpMV blocks: sub-items [i0, i1).  Vector blocks: rows [i0, i1).
+struct Block {
+    int64_t i0, i1;
+    int32_t seg, pad;
+};
+
+// Where one user graph's pairs live: x, y, z of shape [k][n_o] already offset to
+// the first column of the tile; the graph's nodes are internal nodes
+// [base, base + n_o) and its segments [seg0, seg1).
+struct Owner {
+    const void *x, *y;
+    void *z;
+    int64_t base, ld;
+    int32_t kc;        // valid columns of this tile (pairs beyond k are padding)
+    int32_t seg0, seg1;
+    int32_t pad;
+};
+
+// Everything a work kernel needs, passed by value.  Pointers whose element type
+// depends on the solve precision are void* and cast by the kernel templates.
+struct Ctx {
+    // ---- graph (internal node order; components are contiguous node ranges)
+    int64_t n;
+    const int64_t *rowptr;
+    const int32_t *colidx;   // padded to a multiple of 4 entries
+    const void *w;           // TW, padded like colidx
+    const double *deg64, *dinv64;
+    const float *deg32, *dinv32;
+    // ---- segments = connected components with >= 2 nodes
+    int32_t nseg;
+    const int64_t *seg_begin, *seg_end;
+    const int32_t *seg_owner;
+    // ---- SpMV work decomposition
+    const SpItem *items;
+    const Block *sblk;              // [n_sblk]
+    int64_t n_sblk;
+    const int32_t *seg_sblk_off;    // [nseg+1]
+    const int32_t *seg_heavy_off;   // [nseg+1] heavy (split) rows of each segment
+    int32_t *hcount;                // [n_heavy] chunk arrival counters (self-resetting)
+    double *hsum;                   // [n_chunks][KT] partial row sums of split rows
+    // ---- vector-pass work decomposition
+    const Block *vblk;              // [n_vblk]
+    int64_t n_vblk;
+    const int32_t *seg_vblk_off;    // [nseg+1]
+    // ---- deterministic two-level reductions
+    double *part;                   // [ND][part_stride][KT]
+    int64_t part_stride;            // >= max(n_sblk + n_heavy, n_vblk)
+    unsigned *counter;              // [nseg] arrival counters (self-resetting)
+    // ---- per (segment, column) scalar state, [nseg][KT]
+    double *rho, *rr, *rr0, *alpha, *beta, *mean, *meanx, *d2, *dz, *zr;
+    int32_t *active, *iters, *status;
+    int32_t *n_active;              // number of (segment, column) pairs still iterating
+    int32_t *err;                   // sticky device error code (grid-barrier timeout)
+    double rtol2;
+    int32_t max_iter;
+    // ---- sources and destinations: one "owner" per user graph (one for single-graph
+    //      solves, passed inline in own0; G for batched solves, in the owners table)
+    const struct Owner *owners;     // [n_owner] device table, or NULL = use own0
+    int32_t n_owner;
+    const int32_t *perm;            // internal -> user node (NULL = identity)
+    // ---- persistent-kernel grid barrier
+    unsigned *bar_count, *bar_gen;
+    Owner own0;
+};
+
+// Per (owner, column) result collected at the end of a tile.
+struct ColResult {
+    double d2;
+    double rr;
+    double rr0;
+    int32_t iters;
+    int32_t status;
+};
+
+}  // namespace nvd

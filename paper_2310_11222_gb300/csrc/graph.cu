@@ -1,0 +1,810 @@
+// Graph handles: CSR intake, validation, degrees, connected components, work plans.
+//
+// The operator is the graph Laplacian L = D - W of Section 3.1 (undirected,
+// positive weights).  Creation checks the input, drops self-loops, merges
+// repeated entries, computes the weighted degrees D (and D^-1 for the Jacobi
+// preconditioner), finds the connected components (whose per-component
+// constants span the null space of L) and, if a component is not a contiguous
+// node range, relabels the nodes so that every component is one -- the solver
+// then treats each component as an independent "segment".
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "graph.h"
+
+namespace nvd {
+
+// ------------------------------------------------------------------ errors
+
+static thread_local char g_last_error[512] = {0};
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_last_error[0] = 0; }
+const char *last_error() { return g_last_error; }
+
+int DevBuf::alloc(size_t b) {
+    release();
+    cudaError_t e = cudaMalloc(&p, b ? b : 16);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? NVD_ERR_OOM : NVD_ERR_CUDA;
+    }
+    bytes = b;
+    return NVD_OK;
+}
+
+// ------------------------------------------------------------------ kernels
+
+// flags[0] column out of range, [1] unsorted or repeated column, [2] self-loop,
+// [3] weight <= 0 / NaN / Inf.  One warp per row.
+template <class TW>
+__global__ void k_check_rows(int64_t n, const int64_t *__restrict__ rowptr,
+                             const int32_t *__restrict__ colidx, const TW *__restrict__ w,
+                             int *flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int f0 = 0, f1 = 0, f2 = 0, f3 = 0;
+    for (int64_t u = warp; u < n; u += nw) {
+        const int64_t a = rowptr[u], b = rowptr[u + 1];
+        for (int64_t e = a + lane; e < b; e += 32) {
+            const int32_t v = colidx[e];
+            if (v < 0 || v >= n) f0 = 1;
+            if (v == u) f2 = 1;
+            if (e > a && colidx[e - 1] >= v) f1 = 1;
+            if (w) {
+                const double x = (double)w[e];
+                if (!(x > 0.0) || !isfinite(x)) f3 = 1;
+            }
+        }
+    }
+    f0 = __any_sync(0xffffffffu, f0);
+    f1 = __any_sync(0xffffffffu, f1);
+    f2 = __any_sync(0xffffffffu, f2);
+    f3 = __any_sync(0xffffffffu, f3);
+    if (lane == 0) {
+        if (f0) atomicOr(flags + 0, 1);
+        if (f1) atomicOr(flags + 1, 1);
+        if (f2) atomicOr(flags + 2, 1);
+        if (f3) atomicOr(flags + 3, 1);
+    }
+}
+
+// Symmetry: every entry (u, v, w) needs (v, u, w) with the identical weight.
+// Columns are sorted and unique here; one warp per row, binary search in row v.
+template <class TW>
+__global__ void k_check_sym(int64_t n, const int64_t *__restrict__ rowptr,
+                            const int32_t *__restrict__ colidx, const TW *__restrict__ w,
+                            int *bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int f = 0;
+    for (int64_t u = warp; u < n; u += nw) {
+        const int64_t a = rowptr[u], b = rowptr[u + 1];
+        for (int64_t e = a + lane; e < b; e += 32) {
+            const int32_t v = colidx[e];
+            int64_t lo = rowptr[v], hi = rowptr[v + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (colidx[mid] < u) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= rowptr[v + 1] || colidx[lo] != u) f = 1;
+            else if (w && w[lo] != w[e]) f = 1;
+        }
+    }
+    if (__any_sync(0xffffffffu, f) && lane == 0) atomicOr(bad, 1);
+}
+
+// Weighted degree D_uu = sum_v w_uv (FP64, fixed lane-strided order + butterfly).
+template <class TW>
+__global__ void k_degree(int64_t n, const int64_t *__restrict__ rowptr, const TW *__restrict__ w,
+                         double *deg64, double *dinv64, float *deg32, float *dinv32) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nw) {
+        const int64_t a = rowptr[u], b = rowptr[u + 1];
+        double s = 0.0;
+        for (int64_t e = a + lane; e < b; e += 32) s += w ? (double)w[e] : 1.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) {
+            deg64[u] = s;
+            dinv64[u] = s > 0.0 ? 1.0 / s : 0.0;
+            deg32[u] = (float)s;
+            dinv32[u] = s > 0.0 ? (float)(1.0 / s) : 0.0f;
+        }
+    }
+}
+
+template <class T>
+__global__ void k_fill(T *p, int64_t n, T v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_round_w32(const double *__restrict__ w, float *w32, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        w32[i] = (float)w[i];
+}
+
+// Connected components by hooking and pointer jumping.  parent[] only ever
+// decreases and always points to a smaller-or-equal node, so find() terminates;
+// at the fixed point every node points at the smallest node of its component.
+__device__ __forceinline__ int32_t cc_find(const int32_t *parent, int32_t x) {
+    for (;;) {
+        const int32_t p = __ldcg(parent + x);
+        if (p == x) return x;
+        x = p;
+    }
+}
+
+__global__ void k_cc_hook(int64_t n, const int64_t *__restrict__ rowptr,
+                          const int32_t *__restrict__ colidx, int32_t *parent, int *changed) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int ch = 0;
+    for (int64_t u = warp; u < n; u += nw) {
+        const int64_t a = rowptr[u], b = rowptr[u + 1];
+        for (int64_t e = a + lane; e < b; e += 32) {
+            const int32_t v = colidx[e];
+            if (v == u) continue;
+            const int32_t ru = cc_find(parent, (int32_t)u), rv = cc_find(parent, v);
+            if (ru != rv) {
+                const int32_t lo = ru < rv ? ru : rv, hi = ru < rv ? rv : ru;
+                atomicMin(parent + hi, lo);
+                ch = 1;
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, ch) && lane == 0) atomicOr(changed, 1);
+}
+
+__global__ void k_cc_compress(int64_t n, int32_t *parent) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        parent[i] = cc_find(parent, (int32_t)i);
+}
+
+static int grid_for(int64_t work, int threads_per_item, int num_sms) {
+    int64_t b = (work * threads_per_item + 255) / 256;
+    int64_t cap = (int64_t)num_sms * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------------------------------ host helpers
+
+namespace {
+
+struct HostCSR {
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> col;
+    std::vector<double> w;       // weights (as double; converted back to wdtype on upload)
+    std::vector<int64_t> uent;   // user entry -> entry of this CSR (-1 dropped)
+};
+
+// Drop self-loops, sort each row by column, merge repeated columns (summing).
+void clean_csr(int64_t n, const std::vector<int64_t> &rp, const std::vector<int32_t> &col,
+               const std::vector<double> &w, HostCSR &out) {
+    const int64_t nnz = rp[n];
+    out.rowptr.assign(n + 1, 0);
+    out.col.clear();
+    out.w.clear();
+    out.uent.assign(nnz, -1);
+    std::vector<int64_t> idx;
+    for (int64_t u = 0; u < n; ++u) {
+        idx.clear();
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e)
+            if (col[e] != u) idx.push_back(e);
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int64_t a, int64_t b) { return col[a] < col[b]; });
+        for (size_t t = 0; t < idx.size(); ++t) {
+            const int64_t e = idx[t];
+            if (t > 0 && col[idx[t - 1]] == col[e]) {
+                out.w.back() += w[e];
+            } else {
+                out.col.push_back(col[e]);
+                out.w.push_back(w[e]);
+            }
+            out.uent[e] = (int64_t)out.col.size() - 1;
+        }
+        out.rowptr[u + 1] = (int64_t)out.col.size();
+    }
+}
+
+template <class T>
+int upload_padded(nvd::DevBuf &buf, const T *host, int64_t n, cudaStream_t s) {
+    const int64_t npad = ((n + 3) / 4) * 4 + 4;
+    NVD_TRY(buf.alloc((size_t)npad * sizeof(T)));
+    NVD_TRY_CUDA(cudaMemsetAsync(buf.p, 0, (size_t)npad * sizeof(T), s));
+    if (n > 0)
+        NVD_TRY_CUDA(cudaMemcpyAsync(buf.p, host, (size_t)n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return NVD_OK;
+}
+
+int upload_weights(nvd_graph_s *g, const std::vector<double> &w, cudaStream_t s) {
+    if (g->wdtype == NVD_F64) return upload_padded(g->w, w.data(), (int64_t)w.size(), s);
+    std::vector<float> wf(w.size());
+    for (size_t i = 0; i < w.size(); ++i) wf[i] = (float)w[i];
+    NVD_TRY(upload_padded(g->w, wf.data(), (int64_t)wf.size(), s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    return NVD_OK;
+}
+
+int download_csr(nvd_graph_s *g, std::vector<int32_t> &col, std::vector<double> &w, cudaStream_t s) {
+    col.resize(g->nnz);
+    w.resize(g->nnz);
+    if (g->nnz) {
+        NVD_TRY_CUDA(cudaMemcpyAsync(col.data(), g->colidx.p, g->nnz * 4, cudaMemcpyDeviceToHost, s));
+        if (g->wdtype == NVD_F64) {
+            NVD_TRY_CUDA(cudaMemcpyAsync(w.data(), g->w.p, g->nnz * 8, cudaMemcpyDeviceToHost, s));
+            NVD_TRY_CUDA(cudaStreamSynchronize(s));
+        } else {
+            std::vector<float> wf(g->nnz);
+            NVD_TRY_CUDA(cudaMemcpyAsync(wf.data(), g->w.p, g->nnz * 4, cudaMemcpyDeviceToHost, s));
+            NVD_TRY_CUDA(cudaStreamSynchronize(s));
+            for (int64_t i = 0; i < g->nnz; ++i) w[i] = wf[i];
+        }
+    }
+    return NVD_OK;
+}
+
+template <class TW>
+int run_checks(nvd_graph_s *g, bool have_w, int *flags_h, cudaStream_t s) {
+    nvd::DevBuf flags;
+    NVD_TRY(flags.alloc(4 * sizeof(int)));
+    NVD_TRY_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int), s));
+    k_check_rows<TW><<<nvd::grid_for(g->n, 32, g->num_sms), 256, 0, s>>>(
+        g->n, g->rowptr.as<int64_t>(), g->colidx.as<int32_t>(),
+        have_w ? g->w.as<TW>() : nullptr, flags.as<int>());
+    NVD_TRY_CUDA(cudaGetLastError());
+    NVD_TRY_CUDA(cudaMemcpyAsync(flags_h, flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    return NVD_OK;
+}
+
+template <class TW>
+int run_sym(nvd_graph_s *g, int *bad_h, cudaStream_t s) {
+    nvd::DevBuf bad;
+    NVD_TRY(bad.alloc(sizeof(int)));
+    NVD_TRY_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    k_check_sym<TW><<<nvd::grid_for(g->n, 32, g->num_sms), 256, 0, s>>>(
+        g->n, g->rowptr.as<int64_t>(), g->colidx.as<int32_t>(), g->w.as<TW>(), bad.as<int>());
+    NVD_TRY_CUDA(cudaGetLastError());
+    NVD_TRY_CUDA(cudaMemcpyAsync(bad_h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    return NVD_OK;
+}
+
+int run_degree(nvd_graph_s *g, cudaStream_t s) {
+    const int64_t n = g->n;
+    NVD_TRY(g->deg64.alloc(n * 8));
+    NVD_TRY(g->dinv64.alloc(n * 8));
+    NVD_TRY(g->deg32.alloc(n * 4));
+    NVD_TRY(g->dinv32.alloc(n * 4));
+    const int grid = nvd::grid_for(n, 32, g->num_sms);
+    if (g->wdtype == NVD_F64)
+        k_degree<double><<<grid, 256, 0, s>>>(n, g->rowptr.as<int64_t>(), g->w.as<double>(),
+                                              g->deg64.as<double>(), g->dinv64.as<double>(),
+                                              g->deg32.as<float>(), g->dinv32.as<float>());
+    else
+        k_degree<float><<<grid, 256, 0, s>>>(n, g->rowptr.as<int64_t>(), g->w.as<float>(),
+                                             g->deg64.as<double>(), g->dinv64.as<double>(),
+                                             g->deg32.as<float>(), g->dinv32.as<float>());
+    NVD_TRY_CUDA(cudaGetLastError());
+    return NVD_OK;
+}
+
+int run_components(nvd_graph_s *g, std::vector<int32_t> &root, cudaStream_t s) {
+    const int64_t n = g->n;
+    nvd::DevBuf parent, changed;
+    NVD_TRY(parent.alloc(n * 4));
+    NVD_TRY(changed.alloc(sizeof(int)));
+    std::vector<int32_t> iota(n);
+    std::iota(iota.begin(), iota.end(), 0);
+    NVD_TRY_CUDA(cudaMemcpyAsync(parent.p, iota.data(), n * 4, cudaMemcpyHostToDevice, s));
+    int h_changed = 1;
+    const int grid = nvd::grid_for(n, 32, g->num_sms);
+    int rounds = 0;
+    for (; h_changed && rounds < 4096; ++rounds) {
+        NVD_TRY_CUDA(cudaMemsetAsync(changed.p, 0, sizeof(int), s));
+        k_cc_hook<<<grid, 256, 0, s>>>(n, g->rowptr.as<int64_t>(), g->colidx.as<int32_t>(),
+                                       parent.as<int32_t>(), changed.as<int>());
+        k_cc_compress<<<nvd::grid_for(n, 1, g->num_sms), 256, 0, s>>>(n, parent.as<int32_t>());
+        NVD_TRY_CUDA(cudaGetLastError());
+        NVD_TRY_CUDA(cudaMemcpyAsync(&h_changed, changed.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    if (h_changed) {
+        set_error("connected components did not converge in %d rounds", rounds);
+        return NVD_ERR_CUDA;
+    }
+    root.resize(n);
+    NVD_TRY_CUDA(cudaMemcpyAsync(root.data(), parent.p, n * 4, cudaMemcpyDeviceToHost, s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    return NVD_OK;
+}
+
+}  // namespace
+
+int target_blocks(const nvd_graph_s *g) { return 2 * g->num_sms * 8; }
+
+// ------------------------------------------------------------------ plans
+
+int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
+    const int key = KT * 256 + szv * 16 + sza;
+    auto it = g->plans.find(key);
+    if (it != g->plans.end()) {
+        *out = it->second.get();
+        return NVD_OK;
+    }
+    std::unique_ptr<Plan> pl(new Plan());
+    pl->KT = KT;
+    pl->szv = szv;
+    pl->sza = sza;
+    const int RB = sp_rows_budget(KT, sza);
+    const int64_t NB = sp_nnz_budget(KT, szv);
+    const std::vector<int64_t> &rp = g->h_rowptr;
+    const int nseg = g->nseg;
+    std::vector<SpItem> items;
+    std::vector<int32_t> seg_item_off(nseg + 1, 0), seg_heavy_off(nseg + 1, 0);
+    int32_t nheavy = 0, nchunks = 0;
+    for (int s = 0; s < nseg; ++s) {
+        seg_item_off[s] = (int32_t)items.size();
+        seg_heavy_off[s] = nheavy;
+        int64_t r = g->h_seg_begin[s];
+        const int64_t re = g->h_seg_end[s];
+        while (r < re) {
+            const int64_t d = rp[r + 1] - rp[r];
+            if (d > NB) {
+                const int32_t nch = (int32_t)((d + NB - 1) / NB);
+                for (int32_t c = 0; c < nch; ++c) {
+                    SpItem it{};
+                    it.r0 = (int32_t)r;
+                    it.r1 = (int32_t)(r + 1);
+                    it.kind = 1;
+                    it.hrow = nheavy;
+                    it.e0 = rp[r] + (int64_t)c * NB;
+                    it.e1 = std::min(rp[r] + (int64_t)(c + 1) * NB, rp[r + 1]);
+                    it.hbase = nchunks;
+                    it.hchunk = c;
+                    it.nchunk = nch;
+                    items.push_back(it);
+                }
+                ++nheavy;
+                nchunks += nch;
+                ++r;
+                continue;
+            }
+            const int64_t r0 = r;
+            int64_t cnt = 0;
+            while (r < re && r - r0 < RB) {
+                const int64_t dd = rp[r + 1] - rp[r];
+                if (dd > NB) break;
+                if (cnt + dd > NB && r > r0) break;
+                cnt += dd;
+                ++r;
+            }
+            SpItem it{};
+            it.r0 = (int32_t)r0;
+            it.r1 = (int32_t)r;
+            it.kind = 0;
+            it.e0 = rp[r0];
+            it.e1 = rp[r];
+            items.push_back(it);
+        }
+    }
+    seg_item_off[nseg] = (int32_t)items.size();
+    seg_heavy_off[nseg] = nheavy;
+
+    // blocks: about target_blocks() per launch, split in proportion to work
+    const int T = target_blocks(g);
+    double wtot = 0.0;
+    std::vector<double> iw(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
+        iw[i] = (double)(items[i].e1 - items[i].e0) + (double)(items[i].r1 - items[i].r0);
+        wtot += iw[i];
+    }
+    std::vector<Block> sblk;
+    std::vector<int32_t> seg_sblk_off(nseg + 1, 0);
+    for (int s = 0; s < nseg; ++s) {
+        seg_sblk_off[s] = (int32_t)sblk.size();
+        const int64_t a = seg_item_off[s], b = seg_item_off[s + 1];
+        double ws = 0.0;
+        for (int64_t i = a; i < b; ++i) ws += iw[i];
+        int64_t nb = (int64_t)(T * ws / (wtot > 0 ? wtot : 1.0) + 0.5);
+        nb = std::max<int64_t>(1, std::min<int64_t>(nb, b - a));
+        const double target = ws / nb;
+        double acc = 0.0;
+        int64_t start = a;
+        int64_t made = 0;
+        for (int64_t i = a; i < b; ++i) {
+            acc += iw[i];
+            const bool last = (i == b - 1);
+            if (last || (acc >= target * (made + 1) && made < nb - 1)) {
+                sblk.push_back(Block{start, i + 1, s, 0});
+                ++made;
+                start = i + 1;
+            }
+        }
+    }
+    seg_sblk_off[nseg] = (int32_t)sblk.size();
+
+    std::vector<Block> vblk;
+    std::vector<int32_t> seg_vblk_off(nseg + 1, 0);
+    int64_t rows_tot = 0;
+    for (int s = 0; s < nseg; ++s) rows_tot += g->h_seg_end[s] - g->h_seg_begin[s];
+    for (int s = 0; s < nseg; ++s) {
+        seg_vblk_off[s] = (int32_t)vblk.size();
+        const int64_t a = g->h_seg_begin[s], b = g->h_seg_end[s], rows = b - a;
+        int64_t nb = (int64_t)((double)T * rows / (rows_tot > 0 ? rows_tot : 1) + 0.5);
+        const int64_t maxb = std::max<int64_t>(1, (rows * KT + 1023) / 1024);
+        nb = std::max<int64_t>(1, std::min<int64_t>(nb, maxb));
+        for (int64_t k = 0; k < nb; ++k)
+            vblk.push_back(Block{a + rows * k / nb, a + rows * (k + 1) / nb, s, 0});
+    }
+    seg_vblk_off[nseg] = (int32_t)vblk.size();
+
+    pl->n_items = (int64_t)items.size();
+    pl->n_sblk = (int64_t)sblk.size();
+    pl->n_heavy = nheavy;
+    pl->n_chunks = nchunks;
+    pl->n_vblk = (int64_t)vblk.size();
+    auto up = [&](DevBuf &d, const void *h, size_t bytes) -> int {
+        NVD_TRY(d.alloc(bytes));
+        if (bytes) NVD_TRY_CUDA(cudaMemcpy(d.p, h, bytes, cudaMemcpyHostToDevice));
+        return NVD_OK;
+    };
+    NVD_TRY(up(pl->items, items.data(), items.size() * sizeof(SpItem)));
+    NVD_TRY(up(pl->sblk, sblk.data(), sblk.size() * sizeof(Block)));
+    NVD_TRY(up(pl->vblk, vblk.data(), vblk.size() * sizeof(Block)));
+    NVD_TRY(up(pl->seg_sblk_off, seg_sblk_off.data(), seg_sblk_off.size() * 4));
+    NVD_TRY(up(pl->seg_heavy_off, seg_heavy_off.data(), seg_heavy_off.size() * 4));
+    NVD_TRY(up(pl->seg_vblk_off, seg_vblk_off.data(), seg_vblk_off.size() * 4));
+    NVD_TRY(pl->hcount.alloc((size_t)std::max<int32_t>(nheavy, 1) * 4));
+    NVD_TRY_CUDA(cudaMemset(pl->hcount.p, 0, pl->hcount.bytes));
+    *out = pl.get();
+    g->plans[key] = std::move(pl);
+    return NVD_OK;
+}
+
+int get_w32(nvd_graph_s *g, const float **out, cudaStream_t s) {
+    if (g->wdtype == NVD_F32) {
+        *out = g->w.as<float>();
+        return NVD_OK;
+    }
+    if (!g->w32.p) {
+        const int64_t npad = ((g->nnz + 3) / 4) * 4 + 4;
+        NVD_TRY(g->w32.alloc(npad * 4));
+        NVD_TRY_CUDA(cudaMemsetAsync(g->w32.p, 0, npad * 4, s));
+        k_round_w32<<<grid_for(g->nnz, 1, g->num_sms), 256, 0, s>>>(g->w.as<double>(),
+                                                                    g->w32.as<float>(), g->nnz);
+        NVD_TRY_CUDA(cudaGetLastError());
+    }
+    *out = g->w32.as<float>();
+    return NVD_OK;
+}
+
+void set_sp_plan(Ctx *c, const Plan *pl) {
+    c->items = pl->items.as<SpItem>();
+    c->sblk = pl->sblk.as<Block>();
+    c->n_sblk = pl->n_sblk;
+    c->seg_sblk_off = pl->seg_sblk_off.as<int32_t>();
+    c->seg_heavy_off = pl->seg_heavy_off.as<int32_t>();
+    c->hcount = pl->hcount.as<int32_t>();
+}
+
+void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c) {
+    c->n = g->n;
+    c->rowptr = g->rowptr.as<int64_t>();
+    c->colidx = g->colidx.as<int32_t>();
+    c->w = g->w.p;
+    c->deg64 = g->deg64.as<double>();
+    c->dinv64 = g->dinv64.as<double>();
+    c->deg32 = g->deg32.as<float>();
+    c->dinv32 = g->dinv32.as<float>();
+    c->nseg = g->nseg;
+    c->seg_begin = g->seg_begin.as<int64_t>();
+    c->seg_end = g->seg_end.as<int64_t>();
+    c->seg_owner = g->seg_owner.as<int32_t>();
+    c->perm = g->perm.as<int32_t>();
+    if (pl) {
+        set_sp_plan(c, pl);
+        c->vblk = pl->vblk.as<Block>();
+        c->n_vblk = pl->n_vblk;
+        c->seg_vblk_off = pl->seg_vblk_off.as<int32_t>();
+    }
+}
+
+}  // namespace nvd
+
+void *nvd_graph_s::wsp(const std::string &name, size_t bytes, int *st) {
+    auto &slot = ws[name];
+    if (!slot) slot.reset(new nvd::DevBuf());
+    int r = slot->ensure(bytes);
+    if (r != NVD_OK) {
+        *st = r;
+        return nullptr;
+    }
+    return slot->p;
+}
+
+int64_t nvd_graph_s::device_bytes() const {
+    int64_t b = 0;
+    for (const nvd::DevBuf *d : {&rowptr, &colidx, &w, &w32, &deg64, &dinv64, &deg32, &dinv32,
+                                 &perm, &uent, &seg_begin, &seg_end, &seg_owner})
+        b += (int64_t)d->bytes;
+    for (auto &kv : plans)
+        for (const nvd::DevBuf *d : {&kv.second->items, &kv.second->sblk, &kv.second->vblk,
+                                     &kv.second->seg_sblk_off, &kv.second->seg_heavy_off,
+                                     &kv.second->seg_vblk_off, &kv.second->hcount})
+            b += (int64_t)d->bytes;
+    for (auto &kv : ws) b += (int64_t)kv.second->bytes;
+    return b;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+using namespace nvd;
+
+static int graph_create_impl(nvd_graph_t *out, int64_t n, int64_t nnz, const int64_t *rowptr,
+                             const int32_t *colidx, const void *w, int32_t wdtype, uint32_t flags,
+                             cudaStream_t s) {
+    if (n < 1 || n > INT32_MAX - 1 || nnz < 0 || !rowptr || (nnz > 0 && !colidx) ||
+        (wdtype != NVD_F32 && wdtype != NVD_F64) ||
+        (flags & ~(NVD_GRAPH_DEVICE_PTRS | NVD_GRAPH_SKIP_SYM_CHECK))) {
+        set_error("nvd_graph_create: invalid argument (n=%lld nnz=%lld wdtype=%d flags=%u)",
+                  (long long)n, (long long)nnz, wdtype, flags);
+        return NVD_ERR_INVALID_ARG;
+    }
+    const bool dev = flags & NVD_GRAPH_DEVICE_PTRS;
+    std::unique_ptr<nvd_graph_s> g(new nvd_graph_s());
+    NVD_TRY_CUDA(cudaGetDevice(&g->device));
+    NVD_TRY_CUDA(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+    g->n = n;
+    g->nnz = nnz;
+    g->nnz_user = nnz;
+    g->wdtype = wdtype;
+    const size_t wsz = wdtype == NVD_F64 ? 8 : 4;
+
+    // rowptr: host copy (planning) and validation
+    g->h_rowptr.resize(n + 1);
+    if (dev)
+        NVD_TRY_CUDA(cudaMemcpyAsync(g->h_rowptr.data(), rowptr, (n + 1) * 8, cudaMemcpyDeviceToHost, s));
+    else
+        memcpy(g->h_rowptr.data(), rowptr, (n + 1) * 8);
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    if (g->h_rowptr[0] != 0 || g->h_rowptr[n] != nnz) {
+        set_error("nvd_graph_create: rowptr[0] must be 0 and rowptr[n] must equal nnz");
+        return NVD_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (g->h_rowptr[i + 1] < g->h_rowptr[i]) {
+            set_error("nvd_graph_create: rowptr decreases at row %lld", (long long)i);
+            return NVD_ERR_INVALID_ARG;
+        }
+
+    // device copies (padded to a multiple of 4 entries for 16-byte loads)
+    const int64_t npad = ((nnz + 3) / 4) * 4 + 4;
+    NVD_TRY(g->rowptr.alloc((n + 1) * 8));
+    NVD_TRY_CUDA(cudaMemcpyAsync(g->rowptr.p, g->h_rowptr.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s));
+    NVD_TRY(g->colidx.alloc(npad * 4));
+    NVD_TRY_CUDA(cudaMemsetAsync(g->colidx.p, 0, npad * 4, s));
+    NVD_TRY(g->w.alloc(npad * wsz));
+    NVD_TRY_CUDA(cudaMemsetAsync(g->w.p, 0, npad * wsz, s));
+    if (nnz > 0) {
+        const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        NVD_TRY_CUDA(cudaMemcpyAsync(g->colidx.p, colidx, nnz * 4, kind, s));
+        if (w) {
+            NVD_TRY_CUDA(cudaMemcpyAsync(g->w.p, w, nnz * wsz, kind, s));
+        } else if (wdtype == NVD_F64) {
+            k_fill<double><<<grid_for(nnz, 1, g->num_sms), 256, 0, s>>>(g->w.as<double>(), nnz, 1.0);
+        } else {
+            k_fill<float><<<grid_for(nnz, 1, g->num_sms), 256, 0, s>>>(g->w.as<float>(), nnz, 1.0f);
+        }
+        NVD_TRY_CUDA(cudaGetLastError());
+    }
+
+    // structure and weight checks
+    int fl[4] = {0, 0, 0, 0};
+    if (wdtype == NVD_F64)
+        NVD_TRY(run_checks<double>(g.get(), w != nullptr, fl, s));
+    else
+        NVD_TRY(run_checks<float>(g.get(), w != nullptr, fl, s));
+    if (fl[0]) {
+        set_error("nvd_graph_create: column index out of range");
+        return NVD_ERR_INVALID_ARG;
+    }
+    if (fl[3]) {
+        set_error("nvd_graph_create: weights must be finite and > 0");
+        return NVD_ERR_BAD_WEIGHT;
+    }
+    std::vector<int64_t> uent;  // user entry -> internal entry, empty = identity
+    if (fl[1] || fl[2]) {
+        std::vector<int32_t> col;
+        std::vector<double> wv;
+        NVD_TRY(download_csr(g.get(), col, wv, s));
+        HostCSR hc;
+        clean_csr(n, g->h_rowptr, col, wv, hc);
+        g->nnz = (int64_t)hc.col.size();
+        g->h_rowptr = hc.rowptr;
+        uent = hc.uent;
+        NVD_TRY_CUDA(cudaMemcpyAsync(g->rowptr.p, g->h_rowptr.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s));
+        NVD_TRY(upload_padded(g->colidx, hc.col.data(), g->nnz, s));
+        NVD_TRY(upload_weights(g.get(), hc.w, s));
+        NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!(flags & NVD_GRAPH_SKIP_SYM_CHECK)) {
+        int bad = 0;
+        if (wdtype == NVD_F64)
+            NVD_TRY(run_sym<double>(g.get(), &bad, s));
+        else
+            NVD_TRY(run_sym<float>(g.get(), &bad, s));
+        if (bad) {
+            set_error("nvd_graph_create: the CSR is not symmetric (structure or weights)");
+            return NVD_ERR_NOT_SYMMETRIC;
+        }
+    }
+
+    // connected components; relabel if some component is not a contiguous range
+    std::vector<int32_t> root;
+    NVD_TRY(run_components(g.get(), root, s));
+    std::vector<int64_t> cnt(n, 0), mx(n, -1);
+    for (int64_t i = 0; i < n; ++i) {
+        cnt[root[i]]++;
+        mx[root[i]] = std::max<int64_t>(mx[root[i]], i);
+    }
+    bool contiguous = true;
+    int32_t ncomp = 0;
+    for (int64_t r = 0; r < n; ++r)
+        if (cnt[r] > 0) {
+            ++ncomp;
+            if (mx[r] - r + 1 != cnt[r]) contiguous = false;
+        }
+    g->ncomp = ncomp;
+    std::vector<int32_t> perm;  // internal -> user
+    if (!contiguous) {
+        // stable counting sort of nodes by their component's smallest node
+        std::vector<int64_t> start(n + 1, 0);
+        for (int64_t r = 0; r < n; ++r) start[r + 1] = start[r] + cnt[r];
+        perm.resize(n);
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        for (int64_t i = 0; i < n; ++i) perm[fill[root[i]]++] = (int32_t)i;
+        std::vector<int32_t> iperm(n);
+        for (int64_t i = 0; i < n; ++i) iperm[perm[i]] = (int32_t)i;
+        std::vector<int32_t> col;
+        std::vector<double> wv;
+        NVD_TRY(download_csr(g.get(), col, wv, s));
+        std::vector<int64_t> rp2(n + 1, 0);
+        for (int64_t i = 0; i < n; ++i)
+            rp2[i + 1] = rp2[i] + (g->h_rowptr[perm[i] + 1] - g->h_rowptr[perm[i]]);
+        std::vector<int32_t> col2(g->nnz);
+        std::vector<double> w2(g->nnz);
+        std::vector<int64_t> newpos(g->nnz);
+        std::vector<std::pair<int32_t, int64_t>> tmp;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t u = perm[i];
+            tmp.clear();
+            for (int64_t e = g->h_rowptr[u]; e < g->h_rowptr[u + 1]; ++e) tmp.push_back({iperm[col[e]], e});
+            std::sort(tmp.begin(), tmp.end());
+            for (size_t t = 0; t < tmp.size(); ++t) {
+                const int64_t pos = rp2[i] + (int64_t)t;
+                col2[pos] = tmp[t].first;
+                w2[pos] = wv[tmp[t].second];
+                newpos[tmp[t].second] = pos;
+            }
+        }
+        if (uent.empty()) {
+            uent.resize(g->nnz_user);
+            for (int64_t e = 0; e < g->nnz_user; ++e) uent[e] = newpos[e];
+        } else {
+            for (int64_t e = 0; e < g->nnz_user; ++e)
+                if (uent[e] >= 0) uent[e] = newpos[uent[e]];
+        }
+        g->h_rowptr = rp2;
+        NVD_TRY_CUDA(cudaMemcpyAsync(g->rowptr.p, g->h_rowptr.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s));
+        NVD_TRY(upload_padded(g->colidx, col2.data(), g->nnz, s));
+        NVD_TRY(upload_weights(g.get(), w2, s));
+        NVD_TRY(g->perm.alloc(n * 4));
+        NVD_TRY_CUDA(cudaMemcpyAsync(g->perm.p, perm.data(), n * 4, cudaMemcpyHostToDevice, s));
+        // roots in the new order
+        std::vector<int32_t> root2(n);
+        for (int64_t i = 0; i < n; ++i) root2[i] = iperm[root[perm[i]]];
+        // in the new order every component is one run of equal labels
+        root.swap(root2);
+        NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!uent.empty()) {
+        NVD_TRY(g->uent.alloc(uent.size() * 8));
+        NVD_TRY_CUDA(cudaMemcpyAsync(g->uent.p, uent.data(), uent.size() * 8, cudaMemcpyHostToDevice, s));
+    }
+    // segments: contiguous runs of equal component with >= 2 nodes
+    {
+        int64_t i = 0;
+        while (i < n) {
+            int64_t j = i + 1;
+            while (j < n && root[j] == root[i]) ++j;
+            if (j - i >= 2) {
+                g->h_seg_begin.push_back(i);
+                g->h_seg_end.push_back(j);
+            } else {
+                g->n_singleton++;
+            }
+            i = j;
+        }
+    }
+    g->nseg = (int32_t)g->h_seg_begin.size();
+    const size_t ns = std::max<size_t>(g->h_seg_begin.size(), 1);
+    NVD_TRY(g->seg_begin.alloc(ns * 8));
+    NVD_TRY(g->seg_end.alloc(ns * 8));
+    NVD_TRY(g->seg_owner.alloc(ns * 4));
+    NVD_TRY_CUDA(cudaMemsetAsync(g->seg_owner.p, 0, ns * 4, s));
+    if (g->nseg) {
+        NVD_TRY_CUDA(cudaMemcpyAsync(g->seg_begin.p, g->h_seg_begin.data(), g->nseg * 8, cudaMemcpyHostToDevice, s));
+        NVD_TRY_CUDA(cudaMemcpyAsync(g->seg_end.p, g->h_seg_end.data(), g->nseg * 8, cudaMemcpyHostToDevice, s));
+    }
+    NVD_TRY(run_degree(g.get(), s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    *out = g.release();
+    return NVD_OK;
+}
+
+extern "C" int nvd_graph_create(nvd_graph_t *out, int64_t n, int64_t nnz, const int64_t *rowptr,
+                                const int32_t *colidx, const void *w, int32_t wdtype, uint32_t flags,
+                                nvd_stream_t stream) {
+    clear_error();
+    if (!out) {
+        set_error("nvd_graph_create: out is NULL");
+        return NVD_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    try {
+        return graph_create_impl(out, n, nnz, rowptr, colidx, w, wdtype, flags, (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        set_error("nvd_graph_create: host allocation failed");
+        return NVD_ERR_OOM;
+    } catch (...) {
+        set_error("nvd_graph_create: unexpected host exception");
+        return NVD_ERR_CUDA;
+    }
+}
+
+extern "C" int nvd_graph_destroy(nvd_graph_t g) {
+    clear_error();
+    if (!g) return NVD_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(g->device);
+    delete g;
+    cudaSetDevice(dev);
+    return NVD_OK;
+}
+
+extern "C" int nvd_graph_info(nvd_graph_t g, int64_t *n, int64_t *nnz, int32_t *ncomp,
+                              int64_t *device_bytes) {
+    clear_error();
+    if (!g) {
+        set_error("nvd_graph_info: NULL handle");
+        return NVD_ERR_INVALID_ARG;
+    }
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (ncomp) *ncomp = g->ncomp;
+    if (device_bytes) *device_bytes = g->device_bytes();
+    return NVD_OK;
+}

@@ -1,0 +1,105 @@
+// Internal graph handle, device buffers and work plans (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "nvd.h"
+
+namespace nvd {
+
+// Thread-local error detail for nvd_last_error().
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define NVD_TRY_CUDA(call)                                                                 \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ::nvd::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                             __FILE__, __LINE__);                                          \
+            return e_ == cudaErrorMemoryAllocation ? NVD_ERR_OOM : NVD_ERR_CUDA;           \
+        }                                                                                  \
+    } while (0)
+
+#define NVD_TRY(call)                       \
+    do {                                    \
+        int s_ = (call);                    \
+        if (s_ != NVD_OK) return s_;        \
+    } while (0)
+
+// Owned device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // (Re)allocate to exactly `b` bytes (contents undefined).
+    int alloc(size_t b);
+    // Grow to at least `b` bytes (contents undefined after growth).
+    int ensure(size_t b) { return b <= bytes && p ? NVD_OK : alloc(b); }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Work decomposition for one (KT, vector size, accumulator size) configuration.
+struct Plan {
+    int KT = 0, szv = 0, sza = 0;
+    int64_t n_items = 0, n_sblk = 0, n_heavy = 0, n_chunks = 0, n_vblk = 0;
+    DevBuf items, sblk, vblk, seg_sblk_off, seg_heavy_off, seg_vblk_off, hcount;
+    int64_t part_slots() const {
+        int64_t a = n_sblk + n_heavy;
+        return a > n_vblk ? a : n_vblk;
+    }
+};
+
+}  // namespace nvd
+
+struct nvd_graph_s {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0, nnz = 0;      // after cleaning (self-loops dropped, repeats merged)
+    int64_t nnz_user = 0;        // entries given to nvd_graph_create
+    int32_t wdtype = NVD_F64;
+    // internal CSR (component-contiguous node order), arrays padded to 4 entries
+    nvd::DevBuf rowptr, colidx, w, w32;   // w in wdtype; w32 = FP32 copy when wdtype is F64 (lazy)
+    nvd::DevBuf deg64, dinv64, deg32, dinv32;
+    nvd::DevBuf perm;            // int32 internal -> user node; empty when identity
+    nvd::DevBuf uent;            // int64 user entry -> internal entry (-1 dropped); empty when identity
+    int32_t ncomp = 0, nseg = 0;
+    int64_t n_singleton = 0;
+    std::vector<int64_t> h_rowptr, h_seg_begin, h_seg_end;
+    nvd::DevBuf seg_begin, seg_end, seg_owner;
+    std::map<int, std::unique_ptr<nvd::Plan>> plans;
+    std::map<std::string, std::unique_ptr<nvd::DevBuf>> ws;  // named lazily-grown workspace
+
+    void *wsp(const std::string &name, size_t bytes, int *st);
+    int64_t device_bytes() const;
+};
+
+namespace nvd {
+
+// Work plan for (KT, szv, sza), built on first use and cached in the handle.
+int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out);
+// FP32 weights for the FP32 paths (the FP64 weights rounded once, cached).
+int get_w32(nvd_graph_s *g, const float **out, cudaStream_t s);
+// Ctx fields that depend only on the graph and a plan.
+void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c);
+// Only the SpMV/SpMM work-decomposition fields of a Ctx.
+void set_sp_plan(Ctx *c, const Plan *pl);
+
+// Blocks per kernel launch the planner aims for (about two waves of 8 CTAs per SM).
+int target_blocks(const nvd_graph_s *g);
+
+}  // namespace nvd

@@ -1,0 +1,897 @@
+// Device code of the GE-distance solver (internal; sm_103a).
+//
+// The method (Section 3.1, GE equation; Section 3.2 Laplacian solvers): solve
+// L z = P(x - y) by Jacobi-preconditioned conjugate gradient and take
+// (x - y)^T z.  Every pass over the data is one of the "block" routines below;
+// the host-driven solver launches them as separate kernels, the persistent
+// solver calls them inside one cooperative kernel separated by grid barriers.
+//
+// Work layout: block vectors are [n][KT] row-major (KT right-hand sides side by
+// side, one 16-byte-aligned row per node), the graph is CSR in internal node
+// order where every connected component ("segment") is a contiguous node
+// range.  Each CTA block covers a contiguous run of one segment and owns one
+// partial-sum slot per inner product; the last block of a segment to finish
+// (atomic arrival counter) sums the segment's slots in slot order and updates
+// the per-(segment, column) CG scalars -- so every reduction is deterministic
+// and needs no extra launch.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "common.h"
+
+namespace nvd {
+namespace dev {
+
+#define NVD_FULLMASK 0xffffffffu
+
+// ------------------------------------------------------------------ loads/stores
+
+// Read-only data path: data not written by any CTA during the kernel.
+struct LdRO {
+    template <class T>
+    static __device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
+};
+// Coherent path (L2): data written by other CTAs earlier in the same kernel
+// (persistent kernel; L1 is not coherent across SMs).
+struct LdCoh {
+    template <class T>
+    static __device__ __forceinline__ T ld(const T *p) { return __ldcg(p); }
+};
+
+template <class T, int V> struct VecOf;
+template <> struct VecOf<float, 1> { typedef float t; };
+template <> struct VecOf<float, 2> { typedef float2 t; };
+template <> struct VecOf<float, 4> { typedef float4 t; };
+template <> struct VecOf<double, 1> { typedef double t; };
+template <> struct VecOf<double, 2> { typedef double2 t; };
+
+__device__ __forceinline__ void unpack(float a, float (&o)[1]) { o[0] = a; }
+__device__ __forceinline__ void unpack(float2 a, float (&o)[2]) { o[0] = a.x; o[1] = a.y; }
+__device__ __forceinline__ void unpack(float4 a, float (&o)[4]) {
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void unpack(double a, double (&o)[1]) { o[0] = a; }
+__device__ __forceinline__ void unpack(double2 a, double (&o)[2]) { o[0] = a.x; o[1] = a.y; }
+__device__ __forceinline__ float pack(const float (&o)[1]) { return o[0]; }
+__device__ __forceinline__ float2 pack(const float (&o)[2]) { return make_float2(o[0], o[1]); }
+__device__ __forceinline__ float4 pack(const float (&o)[4]) {
+    return make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ double pack(const double (&o)[1]) { return o[0]; }
+__device__ __forceinline__ double2 pack(const double (&o)[2]) { return make_double2(o[0], o[1]); }
+
+// Plain (default-cached) loads for data this kernel may also write.
+struct LdPlain {
+    template <class T>
+    static __device__ __forceinline__ T ld(const T *p) { return *p; }
+};
+
+// V consecutive elements, naturally aligned; wider than 16 bytes = several 16-byte loads.
+template <class LD, class T, int V>
+__device__ __forceinline__ void ldv(const T *p, T (&o)[V]) {
+    if constexpr (V * sizeof(T) <= 16) {
+        unpack(LD::ld(reinterpret_cast<const typename VecOf<T, V>::t *>(p)), o);
+    } else {
+        constexpr int H = V / 2;
+        T a[H], b[H];
+        ldv<LD, T, H>(p, a);
+        ldv<LD, T, H>(p + H, b);
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            o[i] = a[i];
+            o[H + i] = b[i];
+        }
+    }
+}
+template <class T, int V>
+__device__ __forceinline__ void stv(T *p, const T (&o)[V]) {
+    if constexpr (V * sizeof(T) <= 16) {
+        *reinterpret_cast<typename VecOf<T, V>::t *>(p) = pack(o);
+    } else {
+        constexpr int H = V / 2;
+        T a[H], b[H];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            a[i] = o[i];
+            b[i] = o[H + i];
+        }
+        stv<T, H>(p, a);
+        stv<T, H>(p + H, b);
+    }
+}
+
+// Four consecutive CSR weights starting at a multiple of 4 (streaming, evict-first).
+__device__ __forceinline__ void ld4_stream(const float *p, float (&o)[4]) {
+    float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void ld4_stream(const double *p, double (&o)[4]) {
+    double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+// Elements per lane-vector for a [n][KT] array of T (16-byte loads when possible).
+template <class T, int KT>
+struct VecCfg {
+    static constexpr int VEC = (KT * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : KT;
+    static constexpr int CG = KT / VEC;  // lane-vectors per row
+};
+
+__device__ __forceinline__ const Owner &owner_of(const Ctx &c, int seg) {
+    return c.owners ? c.owners[c.seg_owner[seg]] : c.own0;
+}
+
+template <class T> __device__ __forceinline__ const T *dinv_of(const Ctx &c);
+template <> __device__ __forceinline__ const float *dinv_of<float>(const Ctx &c) { return c.dinv32; }
+template <> __device__ __forceinline__ const double *dinv_of<double>(const Ctx &c) { return c.dinv64; }
+template <class T> __device__ __forceinline__ const T *deg_of(const Ctx &c);
+template <> __device__ __forceinline__ const float *deg_of<float>(const Ctx &c) { return c.deg32; }
+template <> __device__ __forceinline__ const double *deg_of<double>(const Ctx &c) { return c.deg64; }
+
+// ------------------------------------------------------------------ reductions
+
+// Block-wide per-column sums.  Thread t holds acc[d][v] for column
+// (t % CG) * VEC + v.  On return tot[d * KT + j] (shared) holds the block total,
+// summed in a fixed order (warp butterfly, then warps 0..7).
+template <int ND, int KT, int VEC>
+__device__ __forceinline__ void block_reduce_cols(double (&acc)[ND > 0 ? ND : 1][VEC], double *red,
+                                                  double *tot) {
+    if constexpr (ND > 0) {
+        constexpr int CG = KT / VEC;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int off = CG; off < 32; off <<= 1)
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v)
+                    acc[d][v] += __shfl_xor_sync(NVD_FULLMASK, acc[d][v], off);
+        if (lane < CG) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) red[(warp * ND + d) * KT + lane * VEC + v] = acc[d][v];
+        }
+        __syncthreads();
+        if (threadIdx.x < ND * KT) {
+            const int d = threadIdx.x / KT, j = threadIdx.x % KT;
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NWARP; ++w) s += red[(w * ND + d) * KT + j];
+            tot[threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int pow2floor(int x) { return x >= 256 ? 256 : x >= 128 ? 128 : x >= 64 ? 64 : x >= 32 ? 32
+                                       : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1; }
+
+// Publish this block's partials into `slot`, count the arrival on the segment
+// and, in the last block of the segment, sum the segment's slots -- blocks
+// [s0, s0 + cnt) then split-row slots [h0, h0 + hcnt) -- in slot order and call
+// fin(c, seg, j, sums) for each column j (one thread per column).
+// `red` needs NT doubles of shared scratch.
+template <int ND, int KT, class Fin>
+__device__ void seg_arrive(const Ctx &c, const Fin &fin, int seg, int64_t slot, const double *tot,
+                           int64_t s0, int32_t cnt, int64_t h0, int32_t hcnt, double *red) {
+    static_assert(ND > 0, "arrival needs a reduction");
+    __shared__ int s_last;
+    if (threadIdx.x < ND * KT) {
+        const int d = threadIdx.x / KT, j = threadIdx.x % KT;
+        c.part[((int64_t)d * c.part_stride + slot) * KT + j] = tot[threadIdx.x];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&c.counter[seg], 1u) == (unsigned)(cnt - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    constexpr int P = ND * KT;
+    constexpr int TPP = pow2floor(NT / P);
+    const int pair = threadIdx.x / TPP, sub = threadIdx.x % TPP;
+    double s = 0.0;
+    if (pair < P) {
+        const int d = pair / KT, j = pair % KT;
+        const double *base = c.part + (int64_t)d * c.part_stride * KT + j;
+        for (int i = sub; i < cnt; i += TPP) s += __ldcg(base + (s0 + i) * KT);
+        for (int i = sub; i < hcnt; i += TPP) s += __ldcg(base + (h0 + i) * KT);
+    }
+    constexpr int WOFF = TPP < 32 ? TPP : 32;
+#pragma unroll
+    for (int off = WOFF / 2; off > 0; off >>= 1) s += __shfl_xor_sync(NVD_FULLMASK, s, off);
+    double *sums = red;          // [P]
+    double *wsum = red + 128;    // [NWARP] (only when TPP > 32)
+    if constexpr (TPP > 32) {
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (sub == 0 && pair < P) {
+            double t = 0.0;
+            for (int w = 0; w < TPP / 32; ++w) t += wsum[pair * (TPP / 32) + w];
+            sums[pair] = t;
+        }
+    } else {
+        if (sub == 0 && pair < P) sums[pair] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < KT) {
+        double v[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) v[d] = sums[d * KT + threadIdx.x];
+        fin(c, seg, threadIdx.x, v);
+    }
+    if (threadIdx.x == 0) atomicExch(&c.counter[seg], 0u);
+    __syncthreads();
+}
+
+// Is any column of the segment still iterating?  (Constant during one phase:
+// only the segment's own finalizer changes it, after all its blocks arrived.)
+template <int KT>
+__device__ __forceinline__ bool seg_live(const Ctx &c, int seg) {
+    int a = 0;
+#pragma unroll
+    for (int j = 0; j < KT; ++j) a |= __ldcg(c.active + (int64_t)seg * KT + j);
+    return a != 0;
+}
+
+// ------------------------------------------------------------------ finalizers
+// Run by one thread per column in the last block of a segment.
+
+struct FinNone {
+    __device__ void operator()(const Ctx &, int, int, const double *) const {}
+};
+
+// Per-segment mean of the right-hand side (projection P, Section 3.1: L^+
+// annihilates constants on every component).
+struct FinMean {
+    __device__ void operator()(const Ctx &c, int seg, int j, const double *s) const {
+        const double sz = (double)(c.seg_end[seg] - c.seg_begin[seg]);
+        c.mean[(int64_t)seg * KT + j] = s[0] / sz;
+    }
+    int KT;
+};
+
+// PCG start: rho = r^T D^-1 r, rr0 = |r|^2; a column iterates if it is a real
+// pair of this owner and its right-hand side is non-zero.
+struct FinInit {
+    int KT;
+    __device__ void operator()(const Ctx &c, int seg, int j, const double *s) const {
+        const int64_t i = (int64_t)seg * KT + j;
+        const bool valid = j < owner_of(c, seg).kc;
+        const double rho = s[0], rr = s[1];
+        c.rho[i] = rho;
+        c.rr[i] = rr;
+        c.rr0[i] = rr;
+        c.alpha[i] = 0.0;
+        c.beta[i] = 0.0;
+        c.iters[i] = 0;
+        const bool finite = isfinite(rr) && isfinite(rho);
+        c.status[i] = (valid && !finite) ? NVD_ERR_NUMERIC : NVD_OK;
+        const bool act = valid && finite && rr > 0.0 && rho > 0.0;
+        c.active[i] = act ? 1 : 0;
+        if (act) atomicAdd(c.n_active, 1);
+    }
+};
+
+// After q = L p: alpha = rho / p^T q.  Loss of positivity is recorded in status
+// and acted on by FinUpdate (so n_active only changes in FinInit/FinUpdate).
+struct FinAlpha {
+    int KT;
+    __device__ void operator()(const Ctx &c, int seg, int j, const double *s) const {
+        const int64_t i = (int64_t)seg * KT + j;
+        if (!c.active[i]) {
+            c.alpha[i] = 0.0;
+            return;
+        }
+        const double pq = s[0];
+        if (pq > 0.0 && isfinite(pq)) {
+            c.alpha[i] = c.rho[i] / pq;
+        } else {
+            c.alpha[i] = 0.0;
+            c.status[i] = NVD_ERR_NUMERIC;
+        }
+    }
+};
+
+// After x += alpha p, r -= alpha q: convergence test on |r|^2 <= rtol^2 |r0|^2,
+// beta = rho_new / rho.
+struct FinBeta {
+    int KT;
+    __device__ void operator()(const Ctx &c, int seg, int j, const double *s) const {
+        const int64_t i = (int64_t)seg * KT + j;
+        if (!c.active[i]) return;
+        const int it = c.iters[i] + 1;
+        c.iters[i] = it;
+        const double rho_new = s[0], rr = s[1];
+        c.rr[i] = rr;
+        int st = -1;
+        if (c.status[i] == NVD_ERR_NUMERIC || !isfinite(rr) || !isfinite(rho_new))
+            st = NVD_ERR_NUMERIC;
+        else if (rr <= c.rtol2 * c.rr0[i])
+            st = NVD_OK;
+        else if (it >= c.max_iter)
+            st = NVD_ERR_NOT_CONVERGED;
+        if (st >= 0) {
+            c.status[i] = st;
+            c.active[i] = 0;
+            c.beta[i] = 0.0;
+            atomicSub(c.n_active, 1);
+        } else {
+            c.beta[i] = rho_new / c.rho[i];
+            c.rho[i] = rho_new;
+        }
+    }
+};
+
+// End of a solve: mean of x per segment, d^2 = delta^T x (Section 3.1; with x
+// projected afterwards, delta^T P x = delta^T x because P delta = delta).
+struct FinFinal {
+    int KT;
+    bool set_d2;  // false after refinement: d^2 is the variational value of FinResid
+    __device__ void operator()(const Ctx &c, int seg, int j, const double *s) const {
+        const int64_t i = (int64_t)seg * KT + j;
+        const double sz = (double)(c.seg_end[seg] - c.seg_begin[seg]);
+        c.meanx[i] = s[0] / sz;
+        if (set_d2) c.d2[i] = s[1];
+    }
+};
+
+// FP64 residual of iterative refinement, r = delta - L z:
+//   d^2 (variational) = 2 delta^T z - z^T L z = delta^T z + z^T r,
+// error -|z* - z|_L^2 (quadratic in the error of z); mean(r) for the next projection.
+struct FinResid {
+    int KT;
+    __device__ void operator()(const Ctx &c, int seg, int j, const double *s) const {
+        const int64_t i = (int64_t)seg * KT + j;
+        const double sz = (double)(c.seg_end[seg] - c.seg_begin[seg]);
+        c.dz[i] = s[0];
+        c.zr[i] = s[1];
+        c.rr[i] = s[2];
+        c.d2[i] = s[0] + s[1];
+        c.mean[i] = s[3] / sz;
+    }
+};
+
+// ------------------------------------------------------------------ SpMV / SpMM epilogues
+// elem(): row i, columns col0..col0+VEC-1; own = src[i][cols], acc = sum_j w_ij src[j][cols].
+
+// q = L p = D p - W p, and p^T q for alpha.
+struct EpiLap {
+    static constexpr int ND = 1;
+    template <class TV, class TA, int VEC>
+    __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
+                                         const TA (&acc)[VEC], TA degi, TV *dst,
+                                         double (&dot)[1][VEC]) const {
+        TV y[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            y[v] = (TV)(degi * (TA)own[v] - acc[v]);
+            dot[0][v] += (double)own[v] * (double)y[v];
+        }
+        stv(dst + i * KT + col0, y);
+    }
+    FinAlpha fin;
+};
+
+// y = L x only (operator application, no reduction).
+struct EpiApply {
+    static constexpr int ND = 0;
+    template <class TV, class TA, int VEC>
+    __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
+                                         const TA (&acc)[VEC], TA degi, TV *dst,
+                                         double (&)[1][VEC]) const {
+        TV y[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) y[v] = (TV)(degi * (TA)own[v] - acc[v]);
+        stv(dst + i * KT + col0, y);
+    }
+    FinNone fin;
+};
+
+// FP64 refinement residual r = delta - L z with delta^T z, z^T r, r^T r, sum r.
+struct EpiResid {
+    static constexpr int ND = 4;
+    const double *delta;
+    template <class TV, class TA, int VEC>
+    __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
+                                         const TA (&acc)[VEC], TA degi, TV *dst,
+                                         double (&dot)[4][VEC]) const {
+        double dl[VEC];
+        ldv<LdRO, double, VEC>(delta + i * KT + col0, dl);
+        TV y[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const double lz = (double)degi * (double)own[v] - (double)acc[v];
+            const double rv = dl[v] - lz;
+            y[v] = (TV)rv;
+            dot[0][v] += dl[v] * (double)own[v];
+            dot[1][v] += (double)own[v] * rv;
+            dot[2][v] += rv * rv;
+            dot[3][v] += rv;
+        }
+        stv(dst + i * KT + col0, y);
+    }
+    FinResid fin;
+};
+
+// ------------------------------------------------------------------ SpMV / SpMM block
+
+// Work budgets per sub-item (also used by the host planner, see plan_params()).
+template <class TV, class TA, int KT>
+struct SpCfg {
+    static constexpr int VEC = VecCfg<TV, KT>::VEC;
+    static constexpr int LPR = KT / VEC;          // lanes per gathered row vector
+    static constexpr int G = 32 / LPR;            // entries in flight per warp
+    // rows per sub-item: s_acc holds RB x KT accumulators (<= 8 KB)
+    static constexpr int RB = sp_rows_budget(KT, (int)sizeof(TA));
+    // entries per sub-item (KT = 1: staged products; KT > 1: ~32 KB of gathers)
+    static constexpr int NB = sp_nnz_budget(KT, (int)sizeof(TV));
+    static constexpr int ND_MAX = 4;
+    static constexpr int RED = red_doubles(KT);
+    static constexpr int SMEM = RB * KT * (int)sizeof(TA)            // s_acc
+                                + (KT == 1 ? NB * (int)sizeof(TA) : 0)  // s_prod
+                                + RED * 8                             // red
+                                + ND_MAX * KT * 8;                    // tot
+};
+
+// Phase B of a sub-item: rows [r0, r1) with accumulated neighbour sums in s_acc.
+template <class LD, class TV, class TA, int KT, class Epi>
+__device__ __forceinline__ void spmm_epilogue(const Ctx &c, const Epi &epi, const TV *src, TV *dst,
+                                              int64_t r0, int64_t r1, const TA *s_acc,
+                                              double (&dot)[Epi::ND > 0 ? Epi::ND : 1][SpCfg<TV, TA, KT>::VEC]) {
+    constexpr int VEC = SpCfg<TV, TA, KT>::VEC, CG = KT / VEC;
+    const TA *deg = deg_of<TA>(c);
+    const int64_t ne = (r1 - r0) * CG;
+    for (int64_t t = threadIdx.x; t < ne; t += NT) {
+        const int64_t li = t / CG;
+        const int col0 = (int)(t % CG) * VEC;
+        const int64_t i = r0 + li;
+        TV own[VEC];
+        ldv<LD, TV, VEC>(src + i * KT + col0, own);
+        TA acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = s_acc[li * KT + col0 + v];
+        epi.template elem<TV, TA, VEC>(c, i, col0, KT, own, acc, __ldg(deg + i), dst, dot);
+    }
+}
+
+// One SpMV/SpMM block b: its sub-items, then the segment arrival.
+template <class LD, class TV, class TW, class TA, int KT, class Epi>
+__device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ src, TV *__restrict__ dst,
+                           int64_t b, char *smem) {
+    typedef SpCfg<TV, TA, KT> C;
+    constexpr int VEC = C::VEC, LPR = C::LPR, G = C::G, ND = Epi::ND;
+    TA *s_acc = reinterpret_cast<TA *>(smem);
+    TA *s_prod = reinterpret_cast<TA *>(smem + C::RB * KT * sizeof(TA));
+    double *red = reinterpret_cast<double *>(smem + C::RB * KT * sizeof(TA) +
+                                             (KT == 1 ? C::NB * sizeof(TA) : 0));
+    double *tot = red + C::RED;
+    const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Block blk = c.sblk[b];
+    const int seg = blk.seg;
+
+    double dot[ND > 0 ? ND : 1][VEC];
+#pragma unroll
+    for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) dot[d][v] = 0.0;
+
+    const bool live = (ND == 0) || seg_live<KT>(c, seg);
+    if (live) {
+        for (int64_t si = blk.i0; si < blk.i1; ++si) {
+            const SpItem it = c.items[si];
+            if (it.kind == 0) {
+                // ---------------- phase A: neighbour sums of rows [r0, r1) into s_acc
+                if constexpr (KT == 1) {
+                    const int64_t e0 = __ldg(c.rowptr + it.r0), e1 = __ldg(c.rowptr + it.r1);
+                    for (int64_t eb = (e0 & ~(int64_t)3) + 4 * threadIdx.x; eb < e1; eb += 4 * NT) {
+                        const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(c.colidx + eb));
+                        TW w4[4];
+                        ld4_stream(w + eb, w4);
+                        const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+                        TA pv[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            pv[q] = (eb + q >= e0 && eb + q < e1) ? (TA)LD::ld(src + cc[q]) : (TA)0;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (eb + q >= e0 && eb + q < e1) s_prod[eb + q - e0] = (TA)w4[q] * pv[q];
+                    }
+                    __syncthreads();
+                    for (int64_t i = it.r0 + warp; i < it.r1; i += NWARP) {
+                        const int64_t a = __ldg(c.rowptr + i) - e0, z = __ldg(c.rowptr + i + 1) - e0;
+                        TA s = 0;
+                        for (int64_t k = a + lane; k < z; k += 32) s += s_prod[k];
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(NVD_FULLMASK, s, off);
+                        if (lane == 0) s_acc[i - it.r0] = s;
+                    }
+                } else {
+                    const int gi = lane / LPR, col0 = (lane % LPR) * VEC;
+                    for (int64_t i = it.r0 + warp; i < it.r1; i += NWARP) {
+                        const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
+                        TA acc[VEC];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[v] = 0;
+                        int64_t e = e0 + gi;
+                        for (; e + G < e1; e += 2 * G) {
+                            const int ca = __ldcs(c.colidx + e), cb = __ldcs(c.colidx + e + G);
+                            const TA wa = (TA)__ldcs(w + e), wb = (TA)__ldcs(w + e + G);
+                            TV pa[VEC], pb[VEC];
+                            ldv<LD, TV, VEC>(src + (int64_t)ca * KT + col0, pa);
+                            ldv<LD, TV, VEC>(src + (int64_t)cb * KT + col0, pb);
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) acc[v] += wa * (TA)pa[v];
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) acc[v] += wb * (TA)pb[v];
+                        }
+                        if (e < e1) {
+                            const int ca = __ldcs(c.colidx + e);
+                            const TA wa = (TA)__ldcs(w + e);
+                            TV pa[VEC];
+                            ldv<LD, TV, VEC>(src + (int64_t)ca * KT + col0, pa);
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) acc[v] += wa * (TA)pa[v];
+                        }
+#pragma unroll
+                        for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(NVD_FULLMASK, acc[v], off);
+                        if (gi == 0) {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) s_acc[(i - it.r0) * KT + col0 + v] = acc[v];
+                        }
+                    }
+                }
+                __syncthreads();
+                // ---------------- phase B: epilogue, coalesced over rows x columns
+                spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, src, dst, it.r0, it.r1, s_acc, dot);
+                __syncthreads();
+            } else {
+                // ---------------- chunk [e0, e1) of split row r0
+                const int64_t i = it.r0;
+                double *chunk = red;  // [KT] block total of this chunk
+                if constexpr (KT == 1) {
+                    TA s = 0;
+                    for (int64_t eb = (it.e0 & ~(int64_t)3) + 4 * threadIdx.x; eb < it.e1; eb += 4 * NT) {
+                        const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(c.colidx + eb));
+                        TW w4[4];
+                        ld4_stream(w + eb, w4);
+                        const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (eb + q >= it.e0 && eb + q < it.e1) s += (TA)w4[q] * (TA)LD::ld(src + cc[q]);
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(NVD_FULLMASK, s, off);
+                    if (lane == 0) red[NT / 2 + warp] = (double)s;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        double t = 0.0;
+                        for (int q = 0; q < NWARP; ++q) t += red[NT / 2 + q];
+                        chunk[0] = t;
+                    }
+                } else {
+                    const int gi = lane / LPR, col0 = (lane % LPR) * VEC;
+                    TA acc[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] = 0;
+                    for (int64_t e = it.e0 + warp * G + gi; e < it.e1; e += NWARP * G) {
+                        const int ca = __ldcs(c.colidx + e);
+                        const TA wa = (TA)__ldcs(w + e);
+                        TV pa[VEC];
+                        ldv<LD, TV, VEC>(src + (int64_t)ca * KT + col0, pa);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[v] += wa * (TA)pa[v];
+                    }
+#pragma unroll
+                    for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(NVD_FULLMASK, acc[v], off);
+                    if (gi == 0) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) red[KT + warp * KT + col0 + v] = (double)acc[v];
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < KT) {
+                        double t = 0.0;
+                        for (int q = 0; q < NWARP; ++q) t += red[KT + q * KT + threadIdx.x];
+                        chunk[threadIdx.x] = t;
+                    }
+                }
+                __syncthreads();
+                __shared__ int s_fin;
+                if (threadIdx.x < KT) c.hsum[(int64_t)(it.hbase + it.hchunk) * KT + threadIdx.x] = chunk[threadIdx.x];
+                __threadfence();
+                __syncthreads();
+                if (threadIdx.x == 0)
+                    s_fin = (atomicAdd(c.hcount + it.hrow, 1) == it.nchunk - 1);
+                __syncthreads();
+                if (s_fin) {
+                    __threadfence();
+                    if (threadIdx.x < KT) {
+                        double t = 0.0;
+                        for (int q = 0; q < it.nchunk; ++q)
+                            t += __ldcg(c.hsum + (int64_t)(it.hbase + q) * KT + threadIdx.x);
+                        s_acc[threadIdx.x] = (TA)t;
+                    }
+                    if (threadIdx.x == 0) atomicExch(c.hcount + it.hrow, 0);
+                    __syncthreads();
+                    double hdot[ND > 0 ? ND : 1][VEC];
+#pragma unroll
+                    for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) hdot[d][v] = 0.0;
+                    spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, src, dst, i, i + 1, s_acc, hdot);
+                    if constexpr (ND > 0) {
+                        constexpr int CG = KT / VEC;
+                        if (threadIdx.x < CG) {
+                            const int64_t hs = c.n_sblk + it.hrow;
+#pragma unroll
+                            for (int d = 0; d < ND; ++d)
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v)
+                                    c.part[((int64_t)d * c.part_stride + hs) * KT + threadIdx.x * VEC + v] = hdot[d][v];
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if constexpr (ND > 0) {
+        block_reduce_cols<ND, KT, VEC>(dot, red, tot);
+        const int64_t s0 = c.seg_sblk_off[seg];
+        const int32_t cnt = c.seg_sblk_off[seg + 1] - (int32_t)s0;
+        const int64_t h0 = c.n_sblk + c.seg_heavy_off[seg];
+        const int32_t hcnt = c.seg_heavy_off[seg + 1] - c.seg_heavy_off[seg];
+        seg_arrive<ND, KT>(c, epi.fin, seg, b, tot, s0, cnt, h0, hcnt, red);
+    }
+}
+
+// ------------------------------------------------------------------ vector passes
+
+// Generic streaming pass over rows [i0, i1) of one segment.  Op provides
+// ND, setup(c, seg, col0) and elem(c, i, col0, dot).
+template <class TV, int KT, class Op>
+__device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
+    constexpr int VEC = VecCfg<TV, KT>::VEC, CG = KT / VEC, ND = Op::ND;
+    double *red = reinterpret_cast<double *>(smem);
+    double *tot = red + red_doubles(KT);
+    const Block blk = c.vblk[b];
+    const int seg = blk.seg;
+    const int col0 = (int)(threadIdx.x % CG) * VEC;
+    double dot[ND > 0 ? ND : 1][VEC];
+#pragma unroll
+    for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) dot[d][v] = 0.0;
+    if (!Op::NEEDS_LIVE || seg_live<KT>(c, seg)) {
+        op.setup(c, seg, col0);
+        const int64_t t1 = blk.i1 * CG;
+        for (int64_t t = blk.i0 * CG + threadIdx.x; t < t1; t += NT) op.elem(c, t / CG, col0, dot);
+    }
+    if constexpr (ND > 0) {
+        block_reduce_cols<ND, KT, VEC>(dot, red, tot);
+        const int64_t s0 = c.seg_vblk_off[seg];
+        const int32_t cnt = c.seg_vblk_off[seg + 1] - (int32_t)s0;
+        seg_arrive<ND, KT>(c, op.fin, seg, b, tot, s0, cnt, 0, 0, red);
+    }
+}
+
+// delta = x - y for this tile (user layout [k][n], optional node permutation) into
+// [n][KT] FP64; per-segment sums for the projection.
+template <class TX, int KT>
+struct OpFormDelta {
+    static constexpr int ND = 1, VEC = VecCfg<double, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = false;
+    double *delta;
+    FinMean fin;
+    const TX *X, *Y;
+    int64_t base, ld;
+    int kc;
+    __device__ void setup(const Ctx &c, int seg, int) {
+        const Owner &o = owner_of(c, seg);
+        X = reinterpret_cast<const TX *>(o.x);
+        Y = reinterpret_cast<const TX *>(o.y);
+        base = o.base;
+        ld = o.ld;
+        kc = o.kc;
+    }
+    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&dot)[1][VEC]) const {
+        const int64_t u = (c.perm ? (int64_t)__ldg(c.perm + i) : i) - base;
+        double dl[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const int j = col0 + v;
+            dl[v] = j < kc ? (double)__ldg(X + (int64_t)j * ld + u) - (double)__ldg(Y + (int64_t)j * ld + u) : 0.0;
+            dot[0][v] += dl[v];
+        }
+        stv(delta + i * KT + col0, dl);
+    }
+};
+
+// PCG start from x = 0: r = P src (src minus its segment mean, optionally written
+// back), u = D^-1 r, p = u; r^T u and |r|^2.
+template <class TV, int KT, class LD = LdPlain>
+struct OpInit {
+    static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = false;
+    const double *src;
+    double *writeback;
+    TV *x, *r, *p;
+    FinInit fin;
+    double mu[VEC];
+    __device__ void setup(const Ctx &c, int seg, int col0) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) mu[v] = __ldcg(c.mean + (int64_t)seg * KT + col0 + v);
+    }
+    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&dot)[2][VEC]) const {
+        const int64_t o = i * KT + col0;
+        double s[VEC];
+        ldv<LD, double, VEC>(src + o, s);
+        const TV di = __ldg(dinv_of<TV>(c) + i);
+        TV rv[VEC], uv[VEC], zv[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            s[v] -= mu[v];
+            rv[v] = (TV)s[v];
+            uv[v] = di * rv[v];
+            zv[v] = (TV)0;
+            dot[0][v] += (double)rv[v] * (double)uv[v];
+            dot[1][v] += (double)rv[v] * (double)rv[v];
+        }
+        if (writeback) stv(writeback + o, s);
+        stv(r + o, rv);
+        stv(p + o, uv);
+        stv(x + o, zv);
+    }
+};
+
+// x += alpha p, r -= alpha q, u = D^-1 r; r^T u and |r|^2.
+template <class TV, int KT, class LD = LdPlain>
+struct OpUpdate {
+    static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = true;
+    TV *x, *r;
+    const TV *p, *q;
+    FinBeta fin;
+    TV al[VEC];
+    __device__ void setup(const Ctx &c, int seg, int col0) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) al[v] = (TV)__ldcg(c.alpha + (int64_t)seg * KT + col0 + v);
+    }
+    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&dot)[2][VEC]) const {
+        const int64_t o = i * KT + col0;
+        TV xv[VEC], rv[VEC], pv[VEC], qv[VEC];
+        ldv<LD, TV, VEC>(x + o, xv);
+        ldv<LD, TV, VEC>(r + o, rv);
+        ldv<LD, TV, VEC>(p + o, pv);
+        ldv<LD, TV, VEC>(q + o, qv);
+        const TV di = __ldg(dinv_of<TV>(c) + i);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            xv[v] += al[v] * pv[v];
+            rv[v] -= al[v] * qv[v];
+            const TV u = di * rv[v];
+            dot[0][v] += (double)rv[v] * (double)u;
+            dot[1][v] += (double)rv[v] * (double)rv[v];
+        }
+        stv(x + o, xv);
+        stv(r + o, rv);
+    }
+};
+
+// p = D^-1 r + beta p on the columns still iterating.
+template <class TV, int KT, class LD = LdPlain>
+struct OpDir {
+    static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = true;
+    const TV *r;
+    TV *p;
+    FinNone fin;
+    TV be[VEC];
+    bool act[VEC];
+    __device__ void setup(const Ctx &c, int seg, int col0) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            be[v] = (TV)__ldcg(c.beta + (int64_t)seg * KT + col0 + v);
+            act[v] = __ldcg(c.active + (int64_t)seg * KT + col0 + v) != 0;
+        }
+    }
+    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&)[1][VEC]) const {
+        const int64_t o = i * KT + col0;
+        TV rv[VEC], pv[VEC];
+        ldv<LD, TV, VEC>(r + o, rv);
+        ldv<LD, TV, VEC>(p + o, pv);
+        const TV di = __ldg(dinv_of<TV>(c) + i);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) pv[v] = act[v] ? di * rv[v] + be[v] * pv[v] : pv[v];
+        stv(p + o, pv);
+    }
+};
+
+// sum of x and delta^T x per segment (end of solve).
+template <class TV, int KT, class LD = LdPlain>
+struct OpFinal {
+    static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = false;
+    const TV *x;
+    const double *delta;
+    FinFinal fin;
+    __device__ void setup(const Ctx &, int, int) {}
+    __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, double (&dot)[2][VEC]) const {
+        const int64_t o = i * KT + col0;
+        TV xv[VEC];
+        double dl[VEC];
+        ldv<LD, TV, VEC>(x + o, xv);
+        ldv<LD, double, VEC>(delta + o, dl);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            dot[0][v] += (double)xv[v];
+            dot[1][v] += dl[v] * (double)xv[v];
+        }
+    }
+};
+
+// z_out = src - mean_seg(src) in the user layout [k][n] (optionally permuted).
+template <class TS, class TZ, int KT, class LD = LdPlain>
+struct OpZout {
+    static constexpr int ND = 0, VEC = VecCfg<TS, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = false;
+    const TS *src;
+    const double *meanv;
+    FinNone fin;
+    TZ *Z;
+    int64_t base, ld;
+    int kc;
+    double mu[VEC];
+    __device__ void setup(const Ctx &c, int seg, int col0) {
+        const Owner &o = owner_of(c, seg);
+        Z = reinterpret_cast<TZ *>(o.z);
+        base = o.base;
+        ld = o.ld;
+        kc = o.kc;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) mu[v] = __ldcg(meanv + (int64_t)seg * KT + col0 + v);
+    }
+    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&)[1][VEC]) const {
+        if (!Z) return;
+        const int64_t u = (c.perm ? (int64_t)__ldg(c.perm + i) : i) - base;
+        TS sv[VEC];
+        ldv<LD, TS, VEC>(src + i * KT + col0, sv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const int j = col0 + v;
+            if (j < kc) Z[(int64_t)j * ld + u] = (TZ)((double)sv[v] - mu[v]);
+        }
+    }
+};
+
+// z64 += x (FP32 correction of one refinement step, accumulated in FP64).
+template <class TV, int KT, class LD = LdPlain>
+struct OpAccum {
+    static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = false;
+    const TV *x;
+    double *z;
+    FinNone fin;
+    __device__ void setup(const Ctx &, int, int) {}
+    __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, double (&)[1][VEC]) const {
+        const int64_t o = i * KT + col0;
+        TV xv[VEC];
+        ldv<LD, TV, VEC>(x + o, xv);
+        double zv[VEC];
+        ldv<LD, double, VEC>(z + o, zv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) zv[v] += (double)xv[v];
+        stv(z + o, zv);
+    }
+};
+
+}  // namespace dev
+}  // namespace nvd

@@ -1,0 +1,256 @@
+// C ABI: nvd_ge_distance and nvd_laplacian_apply.
+//
+// nvd_ge_distance evaluates the GE distance of Section 3.1,
+//   d^2 = (x - y)^T L^+ (x - y),
+// through a Laplacian solve (Section 3.2) instead of the pseudoinverse: pairs are
+// processed in tiles of KT right-hand sides that share one SpMM per CG
+// iteration, each (component, pair) keeping its own CG scalars.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "dispatch.h"
+#include "solver.cuh"
+
+using namespace nvd;
+
+// gather: dst[i] = src[perm[i]] (user -> internal); scatter: dst[perm[i]] = src[i].
+template <class T>
+__global__ void k_permute(const T *__restrict__ src, T *__restrict__ dst, const int32_t *__restrict__ perm,
+                          int64_t n, bool gather) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (gather) dst[i] = src[perm[i]];
+        else dst[perm[i]] = src[i];
+    }
+}
+
+static int permute_vector(const void *src, void *dst, const int32_t *perm, int64_t n, int dtype, bool gather,
+                   cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    if (dtype == NVD_F64)
+        k_permute<double><<<grid, 256, 0, s>>>((const double *)src, (double *)dst, perm, n, gather);
+    else
+        k_permute<float><<<grid, 256, 0, s>>>((const float *)src, (float *)dst, perm, n, gather);
+    NVD_TRY_CUDA(cudaGetLastError());
+    return NVD_OK;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int pick_kt(const nvd_solve_opts &o, int k) {
+    if (o.flags & NVD_SOLVE_SINGLE_RHS) return 1;
+    if (o.kt) return o.kt;
+    const int cap = o.mode == NVD_MODE_FP64 ? 16 : 32;
+    int kt = 1;
+    for (int c : {4, 8, 16, 32})
+        if (kt < k && c <= cap) kt = c;
+    return k == 1 ? 1 : kt;
+}
+
+int check_opts(const nvd_solve_opts &o) {
+    const uint32_t known = NVD_SOLVE_SINGLE_RHS | NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS |
+                           NVD_SOLVE_PERSISTENT | NVD_SOLVE_NO_SYNC;
+    if (o.mode < NVD_MODE_FP64 || o.mode > NVD_MODE_MIXED || !(o.rtol > 0.0) || o.max_iter < 1 ||
+        o.check_every < 1 || !(o.kt == 0 || o.kt == 1 || o.kt == 4 || o.kt == 8 || o.kt == 16 || o.kt == 32) ||
+        (o.flags & ~known) || (o.mode == NVD_MODE_MIXED && (!(o.d2_rtol > 0.0) || o.max_refine < 1))) {
+        set_error("nvd_solve_opts: invalid field (mode=%d rtol=%g max_iter=%d check_every=%d kt=%d flags=%u)",
+                  o.mode, o.rtol, o.max_iter, o.check_every, o.kt, o.flags);
+        return NVD_ERR_INVALID_ARG;
+    }
+    return NVD_OK;
+}
+
+int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdt,
+                  const nvd_solve_opts *opts, double *d2_out, void *z_out, nvd_solve_stats *stats,
+                  cudaStream_t s) {
+    if (!g || k < 0 || (xdt != NVD_F32 && xdt != NVD_F64)) {
+        set_error("nvd_ge_distance: invalid argument");
+        return NVD_ERR_INVALID_ARG;
+    }
+    if (k == 0) return NVD_OK;
+    if (!x || !y || !d2_out) {
+        set_error("nvd_ge_distance: x, y and d2_out are required");
+        return NVD_ERR_INVALID_ARG;
+    }
+    nvd_solve_opts o;
+    if (opts) o = *opts; else nvd_solve_opts_default(&o);
+    NVD_TRY(check_opts(o));
+    DeviceGuard guard(g->device);
+    const int KT = pick_kt(o, k);
+    const bool mixed = o.mode == NVD_MODE_MIXED;
+    const size_t szv = o.mode == NVD_MODE_FP64 ? 8 : 4;
+    const size_t xsz = xdt == NVD_F64 ? 8 : 4;
+    const bool host_in = o.flags & NVD_SOLVE_HOST_INPUTS;
+    const bool d2_dev = o.flags & NVD_SOLVE_D2_DEVICE;
+    Plan *pl = nullptr, *pl64 = nullptr;
+    NVD_TRY(get_plan(g, KT, (int)szv, (int)szv, &pl));
+    if (mixed) NVD_TRY(get_plan(g, KT, 8, 8, &pl64));
+    Ctx c;
+    memset(&c, 0, sizeof(c));
+    fill_graph_ctx(g, pl, &c);
+    SolveWs w;
+    NVD_TRY(setup_ws(g, pl, KT, szv, mixed, 1, &c, &w, s));
+    if (mixed) c.part_stride = std::max(pl->part_slots(), pl64->part_slots());
+    if (mixed) {
+        int st = NVD_OK;
+        w.part = (double *)g->wsp("part", (size_t)4 * c.part_stride * KT * 8 + 64, &st);
+        w.hsum = (double *)g->wsp("hsum", (size_t)std::max<int64_t>({pl->n_chunks, pl64->n_chunks, 1}) * KT * 8, &st);
+        if (st) return st;
+        c.part = w.part;
+        c.hsum = w.hsum;
+    }
+    // staging for host inputs/outputs
+    void *sx = nullptr, *sy = nullptr, *sz = nullptr;
+    if (host_in) {
+        int st = NVD_OK;
+        sx = g->wsp("stage_x", (size_t)KT * g->n * xsz, &st);
+        sy = g->wsp("stage_y", (size_t)KT * g->n * xsz, &st);
+        if (z_out) sz = g->wsp("stage_z", (size_t)KT * g->n * xsz, &st);
+        if (st) return st;
+    }
+    std::vector<ColResult> res(KT);
+    std::vector<int> it_mixed;
+    std::vector<double> rr_mixed;
+    int overall = NVD_OK;
+    const bool need_host = !d2_dev || stats || host_in;
+    for (int32_t c0 = 0; c0 < k; c0 += KT) {
+        const int kc = std::min<int>(KT, k - c0);
+        const size_t off = (size_t)c0 * g->n * xsz;
+        TileIO io;
+        io.kc = kc;
+        if (host_in) {
+            NVD_TRY_CUDA(cudaMemcpyAsync(sx, (const char *)x + off, (size_t)kc * g->n * xsz, cudaMemcpyHostToDevice, s));
+            NVD_TRY_CUDA(cudaMemcpyAsync(sy, (const char *)y + off, (size_t)kc * g->n * xsz, cudaMemcpyHostToDevice, s));
+            io.x = sx;
+            io.y = sy;
+            io.z = sz;
+        } else {
+            io.x = (const char *)x + off;
+            io.y = (const char *)y + off;
+            io.z = z_out ? (char *)z_out + off : nullptr;
+        }
+        if (io.z && g->n_singleton > 0)
+            NVD_TRY_CUDA(cudaMemsetAsync(io.z, 0, (size_t)kc * g->n * xsz, s));
+        int steps = 0, conv = 1;
+        if (o.mode == NVD_MODE_FP64)
+            NVD_TRY(run_tile_fp64(g, c, w, o, io, s, KT, xdt));
+        else if (o.mode == NVD_MODE_FP32)
+            NVD_TRY(run_tile_fp32(g, c, w, o, io, s, KT, xdt));
+        else
+            NVD_TRY(run_tile_mixed(g, c, pl64, w, o, io, s, KT, xdt, it_mixed, rr_mixed, &steps, &conv));
+        NVD_TRY(run_collect(c, KT, w.res, d2_dev ? d2_out + c0 : nullptr, 0, 1, s));
+        if (host_in && z_out)
+            NVD_TRY_CUDA(cudaMemcpyAsync((char *)z_out + off, sz, (size_t)kc * g->n * xsz, cudaMemcpyDeviceToHost, s));
+        if (need_host) {
+            NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), w.res, KT * sizeof(ColResult), cudaMemcpyDeviceToHost, s));
+            NVD_TRY_CUDA(cudaStreamSynchronize(s));
+            for (int j = 0; j < kc; ++j) {
+                ColResult &r = res[j];
+                if (mixed) r.status = conv ? NVD_OK : NVD_ERR_NOT_CONVERGED;
+                if (!d2_dev) d2_out[c0 + j] = r.d2;
+                if (r.status != NVD_OK && overall != NVD_ERR_NUMERIC) overall = r.status;
+                if (stats) {
+                    nvd_solve_stats &st = stats[c0 + j];
+                    st.status = r.status;
+                    st.reserved = 0;
+                    if (mixed) {
+                        st.iters = it_mixed[j];
+                        st.refine_steps = steps;
+                        st.rel_resid = rr_mixed[j];
+                    } else {
+                        st.iters = r.iters;
+                        st.refine_steps = 0;
+                        st.rel_resid = r.rr0 > 0.0 ? std::sqrt(std::max(r.rr, 0.0) / r.rr0) : 0.0;
+                    }
+                }
+            }
+        }
+    }
+    if (!(o.flags & NVD_SOLVE_NO_SYNC) || need_host) NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    if (overall != NVD_OK) set_error("nvd_ge_distance: some pair ended with status %d (%s)", overall,
+                                     nvd_status_string(overall));
+    return overall;
+}
+
+int apply_impl(nvd_graph_t g, int32_t k, const void *x, void *y, int32_t dtype, cudaStream_t s) {
+    if (!g || k < 0 || (k > 0 && (!x || !y)) || (dtype != NVD_F32 && dtype != NVD_F64)) {
+        set_error("nvd_laplacian_apply: invalid argument");
+        return NVD_ERR_INVALID_ARG;
+    }
+    if (k == 0) return NVD_OK;
+    DeviceGuard guard(g->device);
+    const size_t sz = dtype == NVD_F64 ? 8 : 4;
+    Plan *pl = nullptr;
+    NVD_TRY(get_plan(g, 1, (int)sz, (int)sz, &pl));
+    Ctx c;
+    memset(&c, 0, sizeof(c));
+    fill_graph_ctx(g, pl, &c);
+    if (dtype == NVD_F32) {
+        const float *w32 = nullptr;
+        NVD_TRY(get_w32(g, &w32, s));
+        c.w = w32;
+    }
+    int st = NVD_OK;
+    void *xin = nullptr, *yout = nullptr;
+    if (g->perm.p) {
+        xin = g->wsp("apply_x", g->n * sz, &st);
+        yout = g->wsp("apply_y", g->n * sz, &st);
+        if (st) return st;
+    }
+    NVD_TRY_CUDA(cudaMemsetAsync(y, 0, (size_t)k * g->n * sz, s));
+    for (int32_t j = 0; j < k; ++j) {
+        const char *xj = (const char *)x + (size_t)j * g->n * sz;
+        char *yj = (char *)y + (size_t)j * g->n * sz;
+        if (!g->perm.p) {
+            NVD_TRY(run_apply(g, c, xj, yj, dtype, s));
+        } else {
+            NVD_TRY(permute_vector(xj, xin, g->perm.as<int32_t>(), g->n, dtype, true, s));
+            NVD_TRY_CUDA(cudaMemsetAsync(yout, 0, g->n * sz, s));
+            NVD_TRY(run_apply(g, c, xin, yout, dtype, s));
+            NVD_TRY(permute_vector(yout, yj, g->perm.as<int32_t>(), g->n, dtype, false, s));
+        }
+    }
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    return NVD_OK;
+}
+
+}  // namespace
+
+extern "C" int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdtype,
+                               const nvd_solve_opts *opts, double *d2_out, void *z_out,
+                               nvd_solve_stats *stats, nvd_stream_t stream) {
+    clear_error();
+    try {
+        return distance_impl(g, k, x, y, xdtype, opts, d2_out, z_out, stats, (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        set_error("nvd_ge_distance: host allocation failed");
+        return NVD_ERR_OOM;
+    } catch (...) {
+        set_error("nvd_ge_distance: unexpected host exception");
+        return NVD_ERR_CUDA;
+    }
+}
+
+extern "C" int nvd_laplacian_apply(nvd_graph_t g, int32_t k, const void *x, void *y, int32_t dtype,
+                                   nvd_stream_t stream) {
+    clear_error();
+    try {
+        return apply_impl(g, k, x, y, dtype, (cudaStream_t)stream);
+    } catch (...) {
+        set_error("nvd_laplacian_apply: unexpected host exception");
+        return NVD_ERR_CUDA;
+    }
+}

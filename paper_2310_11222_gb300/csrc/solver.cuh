@@ -1,0 +1,336 @@
+// Host-side driver of the PCG solve for one tile of KT right-hand sides (internal).
+//
+// Method (Section 3.1 GE equation, Section 3.2 Laplacian solvers): for every pair
+// delta = x - y, project delta mean-zero on each component, solve L z = delta by
+// Jacobi-preconditioned CG from z = 0, and report d^2 = delta^T z.  Three
+// precision modes share the kernels:
+//   FP64   vectors and arithmetic in FP64 (TV = TA = double);
+//   FP32   vectors, SpMV/SpMM and updates in FP32, inner products and CG scalars in FP64;
+//   MIXED  FP32 PCG corrections inside an FP64 iterative-refinement loop
+//          (r = delta - L z in FP64, z += correction), d^2 from the variational
+//          form 2 delta^T z - z^T L z.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "graph.h"
+#include "kernels.cuh"
+
+namespace nvd {
+
+// ------------------------------------------------------------------ kernels
+
+template <class TV, class TW, class TA, int KT, class Epi>
+__global__ void __launch_bounds__(NT) k_spmm(Ctx c, Epi epi, const TV *src, TV *dst) {
+    __shared__ __align__(16) char smem[dev::SpCfg<TV, TA, KT>::SMEM];
+    dev::spmm_block<dev::LdRO, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, smem);
+}
+
+template <class TV, int KT, class Op>
+__global__ void __launch_bounds__(NT) k_vec(Ctx c, Op op) {
+    __shared__ __align__(16) char smem[vec_smem_bytes(KT)];
+    dev::vec_block<TV, KT, Op>(c, op, blockIdx.x, smem);
+}
+
+// Per (owner, column): sum d^2 and residual norms over the owner's segments, the
+// largest iteration count and the most severe status.
+template <int KT>
+__global__ void k_collect(Ctx c, ColResult *res, double *d2dev, int64_t d2_stride) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int no = c.owners ? c.n_owner : 1;
+    if (t >= no * KT) return;
+    const int o = t / KT, j = t % KT;
+    const Owner ow = c.owners ? c.owners[o] : c.own0;
+    ColResult r{0.0, 0.0, 0.0, 0, NVD_OK};
+    for (int sg = ow.seg0; sg < ow.seg1; ++sg) {
+        const int64_t i = (int64_t)sg * KT + j;
+        r.d2 += c.d2[i];
+        r.rr += c.rr[i];
+        r.rr0 += c.rr0[i];
+        r.iters = max(r.iters, c.iters[i]);
+        const int st = c.status[i];
+        if (st == NVD_ERR_NUMERIC || (st == NVD_ERR_NOT_CONVERGED && r.status == NVD_OK)) r.status = st;
+    }
+    res[t] = r;
+    if (d2dev && j < ow.kc) d2dev[(int64_t)o * d2_stride + j] = r.d2;
+}
+
+// ------------------------------------------------------------------ profiling hooks (api.cu)
+
+bool prof_enabled();
+void prof_begin(cudaStream_t s);
+void prof_end(cudaStream_t s, double bytes);
+
+// ------------------------------------------------------------------ workspace
+
+struct SolveWs {
+    double *part = nullptr;
+    unsigned *counter = nullptr;
+    double *st_d = nullptr;   // 10 x [nseg][KT]
+    int32_t *st_i = nullptr;  // 3 x [nseg][KT] + n_active + err
+    ColResult *res = nullptr;
+    double *hsum = nullptr;       // [n_chunks][KT] partial row sums of split rows
+    double *delta = nullptr, *z64 = nullptr, *r64 = nullptr;
+    void *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+};
+
+// Allocate (or reuse) the workspace of a solve and point the Ctx state at it.
+inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixed, int n_owner,
+                    Ctx *c, SolveWs *w, cudaStream_t s) {
+    int st = NVD_OK;
+    const int64_t nseg = std::max(g->nseg, 1);
+    const int64_t sk = nseg * KT;
+    const int64_t nk = g->n * KT;
+    w->part = (double *)g->wsp("part", (size_t)4 * pl->part_slots() * KT * 8 + 64, &st);
+    w->counter = (unsigned *)g->wsp("counter", (size_t)nseg * 4, &st);
+    w->st_d = (double *)g->wsp("st_d", (size_t)10 * sk * 8, &st);
+    w->st_i = (int32_t *)g->wsp("st_i", (size_t)(3 * sk + 8) * 4, &st);
+    w->res = (ColResult *)g->wsp("res", (size_t)std::max(n_owner, 1) * KT * sizeof(ColResult), &st);
+    w->hsum = (double *)g->wsp("hsum", (size_t)std::max<int64_t>(pl->n_chunks, 1) * KT * 8, &st);
+    w->delta = (double *)g->wsp("delta", (size_t)nk * 8, &st);
+    w->x = g->wsp("x", (size_t)nk * tv, &st);
+    w->r = g->wsp("r", (size_t)nk * tv, &st);
+    w->p = g->wsp("p", (size_t)nk * tv, &st);
+    w->q = g->wsp("q", (size_t)nk * tv, &st);
+    if (mixed) {
+        w->z64 = (double *)g->wsp("z64", (size_t)nk * 8, &st);
+        w->r64 = (double *)g->wsp("r64", (size_t)nk * 8, &st);
+    }
+    if (st != NVD_OK) return st;
+    NVD_TRY_CUDA(cudaMemsetAsync(w->counter, 0, (size_t)nseg * 4, s));
+    NVD_TRY_CUDA(cudaMemsetAsync(w->st_i, 0, (size_t)(3 * sk + 8) * 4, s));
+    double *d = w->st_d;
+    c->rho = d; c->rr = d + sk; c->rr0 = d + 2 * sk; c->alpha = d + 3 * sk; c->beta = d + 4 * sk;
+    c->mean = d + 5 * sk; c->meanx = d + 6 * sk; c->d2 = d + 7 * sk; c->dz = d + 8 * sk; c->zr = d + 9 * sk;
+    c->active = w->st_i; c->iters = w->st_i + sk; c->status = w->st_i + 2 * sk;
+    c->n_active = w->st_i + 3 * sk;
+    c->err = w->st_i + 3 * sk + 1;
+    c->part = w->part;
+    c->part_stride = pl->part_slots();
+    c->counter = w->counter;
+    c->hsum = w->hsum;
+    return NVD_OK;
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <class TV, class TW, class TA, int KT, class Epi>
+inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cudaStream_t s,
+                       double bytes) {
+    if (c.n_sblk == 0) return NVD_OK;
+    const bool prof = prof_enabled();
+    if (prof) prof_begin(s);
+    k_spmm<TV, TW, TA, KT, Epi><<<(unsigned)c.n_sblk, NT, 0, s>>>(c, epi, src, dst);
+    if (prof) prof_end(s, bytes);
+    NVD_TRY_CUDA(cudaGetLastError());
+    return NVD_OK;
+}
+
+template <class TV, int KT, class Op>
+inline int launch_vec(const Ctx &c, const Op &op, cudaStream_t s) {
+    if (c.n_vblk == 0) return NVD_OK;
+    k_vec<TV, KT, Op><<<(unsigned)c.n_vblk, NT, 0, s>>>(c, op);
+    NVD_TRY_CUDA(cudaGetLastError());
+    return NVD_OK;
+}
+
+// Algorithmic bytes of one SpMV/SpMM launch: the CSR (column indices, weights,
+// row pointers), the degrees, one read of the gathered vector and one write of
+// the result, over the nodes that belong to a segment.
+inline double spmm_bytes(const nvd_graph_s *g, int KT, size_t szv, size_t szw, size_t sza) {
+    int64_t rows = 0;
+    for (int s2 = 0; s2 < g->nseg; ++s2) rows += g->h_seg_end[s2] - g->h_seg_begin[s2];
+    return (double)g->nnz * (4.0 + (double)szw) + 8.0 * (double)(rows + 1) + (double)rows * (double)sza +
+           2.0 * (double)rows * KT * (double)szv;
+}
+
+// Host-visible polling buffers (pinned) and events, one set per thread.
+struct PollBufs {
+    int32_t *h = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int init() {
+        if (h) return NVD_OK;
+        NVD_TRY_CUDA(cudaHostAlloc((void **)&h, 64, cudaHostAllocDefault));
+        NVD_TRY_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        NVD_TRY_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        return NVD_OK;
+    }
+};
+inline PollBufs &poll_bufs() {
+    static thread_local PollBufs pb;
+    return pb;
+}
+
+// PCG iterations until every (segment, column) left the active set.  The device
+// deactivates a column at convergence or at max_iter, so the loop always ends;
+// the host polls n_active every `check_every` iterations, one batch behind, so
+// polling never drains the GPU queue.  Iterations issued after convergence cost
+// one near-empty launch per pass (inactive segments skip their work).
+template <class TV, class TW, class TA, int KT>
+int pcg_loop(const Ctx &c, TV *x, TV *r, TV *p, TV *q, int max_iter, int check_every,
+             double bytes, cudaStream_t s) {
+    PollBufs &pb = poll_bufs();
+    NVD_TRY(pb.init());
+    dev::EpiLap epi;
+    epi.fin.KT = KT;
+    dev::OpUpdate<TV, KT> ou;
+    ou.x = x; ou.r = r; ou.p = p; ou.q = q;
+    ou.fin.KT = KT;
+    dev::OpDir<TV, KT> od;
+    od.r = r; od.p = p;
+    const int C = std::max(1, check_every);
+    int64_t issued = 0;
+    int batch = 0;
+    bool done = false;
+    const int64_t cap = (int64_t)max_iter + 2 * C;
+    while (!done && issued < cap) {
+        for (int t = 0; t < C; ++t) {
+            NVD_TRY((launch_spmm<TV, TW, TA, KT>(c, epi, p, q, s, bytes)));
+            NVD_TRY((launch_vec<TV, KT>(c, ou, s)));
+            NVD_TRY((launch_vec<TV, KT>(c, od, s)));
+        }
+        issued += C;
+        NVD_TRY_CUDA(cudaMemcpyAsync(pb.h + (batch & 1), c.n_active, 4, cudaMemcpyDeviceToHost, s));
+        NVD_TRY_CUDA(cudaEventRecord(pb.ev[batch & 1], s));
+        if (batch > 0) {
+            NVD_TRY_CUDA(cudaEventSynchronize(pb.ev[(batch - 1) & 1]));
+            if (pb.h[(batch - 1) & 1] == 0) done = true;
+        }
+        ++batch;
+    }
+    return NVD_OK;
+}
+
+// ------------------------------------------------------------------ one tile
+
+struct TileIO {
+    int32_t kc;           // valid pairs in this tile
+    const void *x, *y;    // device, [kc][n], offset to the tile
+    void *z;              // device or NULL
+};
+
+// FP64 / FP32 PCG on one tile.  Results stay in the Ctx state (d2, rr, ...).
+template <class TV, class TW, class TA, int KT, class TX>
+int tile_pcg(nvd_graph_s *g, Ctx c, SolveWs &w, const nvd_solve_opts &o, const TileIO &io,
+             cudaStream_t s) {
+    c.own0 = Owner{io.x, io.y, io.z, 0, g->n, io.kc, 0, g->nseg, 0};
+    c.owners = nullptr;
+    c.n_owner = 1;
+    c.rtol2 = o.rtol * o.rtol;
+    c.max_iter = o.max_iter;
+    double *delta = w.delta;
+    TV *x = (TV *)w.x, *r = (TV *)w.r, *p = (TV *)w.p, *q = (TV *)w.q;
+    dev::OpFormDelta<TX, KT> fd;
+    fd.delta = delta;
+    fd.fin.KT = KT;
+    NVD_TRY((launch_vec<double, KT>(c, fd, s)));
+    NVD_TRY_CUDA(cudaMemsetAsync(c.n_active, 0, 4, s));
+    dev::OpInit<TV, KT> oi;
+    oi.src = delta; oi.writeback = delta; oi.x = x; oi.r = r; oi.p = p;
+    oi.fin.KT = KT;
+    NVD_TRY((launch_vec<TV, KT>(c, oi, s)));
+    const double bytes = spmm_bytes(g, KT, sizeof(TV), sizeof(TW), sizeof(TA));
+    NVD_TRY((pcg_loop<TV, TW, TA, KT>(c, x, r, p, q, o.max_iter, o.check_every, bytes, s)));
+    dev::OpFinal<TV, KT> of;
+    of.x = x; of.delta = delta;
+    of.fin.KT = KT; of.fin.set_d2 = true;
+    NVD_TRY((launch_vec<TV, KT>(c, of, s)));
+    if (io.z) {
+        dev::OpZout<TV, TX, KT> oz;
+        oz.src = x; oz.meanv = c.meanx;
+        NVD_TRY((launch_vec<TV, KT>(c, oz, s)));
+    }
+    return NVD_OK;
+}
+
+// MIXED: FP32 PCG corrections inside FP64 iterative refinement on one tile.
+// Per column: iters_acc = inner CG iterations summed over steps, relres = final
+// ||delta - L z|| / ||delta|| in FP64; *steps_out = refinement steps taken.
+template <class TWN, int KT, class TX>
+int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_solve_opts &o,
+               const TileIO &io, cudaStream_t s, std::vector<int> &iters_acc,
+               std::vector<double> &relres, int *steps_out, int *conv_out) {
+    c.own0 = Owner{io.x, io.y, io.z, 0, g->n, io.kc, 0, g->nseg, 0};
+    c.owners = nullptr;
+    c.n_owner = 1;
+    c.rtol2 = o.rtol * o.rtol;
+    c.max_iter = o.max_iter;
+    const float *w32 = nullptr;
+    NVD_TRY(get_w32(g, &w32, s));
+    const void *wnat = g->w.p;
+    double *delta = w.delta;
+    float *x = (float *)w.x, *r = (float *)w.r, *p = (float *)w.p, *q = (float *)w.q;
+    dev::OpFormDelta<TX, KT> fd;
+    fd.delta = delta;
+    fd.fin.KT = KT;
+    NVD_TRY((launch_vec<double, KT>(c, fd, s)));
+    NVD_TRY_CUDA(cudaMemsetAsync(w.z64, 0, (size_t)g->n * KT * 8, s));
+    const double bytes32 = spmm_bytes(g, KT, 4, 4, 4);
+    const double bytes64 = spmm_bytes(g, KT, 8, sizeof(TWN), 8);
+    std::vector<ColResult> res(KT);
+    std::vector<double> prev(KT, 0.0), dd(KT, 0.0);
+    iters_acc.assign(KT, 0);
+    relres.assign(KT, 0.0);
+    Ctx ci = c;
+    ci.w = w32;
+    Ctx cr = c;
+    cr.w = wnat;
+    set_sp_plan(&cr, pl64);
+    int step = 0;
+    *conv_out = 0;
+    const int max_steps = std::max(1, o.max_refine);
+    while (step < max_steps) {
+        NVD_TRY_CUDA(cudaMemsetAsync(c.n_active, 0, 4, s));
+        dev::OpInit<float, KT> oi;
+        oi.src = step == 0 ? delta : w.r64;
+        oi.writeback = step == 0 ? delta : nullptr;
+        oi.x = x; oi.r = r; oi.p = p;
+        oi.fin.KT = KT;
+        NVD_TRY((launch_vec<float, KT>(ci, oi, s)));
+        NVD_TRY((pcg_loop<float, float, float, KT>(ci, x, r, p, q, o.max_iter, o.check_every, bytes32, s)));
+        dev::OpAccum<float, KT> oa;
+        oa.x = x; oa.z = w.z64;
+        NVD_TRY((launch_vec<float, KT>(c, oa, s)));
+        k_collect<KT><<<1, 128, 0, s>>>(c, w.res, nullptr, 0);
+        NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), w.res, KT * sizeof(ColResult), cudaMemcpyDeviceToHost, s));
+        NVD_TRY_CUDA(cudaStreamSynchronize(s));
+        for (int j = 0; j < KT; ++j) {
+            iters_acc[j] += res[j].iters;
+            if (step == 0) dd[j] = res[j].rr0;   // |P delta|^2
+        }
+        // FP64 residual r = delta - L z and the variational d^2
+        dev::EpiResid er;
+        er.delta = delta;
+        er.fin.KT = KT;
+        NVD_TRY((launch_spmm<double, TWN, double, KT>(cr, er, w.z64, w.r64, s, bytes64)));
+        k_collect<KT><<<1, 128, 0, s>>>(c, w.res, nullptr, 0);
+        NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), w.res, KT * sizeof(ColResult), cudaMemcpyDeviceToHost, s));
+        NVD_TRY_CUDA(cudaStreamSynchronize(s));
+        ++step;
+        bool d2_settled = step > 1, resid_floor = true;
+        for (int j = 0; j < io.kc; ++j) {
+            const double d2 = res[j].d2;
+            if (!(std::fabs(d2 - prev[j]) <= o.d2_rtol * std::fabs(d2))) d2_settled = false;
+            prev[j] = d2;
+            relres[j] = dd[j] > 0.0 ? std::sqrt(std::max(res[j].rr, 0.0) / dd[j]) : 0.0;
+            if (!(relres[j] <= 1e-14)) resid_floor = false;
+        }
+        *conv_out = (d2_settled || resid_floor) ? 1 : 0;
+        if (*conv_out) break;
+    }
+    *steps_out = step;
+    dev::OpFinal<double, KT> of;
+    of.x = w.z64; of.delta = delta;
+    of.fin.KT = KT; of.fin.set_d2 = false;
+    NVD_TRY((launch_vec<double, KT>(c, of, s)));
+    if (io.z) {
+        dev::OpZout<double, TX, KT> oz;
+        oz.src = w.z64; oz.meanv = c.meanx;
+        NVD_TRY((launch_vec<double, KT>(c, oz, s)));
+    }
+    return NVD_OK;
+}
+
+}  // namespace nvd

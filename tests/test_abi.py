@@ -1,0 +1,74 @@
+"""Host-side checks of the C ABI library (no GPU work): it loads, exports every
+symbol include/nvd.h declares, and its pure host functions behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nvd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_11222_gb300 import build
+    build.build()
+    import paper_2310_11222_gb300 as nvd
+    return nvd.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(nvd_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["nvd_graph_create", "nvd_graph_destroy", "nvd_graph_info", "nvd_ge_distance",
+                 "nvd_ge_distance_batched", "nvd_ge_grad", "nvd_status_string", "nvd_laplacian_apply"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(lib):
+    assert lib.nvd_status_string(0) == b"NVD_OK"
+    assert lib.nvd_status_string(2) == b"NVD_ERR_NOT_SYMMETRIC"
+    assert lib.nvd_status_string(123) == b"NVD_ERR_UNKNOWN"
+    assert b"sm_103a" in lib.nvd_version()
+
+
+def test_default_opts(lib):
+    import paper_2310_11222_gb300 as nvd
+    o = nvd.SolveOpts()
+    lib.nvd_solve_opts_default(ctypes.byref(o))
+    assert o.mode == 0 and o.rtol == 1e-10 and o.max_iter == 10000 and o.kt == 0
+    assert ctypes.sizeof(nvd.SolveOpts) == 40 and ctypes.sizeof(nvd.SolveStats) == 24
+
+
+def test_invalid_arguments_rejected_before_device_work(lib):
+    h = ctypes.c_void_p(None)
+    # n = 0, NULL rowptr, bad dtype: all rejected on the host
+    assert lib.nvd_graph_create(ctypes.byref(h), 0, 0, None, None, None, 1, 0, None) == 1
+    assert h.value is None
+    assert lib.nvd_graph_create(None, 3, 0, None, None, None, 1, 0, None) == 1
+    assert lib.nvd_graph_create(ctypes.byref(h), 3, 0, None, None, None, 7, 0, None) == 1
+    assert b"invalid" in lib.nvd_last_error()
+    assert lib.nvd_ge_distance(None, 1, None, None, 1, None, None, None, None, None) == 1
+    assert lib.nvd_ge_grad(None, 1, None, 1, None, None, None, None, None) == 1
+    assert lib.nvd_graph_destroy(None) == 0
+    assert lib.nvd_profile_read(3, None, None, None) == 1
+
+
+def test_package_fails_loudly_without_library(monkeypatch):
+    import paper_2310_11222_gb300 as nvd
+    monkeypatch.setattr(nvd, "_LIB_PATH", "/nonexistent/libnvd.so")
+    monkeypatch.setattr(nvd, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        nvd.load_library()
