@@ -361,6 +361,7 @@ struct FinResid {
 // q = L p = D p - W p, and p^T q for alpha.
 struct EpiLap {
     static constexpr int ND = 1;
+    static constexpr bool NEEDS_LIVE = true;   // CG step: converged segments skip the work
     template <class TV, class TA, int VEC>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
                                          const TA (&acc)[VEC], TA degi, TV *dst,
@@ -379,6 +380,7 @@ struct EpiLap {
 // y = L x only (operator application, no reduction).
 struct EpiApply {
     static constexpr int ND = 0;
+    static constexpr bool NEEDS_LIVE = false;
     template <class TV, class TA, int VEC>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
                                          const TA (&acc)[VEC], TA degi, TV *dst,
@@ -394,6 +396,7 @@ struct EpiApply {
 // FP64 refinement residual r = delta - L z with delta^T z, z^T r, r^T r, sum r.
 struct EpiResid {
     static constexpr int ND = 4;
+    static constexpr bool NEEDS_LIVE = false;  // runs after the inner solve, always on every segment
     const double *delta;
     template <class TV, class TA, int VEC>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
@@ -480,7 +483,7 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
 #pragma unroll
         for (int v = 0; v < VEC; ++v) dot[d][v] = 0.0;
 
-    const bool live = (ND == 0) || seg_live<KT>(c, seg);
+    const bool live = !Epi::NEEDS_LIVE || seg_live<KT>(c, seg);
     if (live) {
         for (int64_t si = blk.i0; si < blk.i1; ++si) {
             const SpItem it = c.items[si];

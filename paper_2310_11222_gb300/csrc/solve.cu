@@ -144,6 +144,12 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         }
         if (io.z && g->n_singleton > 0)
             NVD_TRY_CUDA(cudaMemsetAsync(io.z, 0, (size_t)kc * g->n * xsz, s));
+        // the tile's single owner: every segment of the graph, kc valid columns
+        c.own0 = Owner{io.x, io.y, io.z, 0, g->n, kc, 0, g->nseg, 0};
+        c.owners = nullptr;
+        c.n_owner = 1;
+        c.rtol2 = o.rtol * o.rtol;
+        c.max_iter = o.max_iter;
         int steps = 0, conv = 1;
         if (o.mode == NVD_MODE_FP64)
             NVD_TRY(run_tile_fp64(g, c, w, o, io, s, KT, xdt));
