@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput of the GE node-vector distance on GB300.
+
+Workload (one "step"): the Erdos-Renyi graph with n = 1,000,000 nodes and
+m = 5,000,000 edges (mean degree 10, largest component), FP64 weights
+Uniform[0.5, 2), and 8 vector pairs whose x and y have Uniform[0,1) values on 1%
+of the nodes, normalised to sum 1.  Each pair is solved on its own (one
+right-hand side at a time) by FP64 Jacobi-PCG to relative residual 1e-10 and
+d^2 = delta^T L^+ delta is returned (Section 3.1 GE equation via the Laplacian
+solve of Section 3.2).  Inputs are seeded and synthetic (no dataset).
+
+Metric: GE distances per second (whole job).  Beside it: the live roofline of
+the SpMV kernel (algorithmic bytes / CUDA-event time of its launches in the
+timed region, against the measured HBM copy bandwidth), the end-to-end rate
+through the C ABI with host buffers, and the oracle (plain FP64 CPU CG) timed
+on this machine's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank solves its own 8 pairs on its
+own copy of the graph (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GE distances/s on 1 GB300 at d² rel.err≤1e-6; SpMV HBM GB/s vs peak"
+UNIT = "distances/s"
+PAIRS_PER_STEP = 8
+RTOL = 1e-10
+
+
+def workload_config(g, n0):
+    return {
+        "workload": "er_large: Erdos-Renyi G(n=1e6, m=5e6) largest component, FP64 weights "
+                    "U[0.5,2), 8 pairs x,y U[0,1) on 1% of nodes normalised, single-RHS FP64 "
+                    "Jacobi-PCG to relative residual 1e-10",
+        "n": int(g.n), "nnz": int(g.nnz), "n_generated": int(n0), "pairs_per_step": PAIRS_PER_STEP,
+        "rtol": RTOL, "solver": "FP64 PCG, one right-hand side at a time",
+        "l2": "L2 flushed (256 MB write) between timed steps; working set 0.3 GB > 129 MB L2",
+    }
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2310_11222_gb300/csrc/kernels.cuh", "paper_2310_11222_gb300/csrc/common.h"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per SpMV launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "spmv_er_large_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        idx = str(local_rank)
+        if vis:
+            parts = [p.strip() for p in vis.split(",") if p.strip()]
+            if local_rank < len(parts):
+                idx = parts[local_rank]
+        self.idx = idx
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.idx], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(g, X, Y, budget_s=12.0, max_pairs=8):
+    """The oracle (plain FP64 CPU Jacobi-PCG, oracle/pcg.c) on this host's cores over a
+    bounded sample of the same pairs: returns (distances/s, threads, pairs, seconds, d2)."""
+    from oracle import cg as ocg
+    ocg.build()
+    threads = ocg.default_threads()
+    t0 = time.perf_counter()
+    d2s = []
+    for j in range(max_pairs):
+        d2, it, rr = ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X[j:j + 1], Y[j:j + 1], rtol=RTOL,
+                                  threads=threads)
+        d2s.append(float(d2[0]))
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return len(d2s) / dt, threads, len(d2s), dt, d2s
+
+
+def run_reference(args):
+    """Reference arm: the oracle timed as it stands on the host cores."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import synth
+    from oracle import cg as ocg
+    wl = synth.workload_er_large()
+    g = wl.graph
+    X, Y = wl.pairs(0, PAIRS_PER_STEP)
+    ocg.build()
+    threads = ocg.default_threads()
+    # one step = one pair of the workload (a bounded sample), oracle CG at rtol 1e-10
+    for s in range(args.warmup):
+        j = s % PAIRS_PER_STEP
+        ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X[j:j + 1], Y[j:j + 1], rtol=RTOL, threads=threads)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        j = s % PAIRS_PER_STEP
+        ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X[j:j + 1], Y[j:j + 1], rtol=RTOL, threads=threads)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    cfg = workload_config(g, wl.meta["n_generated"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} pairs of the workload, one per step, oracle FP64 CG "
+                                   f"(oracle/pcg.c) at rtol 1e-10"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS comparison runs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2310_11222_gb300 as nvd
+    import synth
+    nvd.load_library()
+
+    wl = synth.workload_er_large()
+    g = wl.graph
+    X, Y = wl.pairs(rank * PAIRS_PER_STEP, PAIRS_PER_STEP)     # each rank its own pairs
+    G = nvd.Graph.from_csr(g)
+    xt = torch.from_numpy(X).to(dev)
+    yt = torch.from_numpy(Y).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return nvd.ge_distance(G, xt, yt, rtol=RTOL, single_rhs=True, return_stats=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    nvd.profile_enable(True)
+    nvd.profile_read()
+    launches0 = nvd.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_wall0 = time.perf_counter()
+    last = None
+    for k in range(args.steps):
+        flush.zero_()                                   # evict L2 between steps (not timed)
+        ev[k][0].record()
+        last = step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = nvd.kernel_launches() - launches0
+    n_spmv, spmv_ms, spmv_bytes = nvd.profile_read()
+    nvd.profile_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    d2_last, stats = last
+    iters = [s["iters"] for s in stats]
+    statuses = [s["status"] for s in stats]
+
+    # ---- end to end through the C ABI with host buffers (copies inside the call)
+    xh = torch.from_numpy(X).pin_memory()
+    yh = torch.from_numpy(Y).pin_memory()
+    for _ in range(2):
+        nvd.ge_distance(G, xh, yh, rtol=RTOL, single_rhs=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        d2_host = nvd.ge_distance(G, xh, yh, rtol=RTOL, single_rhs=True)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te0
+    if dist is not None:
+        t = torch.tensor([te], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+
+    # ---- the batched comparison the method is built for (same graph, same 8 pairs)
+    extra = None
+    if not args.no_extra and rank == 0:
+        def rate(**kw):
+            for _ in range(2):
+                nvd.ge_distance(G, xt, yt, **kw)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            a.record()
+            for _ in range(reps):
+                out = nvd.ge_distance(G, xt, yt, **kw)
+            b.record()
+            torch.cuda.synchronize()
+            return PAIRS_PER_STEP * reps / (a.elapsed_time(b) / 1e3), out
+        r64, d64 = rate(rtol=RTOL)
+        rmx, dmx = rate(mode=nvd.MODE_MIXED, rtol=1e-4, d2_rtol=1e-10)
+        extra = {"fp64_multi_rhs_distances_per_s": r64, "mixed_multi_rhs_distances_per_s": rmx,
+                 "d2_fp64_multi": d64.cpu().numpy().tolist(), "d2_mixed": dmx.cpu().numpy().tolist()}
+
+    value = PAIRS_PER_STEP * world * args.steps / (total_ms / 1e3)
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = (spmv_bytes / n_spmv) / (spmv_ms / n_spmv / 1e3) / 1e9 if n_spmv else None
+    traffic = ncu_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(g, wl.meta["n_generated"]),
+        "e2e": {"value": PAIRS_PER_STEP * world * args.steps / te, "unit": UNIT,
+                "h2d_bytes_per_step": int(xh.numel() * 8 * 2), "d2h_bytes_per_step": PAIRS_PER_STEP * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "k_spmm<double,double,double,1,EpiLap> (Laplacian SpMV + fused p^T q)",
+                     "launches": n_spmv, "avg_launch_us": 1e3 * spmv_ms / n_spmv if n_spmv else None,
+                     "algorithmic_bytes_per_launch": spmv_bytes / n_spmv if n_spmv else None,
+                     "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy) of MEASURED_PEAKS.json"},
+        "solver": {"iters_per_pair": iters, "status": statuses, "wall_s_timed": t_wall},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, th, npairs, dt, d2_or = cpu_baseline(g, X, Y)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+                                "sample": f"first {npairs} of the step's 8 pairs ({dt:.1f} s), oracle "
+                                          f"FP64 Jacobi-PCG (oracle/pcg.c) at rtol 1e-10"}
+        got = d2_last.cpu().numpy()[:npairs]
+        line["max_rel_err_vs_oracle"] = float(np.max(np.abs(got - d2_or) / np.abs(d2_or)))
+        line["max_rel_err_e2e_vs_oracle"] = float(np.max(np.abs(d2_host.numpy()[:npairs] - d2_or)
+                                                         / np.abs(d2_or)))
+        if extra:
+            extra["max_rel_err_fp64_multi"] = float(np.max(np.abs(np.array(extra["d2_fp64_multi"][:npairs])
+                                                                  - d2_or) / np.abs(d2_or)))
+            extra["max_rel_err_mixed"] = float(np.max(np.abs(np.array(extra["d2_mixed"][:npairs]) - d2_or)
+                                                     / np.abs(d2_or)))
+    if extra:
+        extra["multiple_mixed_vs_single_rhs_fp64"] = extra["mixed_multi_rhs_distances_per_s"] / value
+        extra["multiple_fp64_multi_vs_single_rhs_fp64"] = extra["fp64_multi_rhs_distances_per_s"] / value
+        del extra["d2_fp64_multi"], extra["d2_mixed"]
+        line["batched_comparison"] = extra
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

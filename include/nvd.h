@@ -222,12 +222,18 @@ const char *nvd_last_error(void);
  * made by nvd_ge_distance is bracketed by CUDA events on its stream;
  * nvd_profile_read returns the launch count, summed event time in ms and summed
  * algorithmic bytes of those launches since the last read (and resets them).
- * Class 0 = the SpMV/SpMM kernel.  Enabling forces the host-driven loop (no
- * persistent kernel) so launches can be bracketed.
+ * Class 0 = the SpMV/SpMM kernel.  Launches issued after every pair of a tile
+ * had converged (they find nothing to do) are dropped from the count.  Enabling
+ * forces the host-driven loop (no persistent kernel) so launches can be
+ * bracketed.
  */
 int nvd_profile_enable(int32_t on);
 int nvd_profile_read(int32_t kernel_class, int64_t *launches, double *total_ms,
                      double *bytes);
+
+/* nvd_kernel_launches -- number of kernels this library has launched in the
+ * process so far (all entry points, all devices). */
+int64_t nvd_kernel_launches(void);
 
 /* nvd_version -- library version string. */
 const char *nvd_version(void);

@@ -95,6 +95,7 @@ _SIGS = {
     "nvd_profile_read": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "nvd_version": (ctypes.c_char_p, []),
+    "nvd_kernel_launches": (ctypes.c_int64, []),
 }
 
 
@@ -355,6 +356,11 @@ def laplacian_apply(graph: Graph, x):
                                      _stream_ptr(X.device))
     _check(rc, "nvd_laplacian_apply")
     return Yt[0] if x.dim() == 1 else Yt
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().nvd_kernel_launches())
 
 
 def profile_enable(on: bool = True):

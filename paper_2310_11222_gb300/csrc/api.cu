@@ -1,4 +1,5 @@
 // C ABI: status strings, defaults, version and the SpMV/SpMM launch timer.
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -34,7 +35,31 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+std::atomic<int64_t> g_kernel_launches{0};
+
+void note_launch(int64_t n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
 bool prof_enabled() { return g_enabled; }
+
+size_t prof_mark() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_pending.size();
+}
+
+// Keep the first `keep` SpMV launches recorded after `mark`; the rest ran after
+// convergence and found no work.
+void prof_keep(size_t mark, int64_t keep) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (mark > g_pending.size()) return;
+    const size_t upto = mark + (size_t)(keep < 0 ? 0 : keep);
+    if (upto >= g_pending.size()) return;
+    for (size_t i = upto; i < g_pending.size(); ++i) {
+        cudaEventSynchronize(g_pending[i].b);
+        g_pool.push_back(g_pending[i].a);
+        g_pool.push_back(g_pending[i].b);
+    }
+    g_pending.resize(upto);
+}
 
 void prof_begin(cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -122,3 +147,5 @@ extern "C" void nvd_solve_opts_default(nvd_solve_opts *o) {
 }
 
 extern "C" const char *nvd_version(void) { return "nvd-gb300 0.1.0 (sm_103a)"; }
+
+extern "C" int64_t nvd_kernel_launches(void) { return g_kernel_launches.load(); }

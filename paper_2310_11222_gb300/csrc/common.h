@@ -11,20 +11,29 @@ constexpr int NWARP = NT / 32;
 
 // Sub-item budgets of the SpMV/SpMM for KT right-hand sides with vector/accumulator
 // element sizes szv/sza (shared by the host planner and the kernels).
-//   rows per sub-item: the row accumulators (rows x KT x sza) fit 8 KB, at most NT;
-//   entries per sub-item: KT = 1 stages 1024 products in shared memory, KT > 1
-//   gathers about 32 KB of neighbour rows.  Longer rows are split into chunks.
+//   KT = 1: a sub-item is up to 256 rows with at most 2048 entries, every row at
+//           most sp_row_max = 128 entries; one warp takes it, a group of G lanes
+//           per row.  A row with more entries, up to sp_long_max, is a sub-item of
+//           its own for a whole warp; longer rows are split into chunks of
+//           sp_chunk entries, one warp each.
+//   KT > 1: one CTA per sub-item; the row accumulators (rows x KT x sza) fit 8 KB
+//           (at most NT rows) and the entries gather about 32 KB of neighbour rows;
+//           longer rows are split into chunks of that many entries.
 constexpr int sp_rows_budget(int KT, int sza) {
-    return (8192 / (KT * sza)) > NT ? NT : (8192 / (KT * sza));
+    return KT == 1 ? 256 : ((8192 / (KT * sza)) > NT ? NT : (8192 / (KT * sza)));
 }
-constexpr int sp_nnz_budget(int KT, int szv) { return KT == 1 ? 1024 : 32768 / (KT * szv); }
+constexpr int sp_nnz_budget(int KT, int szv) { return KT == 1 ? 2048 : 32768 / (KT * szv); }
+constexpr int sp_row_max(int KT, int szv) { return KT == 1 ? 128 : 32768 / (KT * szv); }
+constexpr int sp_long_max(int KT) { return KT == 1 ? 8192 : 0; }
+constexpr int sp_chunk(int KT, int szv) { return KT == 1 ? 4096 : 32768 / (KT * szv); }
 // doubles of reduction scratch per CTA
 constexpr int red_doubles(int KT) { return (NWARP * 4 * KT) > 256 ? NWARP * 4 * KT : 256; }
 constexpr int vec_smem_bytes(int KT) { return (red_doubles(KT) + 4 * KT) * 8; }
 
 // Sub-item of the Laplacian SpMV/SpMM.
-//   kind 0: rows [r0, r1) of one segment whose entries fit one CTA pass.
-//   kind 1: entries [e0, e1) of a long row r0 split over several sub-items
+//   kind 0: rows [r0, r1) of one segment whose entries fit one pass.
+//   kind 2: one long row r0, entries [e0, e1), processed whole (KT = 1 only).
+//   kind 1: entries [e0, e1) of a very long row r0 split over several sub-items
 //           (merge-path style row splitting); this is chunk `hchunk` of `nchunk`;
 //           its partial row sum goes to hsum[hbase + hchunk] and the chunk that
 //           finishes last (counter hcount[hrow]) adds the chunks in chunk order,
@@ -97,6 +106,7 @@ struct Ctx {
     const struct Owner *owners;     // [n_owner] device table, or NULL = use own0
     int32_t n_owner;
     const int32_t *perm;            // internal -> user node (NULL = identity)
+    int32_t spmv_group;             // lanes per row of the single right-hand-side SpMV (2..32)
     // ---- persistent-kernel grid barrier
     unsigned *bar_count, *bar_gen;
     Owner own0;

@@ -359,6 +359,9 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     pl->sza = sza;
     const int RB = sp_rows_budget(KT, sza);
     const int64_t NB = sp_nnz_budget(KT, szv);
+    const int64_t RMAX = sp_row_max(KT, szv);
+    const int64_t LONG = sp_long_max(KT);
+    const int64_t CH = sp_chunk(KT, szv);
     const std::vector<int64_t> &rp = g->h_rowptr;
     const int nseg = g->nseg;
     std::vector<SpItem> items;
@@ -371,16 +374,27 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
         const int64_t re = g->h_seg_end[s];
         while (r < re) {
             const int64_t d = rp[r + 1] - rp[r];
-            if (d > NB) {
-                const int32_t nch = (int32_t)((d + NB - 1) / NB);
+            if (d > RMAX && d <= LONG) {
+                SpItem it{};
+                it.r0 = (int32_t)r;
+                it.r1 = (int32_t)(r + 1);
+                it.kind = 2;
+                it.e0 = rp[r];
+                it.e1 = rp[r + 1];
+                items.push_back(it);
+                ++r;
+                continue;
+            }
+            if (d > RMAX) {
+                const int32_t nch = (int32_t)((d + CH - 1) / CH);
                 for (int32_t c = 0; c < nch; ++c) {
                     SpItem it{};
                     it.r0 = (int32_t)r;
                     it.r1 = (int32_t)(r + 1);
                     it.kind = 1;
                     it.hrow = nheavy;
-                    it.e0 = rp[r] + (int64_t)c * NB;
-                    it.e1 = std::min(rp[r] + (int64_t)(c + 1) * NB, rp[r + 1]);
+                    it.e0 = rp[r] + (int64_t)c * CH;
+                    it.e1 = std::min(rp[r] + (int64_t)(c + 1) * CH, rp[r + 1]);
                     it.hbase = nchunks;
                     it.hchunk = c;
                     it.nchunk = nch;
@@ -395,7 +409,7 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
             int64_t cnt = 0;
             while (r < re && r - r0 < RB) {
                 const int64_t dd = rp[r + 1] - rp[r];
-                if (dd > NB) break;
+                if (dd > RMAX) break;
                 if (cnt + dd > NB && r > r0) break;
                 cnt += dd;
                 ++r;
@@ -523,6 +537,7 @@ void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c) {
     c->seg_end = g->seg_end.as<int64_t>();
     c->seg_owner = g->seg_owner.as<int32_t>();
     c->perm = g->perm.as<int32_t>();
+    c->spmv_group = g->spmv_group;
     if (pl) {
         set_sp_plan(c, pl);
         c->vblk = pl->vblk.as<Block>();
@@ -760,6 +775,14 @@ static int graph_create_impl(nvd_graph_t *out, int64_t n, int64_t nnz, const int
     }
     NVD_TRY(run_degree(g.get(), s));
     NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    // default group size of the single-RHS SpMV from the mean row length of the
+    // rows that belong to a segment (two entries per lane per pass)
+    {
+        int64_t rows = 0;
+        for (int s2 = 0; s2 < g->nseg; ++s2) rows += g->h_seg_end[s2] - g->h_seg_begin[s2];
+        const double mean = rows ? (double)g->nnz / (double)rows : 0.0;
+        g->spmv_group = mean <= 8 ? 1 : mean <= 16 ? 2 : mean <= 32 ? 4 : mean <= 64 ? 8 : 16;
+    }
     *out = g.release();
     return NVD_OK;
 }

@@ -78,6 +78,7 @@ struct nvd_graph_s {
     nvd::DevBuf perm;            // int32 internal -> user node; empty when identity
     nvd::DevBuf uent;            // int64 user entry -> internal entry (-1 dropped); empty when identity
     int32_t ncomp = 0, nseg = 0;
+    int32_t spmv_group = 4;      // lanes per row of the single-RHS SpMV (autotuned, see tune.cu)
     int64_t n_singleton = 0;
     std::vector<int64_t> h_rowptr, h_seg_begin, h_seg_end;
     nvd::DevBuf seg_begin, seg_end, seg_owner;

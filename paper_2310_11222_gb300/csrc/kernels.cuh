@@ -26,6 +26,11 @@ namespace dev {
 
 #define NVD_FULLMASK 0xffffffffu
 
+// Entries each lane keeps in flight per pass of the single-RHS SpMV row loop.
+#ifndef SPMV1_UNROLL
+#define SPMV1_UNROLL 2
+#endif
+
 // ------------------------------------------------------------------ loads/stores
 
 // Read-only data path: data not written by any CTA during the kernel.
@@ -434,10 +439,9 @@ struct SpCfg {
     static constexpr int NB = sp_nnz_budget(KT, (int)sizeof(TV));
     static constexpr int ND_MAX = 4;
     static constexpr int RED = red_doubles(KT);
-    static constexpr int SMEM = RB * KT * (int)sizeof(TA)            // s_acc
-                                + (KT == 1 ? NB * (int)sizeof(TA) : 0)  // s_prod
-                                + RED * 8                             // red
-                                + ND_MAX * KT * 8;                    // tot
+    static constexpr int SMEM = (KT == 1 ? 0 : RB * KT * (int)sizeof(TA))  // row accumulators
+                                + RED * 8                                 // red
+                                + ND_MAX * KT * 8;                        // tot
 };
 
 // Phase B of a sub-item: rows [r0, r1) with accumulated neighbour sums in s_acc.
@@ -461,16 +465,267 @@ __device__ __forceinline__ void spmm_epilogue(const Ctx &c, const Epi &epi, cons
     }
 }
 
+// One chunk [e0, e1) of a split row r0 (merge-path style row splitting): block-wide
+// partial row sum into hsum; the chunk that arrives last adds the chunks in chunk
+// order, applies the row epilogue and writes the row's partial slot.
+template <class LD, class TV, class TW, class TA, int KT, class Epi>
+__device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, const TV *__restrict__ src,
+                                           TV *__restrict__ dst, const SpItem &it, TA *s_acc, double *red) {
+    typedef SpCfg<TV, TA, KT> C;
+    constexpr int VEC = C::VEC, LPR = C::LPR, G = C::G, ND = Epi::ND;
+    const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // ---------------- chunk [e0, e1) of split row r0
+    const int64_t i = it.r0;
+    double *chunk = red;  // [KT] block total of this chunk
+    if constexpr (KT == 1) {
+        TA s = 0;
+        for (int64_t eb = (it.e0 & ~(int64_t)3) + 4 * threadIdx.x; eb < it.e1; eb += 4 * NT) {
+            const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(c.colidx + eb));
+            TW w4[4];
+            ld4_stream(w + eb, w4);
+            const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (eb + q >= it.e0 && eb + q < it.e1) s += (TA)w4[q] * (TA)LD::ld(src + cc[q]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(NVD_FULLMASK, s, off);
+        if (lane == 0) red[NT / 2 + warp] = (double)s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < NWARP; ++q) t += red[NT / 2 + q];
+            chunk[0] = t;
+        }
+    } else {
+        const int gi = lane / LPR, col0 = (lane % LPR) * VEC;
+        TA acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = 0;
+        for (int64_t e = it.e0 + warp * G + gi; e < it.e1; e += NWARP * G) {
+            const int ca = __ldcs(c.colidx + e);
+            const TA wa = (TA)__ldcs(w + e);
+            TV pa[VEC];
+            ldv<LD, TV, VEC>(src + (int64_t)ca * KT + col0, pa);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] += wa * (TA)pa[v];
+        }
+#pragma unroll
+        for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(NVD_FULLMASK, acc[v], off);
+        if (gi == 0) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) red[KT + warp * KT + col0 + v] = (double)acc[v];
+        }
+        __syncthreads();
+        if (threadIdx.x < KT) {
+            double t = 0.0;
+            for (int q = 0; q < NWARP; ++q) t += red[KT + q * KT + threadIdx.x];
+            chunk[threadIdx.x] = t;
+        }
+    }
+    __syncthreads();
+    __shared__ int s_fin;
+    if (threadIdx.x < KT) c.hsum[(int64_t)(it.hbase + it.hchunk) * KT + threadIdx.x] = chunk[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_fin = (atomicAdd(c.hcount + it.hrow, 1) == it.nchunk - 1);
+    __syncthreads();
+    if (s_fin) {
+        __threadfence();
+        if (threadIdx.x < KT) {
+            double t = 0.0;
+            for (int q = 0; q < it.nchunk; ++q)
+                t += __ldcg(c.hsum + (int64_t)(it.hbase + q) * KT + threadIdx.x);
+            s_acc[threadIdx.x] = (TA)t;
+        }
+        if (threadIdx.x == 0) atomicExch(c.hcount + it.hrow, 0);
+        __syncthreads();
+        double hdot[ND > 0 ? ND : 1][VEC];
+#pragma unroll
+        for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) hdot[d][v] = 0.0;
+        spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, src, dst, i, i + 1, s_acc, hdot);
+        if constexpr (ND > 0) {
+            constexpr int CG = KT / VEC;
+            if (threadIdx.x < CG) {
+                const int64_t hs = c.n_sblk + it.hrow;
+#pragma unroll
+                for (int d = 0; d < ND; ++d)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        c.part[((int64_t)d * c.part_stride + hs) * KT + threadIdx.x * VEC + v] = hdot[d][v];
+            }
+        }
+    }
+    __syncthreads();
+
+}
+
+// Whole-warp part of the single-RHS SpMV: one long row (kind 2) or one chunk of a
+// split row (kind 1).  Kept out of line so the short-row loop keeps few registers.
+template <class LD, class TV, class TW, class TA, class Epi>
+__device__ __noinline__ void spmv1_long(const Ctx &c, const Epi &epi, const TV *__restrict__ src,
+                                        TV *__restrict__ dst, const SpItem &it,
+                                        double (&dot)[Epi::ND > 0 ? Epi::ND : 1][1]) {
+    constexpr int ND = Epi::ND;
+    const int lane = threadIdx.x & 31;
+    const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
+    const TA *__restrict__ deg = deg_of<TA>(c);
+        const int64_t i = it.r0;
+        TA s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int64_t qb = (it.e0 & ~(int64_t)3) + 4 * lane; qb < it.e1; qb += 128) {
+            const int4 cq = __ldcs(reinterpret_cast<const int4 *>(c.colidx + qb));
+            TW wq[4];
+            ld4_stream(w + qb, wq);
+            const bool in0 = qb >= it.e0 && qb < it.e1, in1 = qb + 1 >= it.e0 && qb + 1 < it.e1;
+            const bool in2 = qb + 2 >= it.e0 && qb + 2 < it.e1, in3 = qb + 3 >= it.e0 && qb + 3 < it.e1;
+            if (in0) s0 += (TA)wq[0] * (TA)LD::ld(src + cq.x);
+            if (in1) s1 += (TA)wq[1] * (TA)LD::ld(src + cq.y);
+            if (in2) s2 += (TA)wq[2] * (TA)LD::ld(src + cq.z);
+            if (in3) s3 += (TA)wq[3] * (TA)LD::ld(src + cq.w);
+        }
+        TA sum = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(NVD_FULLMASK, sum, off);
+        if (it.kind == 2) {
+            if (lane == 0) {
+                TV own[1] = {LD::ld(src + i)};
+                const TA acc[1] = {sum};
+                epi.template elem<TV, TA, 1>(c, i, 0, 1, own, acc, __ldg(deg + i), dst, dot);
+            }
+        } else {
+            int fin = 0;
+            if (lane == 0) {
+                c.hsum[it.hbase + it.hchunk] = (double)sum;
+                __threadfence();
+                fin = (atomicAdd(c.hcount + it.hrow, 1) == it.nchunk - 1);
+            }
+            fin = __shfl_sync(NVD_FULLMASK, fin, 0);
+            if (fin && lane == 0) {
+                __threadfence();
+                double t = 0.0;
+                for (int q = 0; q < it.nchunk; ++q) t += __ldcg(c.hsum + it.hbase + q);
+                atomicExch(c.hcount + it.hrow, 0);
+                TV own[1] = {LD::ld(src + i)};
+                const TA acc[1] = {(TA)t};
+                double hdot[ND > 0 ? ND : 1][1];
+#pragma unroll
+                for (int d = 0; d < (ND > 0 ? ND : 1); ++d) hdot[d][0] = 0.0;
+                epi.template elem<TV, TA, 1>(c, i, 0, 1, own, acc, __ldg(deg + i), dst, hdot);
+                if constexpr (ND > 0) {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d)
+                        c.part[(int64_t)d * c.part_stride + c.n_sblk + it.hrow] = hdot[d][0];
+                }
+            }
+        }
+
+}
+
+// Single right-hand side (KT = 1) SpMV block.  Every warp walks the block's
+// sub-items; warps never wait for each other and use no shared memory, so many
+// independent load chains are in flight per SM:
+//   kind 0: up to 256 short rows shared by the 8 warps; each warp's 32/G groups of
+//           G lanes take one row each (G = c.spmv_group, chosen from the degree
+//           profile): the lanes
+//           stride over the row two entries at a time, a butterfly inside the
+//           group adds them and the group's first lane applies the row epilogue;
+//   kind 2: one long row for one warp (dealt round-robin), striding over it in
+//           16-byte quads;
+//   kind 1: one chunk of a split row for one warp: its sum goes to hsum, and the warp
+//           that completes the row last (hcount) adds the chunks in chunk order,
+//           applies the epilogue and writes the row's own partial slot.
+template <class LD, class TV, class TW, class TA, class Epi>
+__device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__ src, TV *__restrict__ dst,
+                            int64_t b, char *smem) {
+    constexpr int ND = Epi::ND;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *red = reinterpret_cast<double *>(smem);
+    double *tot = red + red_doubles(1);
+    const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
+    const TA *__restrict__ deg = deg_of<TA>(c);
+    const int G = c.spmv_group;
+    const int ngw = 32 / G, gl = lane & (G - 1), gid = lane / G;
+    const Block blk = c.sblk[b];
+    const int seg = blk.seg;
+    double dot[ND > 0 ? ND : 1][1];
+#pragma unroll
+    for (int d = 0; d < (ND > 0 ? ND : 1); ++d) dot[d][0] = 0.0;
+    const bool live = !Epi::NEEDS_LIVE || seg_live<1>(c, seg);
+    if (live) {
+        for (int64_t si = blk.i0; si < blk.i1; ++si) {
+            const SpItem it = c.items[si];
+            if (it.kind == 0) {
+                for (int64_t base = it.r0 + warp * ngw; base < it.r1; base += NWARP * ngw) {
+                    const int64_t i = base + gid;
+                    const bool valid = i < it.r1;
+                    constexpr int U = SPMV1_UNROLL;   // entries per lane in flight
+                    TA a[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) a[u] = 0;
+                    TV own[1] = {(TV)0};
+                    TA dg = 0;
+                    if (valid) {
+                        const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
+                        if (gl == 0) {
+                            own[0] = LD::ld(src + i);
+                            dg = __ldg(deg + i);
+                        }
+                        for (int64_t e = e0 + gl; e < e1; e += (int64_t)U * G) {
+                            int cu[U];
+                            TW wu[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const bool in = e + (int64_t)u * G < e1;
+                                cu[u] = in ? __ldcs(c.colidx + e + (int64_t)u * G) : -1;
+                                wu[u] = in ? __ldcs(w + e + (int64_t)u * G) : (TW)0;
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u)
+                                if (cu[u] >= 0) a[u] += (TA)wu[u] * (TA)LD::ld(src + cu[u]);
+                        }
+                    }
+                    TA acc = a[0];
+#pragma unroll
+                    for (int u = 1; u < U; ++u) acc += a[u];
+                    for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(NVD_FULLMASK, acc, off);
+                    if (valid && gl == 0) {
+                        const TA av[1] = {acc};
+                        epi.template elem<TV, TA, 1>(c, i, 0, 1, own, av, dg, dst, dot);
+                    }
+                }
+            } else if ((int)((si - blk.i0) % NWARP) == warp) {
+                spmv1_long<LD, TV, TW, TA, Epi>(c, epi, src, dst, it, dot);
+            }
+        }
+    }
+    if constexpr (ND > 0) {
+        block_reduce_cols<ND, 1, 1>(dot, red, tot);
+        const int64_t s0 = c.seg_sblk_off[seg];
+        const int32_t cnt = c.seg_sblk_off[seg + 1] - (int32_t)s0;
+        const int64_t h0 = c.n_sblk + c.seg_heavy_off[seg];
+        const int32_t hcnt = c.seg_heavy_off[seg + 1] - c.seg_heavy_off[seg];
+        seg_arrive<ND, 1>(c, epi.fin, seg, b, tot, s0, cnt, h0, hcnt, red);
+    }
+}
+
 // One SpMV/SpMM block b: its sub-items, then the segment arrival.
 template <class LD, class TV, class TW, class TA, int KT, class Epi>
 __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ src, TV *__restrict__ dst,
                            int64_t b, char *smem) {
+    if constexpr (KT == 1) {
+        spmv1_block<LD, TV, TW, TA, Epi>(c, epi, src, dst, b, smem);
+        return;
+    }
     typedef SpCfg<TV, TA, KT> C;
     constexpr int VEC = C::VEC, LPR = C::LPR, G = C::G, ND = Epi::ND;
     TA *s_acc = reinterpret_cast<TA *>(smem);
-    TA *s_prod = reinterpret_cast<TA *>(smem + C::RB * KT * sizeof(TA));
-    double *red = reinterpret_cast<double *>(smem + C::RB * KT * sizeof(TA) +
-                                             (KT == 1 ? C::NB * sizeof(TA) : 0));
+    double *red = reinterpret_cast<double *>(smem + C::RB * KT * sizeof(TA));
     double *tot = red + C::RED;
     const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -489,31 +744,7 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
             const SpItem it = c.items[si];
             if (it.kind == 0) {
                 // ---------------- phase A: neighbour sums of rows [r0, r1) into s_acc
-                if constexpr (KT == 1) {
-                    const int64_t e0 = __ldg(c.rowptr + it.r0), e1 = __ldg(c.rowptr + it.r1);
-                    for (int64_t eb = (e0 & ~(int64_t)3) + 4 * threadIdx.x; eb < e1; eb += 4 * NT) {
-                        const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(c.colidx + eb));
-                        TW w4[4];
-                        ld4_stream(w + eb, w4);
-                        const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-                        TA pv[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            pv[q] = (eb + q >= e0 && eb + q < e1) ? (TA)LD::ld(src + cc[q]) : (TA)0;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (eb + q >= e0 && eb + q < e1) s_prod[eb + q - e0] = (TA)w4[q] * pv[q];
-                    }
-                    __syncthreads();
-                    for (int64_t i = it.r0 + warp; i < it.r1; i += NWARP) {
-                        const int64_t a = __ldg(c.rowptr + i) - e0, z = __ldg(c.rowptr + i + 1) - e0;
-                        TA s = 0;
-                        for (int64_t k = a + lane; k < z; k += 32) s += s_prod[k];
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(NVD_FULLMASK, s, off);
-                        if (lane == 0) s_acc[i - it.r0] = s;
-                    }
-                } else {
+                {
                     const int gi = lane / LPR, col0 = (lane % LPR) * VEC;
                     for (int64_t i = it.r0 + warp; i < it.r1; i += NWARP) {
                         const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
@@ -555,94 +786,7 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
                 spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, src, dst, it.r0, it.r1, s_acc, dot);
                 __syncthreads();
             } else {
-                // ---------------- chunk [e0, e1) of split row r0
-                const int64_t i = it.r0;
-                double *chunk = red;  // [KT] block total of this chunk
-                if constexpr (KT == 1) {
-                    TA s = 0;
-                    for (int64_t eb = (it.e0 & ~(int64_t)3) + 4 * threadIdx.x; eb < it.e1; eb += 4 * NT) {
-                        const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(c.colidx + eb));
-                        TW w4[4];
-                        ld4_stream(w + eb, w4);
-                        const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (eb + q >= it.e0 && eb + q < it.e1) s += (TA)w4[q] * (TA)LD::ld(src + cc[q]);
-                    }
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(NVD_FULLMASK, s, off);
-                    if (lane == 0) red[NT / 2 + warp] = (double)s;
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
-                        double t = 0.0;
-                        for (int q = 0; q < NWARP; ++q) t += red[NT / 2 + q];
-                        chunk[0] = t;
-                    }
-                } else {
-                    const int gi = lane / LPR, col0 = (lane % LPR) * VEC;
-                    TA acc[VEC];
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[v] = 0;
-                    for (int64_t e = it.e0 + warp * G + gi; e < it.e1; e += NWARP * G) {
-                        const int ca = __ldcs(c.colidx + e);
-                        const TA wa = (TA)__ldcs(w + e);
-                        TV pa[VEC];
-                        ldv<LD, TV, VEC>(src + (int64_t)ca * KT + col0, pa);
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[v] += wa * (TA)pa[v];
-                    }
-#pragma unroll
-                    for (int off = LPR; off < 32; off <<= 1)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(NVD_FULLMASK, acc[v], off);
-                    if (gi == 0) {
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) red[KT + warp * KT + col0 + v] = (double)acc[v];
-                    }
-                    __syncthreads();
-                    if (threadIdx.x < KT) {
-                        double t = 0.0;
-                        for (int q = 0; q < NWARP; ++q) t += red[KT + q * KT + threadIdx.x];
-                        chunk[threadIdx.x] = t;
-                    }
-                }
-                __syncthreads();
-                __shared__ int s_fin;
-                if (threadIdx.x < KT) c.hsum[(int64_t)(it.hbase + it.hchunk) * KT + threadIdx.x] = chunk[threadIdx.x];
-                __threadfence();
-                __syncthreads();
-                if (threadIdx.x == 0)
-                    s_fin = (atomicAdd(c.hcount + it.hrow, 1) == it.nchunk - 1);
-                __syncthreads();
-                if (s_fin) {
-                    __threadfence();
-                    if (threadIdx.x < KT) {
-                        double t = 0.0;
-                        for (int q = 0; q < it.nchunk; ++q)
-                            t += __ldcg(c.hsum + (int64_t)(it.hbase + q) * KT + threadIdx.x);
-                        s_acc[threadIdx.x] = (TA)t;
-                    }
-                    if (threadIdx.x == 0) atomicExch(c.hcount + it.hrow, 0);
-                    __syncthreads();
-                    double hdot[ND > 0 ? ND : 1][VEC];
-#pragma unroll
-                    for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) hdot[d][v] = 0.0;
-                    spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, src, dst, i, i + 1, s_acc, hdot);
-                    if constexpr (ND > 0) {
-                        constexpr int CG = KT / VEC;
-                        if (threadIdx.x < CG) {
-                            const int64_t hs = c.n_sblk + it.hrow;
-#pragma unroll
-                            for (int d = 0; d < ND; ++d)
-#pragma unroll
-                                for (int v = 0; v < VEC; ++v)
-                                    c.part[((int64_t)d * c.part_stride + hs) * KT + threadIdx.x * VEC + v] = hdot[d][v];
-                        }
-                    }
-                }
-                __syncthreads();
+                spmm_chunk<LD, TV, TW, TA, KT, Epi>(c, epi, src, dst, it, s_acc, red);
             }
         }
     }
@@ -658,11 +802,13 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
 
 // ------------------------------------------------------------------ vector passes
 
-// Generic streaming pass over rows [i0, i1) of one segment.  Op provides
-// ND, setup(c, seg, col0) and elem(c, i, col0, dot).
+// Generic streaming pass over rows [i0, i1) of one segment.  Op provides ND,
+// NEEDS_LIVE, a register type R, setup(c, seg, col0), load(c, i, col0, R&) and
+// apply(c, i, col0, R&, dot).  Each thread handles U lane-vectors per trip with all
+// U loads issued before the first use.
 template <class TV, int KT, class Op>
 __device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
-    constexpr int VEC = VecCfg<TV, KT>::VEC, CG = KT / VEC, ND = Op::ND;
+    constexpr int VEC = VecCfg<TV, KT>::VEC, CG = KT / VEC, ND = Op::ND, U = 4;
     double *red = reinterpret_cast<double *>(smem);
     double *tot = red + red_doubles(KT);
     const Block blk = c.vblk[b];
@@ -676,7 +822,19 @@ __device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
     if (!Op::NEEDS_LIVE || seg_live<KT>(c, seg)) {
         op.setup(c, seg, col0);
         const int64_t t1 = blk.i1 * CG;
-        for (int64_t t = blk.i0 * CG + threadIdx.x; t < t1; t += NT) op.elem(c, t / CG, col0, dot);
+        for (int64_t t = blk.i0 * CG + threadIdx.x; t < t1; t += (int64_t)NT * U) {
+            typename Op::R regs[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t tu = t + (int64_t)u * NT;
+                if (tu < t1) op.load(c, tu / CG, col0, regs[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t tu = t + (int64_t)u * NT;
+                if (tu < t1) op.apply(c, tu / CG, col0, regs[u], dot);
+            }
+        }
     }
     if constexpr (ND > 0) {
         block_reduce_cols<ND, KT, VEC>(dot, red, tot);
@@ -692,6 +850,7 @@ template <class TX, int KT>
 struct OpFormDelta {
     static constexpr int ND = 1, VEC = VecCfg<double, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
+    struct R { double d[VEC]; };
     double *delta;
     FinMean fin;
     const TX *X, *Y;
@@ -705,16 +864,18 @@ struct OpFormDelta {
         ld = o.ld;
         kc = o.kc;
     }
-    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&dot)[1][VEC]) const {
+    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &r) const {
         const int64_t u = (c.perm ? (int64_t)__ldg(c.perm + i) : i) - base;
-        double dl[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             const int j = col0 + v;
-            dl[v] = j < kc ? (double)__ldg(X + (int64_t)j * ld + u) - (double)__ldg(Y + (int64_t)j * ld + u) : 0.0;
-            dot[0][v] += dl[v];
+            r.d[v] = j < kc ? (double)__ldg(X + (int64_t)j * ld + u) - (double)__ldg(Y + (int64_t)j * ld + u) : 0.0;
         }
-        stv(delta + i * KT + col0, dl);
+    }
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &r, double (&dot)[1][VEC]) const {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) dot[0][v] += r.d[v];
+        stv(delta + i * KT + col0, r.d);
     }
 };
 
@@ -724,6 +885,7 @@ template <class TV, int KT, class LD = LdPlain>
 struct OpInit {
     static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
+    struct R { double s[VEC]; TV di; };
     const double *src;
     double *writeback;
     TV *x, *r, *p;
@@ -733,22 +895,23 @@ struct OpInit {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) mu[v] = __ldcg(c.mean + (int64_t)seg * KT + col0 + v);
     }
-    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&dot)[2][VEC]) const {
+    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &q) const {
+        ldv<LD, double, VEC>(src + i * KT + col0, q.s);
+        q.di = __ldg(dinv_of<TV>(c) + i);
+    }
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &q, double (&dot)[2][VEC]) const {
         const int64_t o = i * KT + col0;
-        double s[VEC];
-        ldv<LD, double, VEC>(src + o, s);
-        const TV di = __ldg(dinv_of<TV>(c) + i);
         TV rv[VEC], uv[VEC], zv[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            s[v] -= mu[v];
-            rv[v] = (TV)s[v];
-            uv[v] = di * rv[v];
+            q.s[v] -= mu[v];
+            rv[v] = (TV)q.s[v];
+            uv[v] = q.di * rv[v];
             zv[v] = (TV)0;
             dot[0][v] += (double)rv[v] * (double)uv[v];
             dot[1][v] += (double)rv[v] * (double)rv[v];
         }
-        if (writeback) stv(writeback + o, s);
+        if (writeback) stv(writeback + o, q.s);
         stv(r + o, rv);
         stv(p + o, uv);
         stv(x + o, zv);
@@ -760,6 +923,7 @@ template <class TV, int KT, class LD = LdPlain>
 struct OpUpdate {
     static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = true;
+    struct R { TV x[VEC], r[VEC], p[VEC], q[VEC]; TV di; };
     TV *x, *r;
     const TV *p, *q;
     FinBeta fin;
@@ -768,24 +932,26 @@ struct OpUpdate {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) al[v] = (TV)__ldcg(c.alpha + (int64_t)seg * KT + col0 + v);
     }
-    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&dot)[2][VEC]) const {
+    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &g) const {
         const int64_t o = i * KT + col0;
-        TV xv[VEC], rv[VEC], pv[VEC], qv[VEC];
-        ldv<LD, TV, VEC>(x + o, xv);
-        ldv<LD, TV, VEC>(r + o, rv);
-        ldv<LD, TV, VEC>(p + o, pv);
-        ldv<LD, TV, VEC>(q + o, qv);
-        const TV di = __ldg(dinv_of<TV>(c) + i);
+        ldv<LD, TV, VEC>(x + o, g.x);
+        ldv<LD, TV, VEC>(r + o, g.r);
+        ldv<LD, TV, VEC>(p + o, g.p);
+        ldv<LD, TV, VEC>(q + o, g.q);
+        g.di = __ldg(dinv_of<TV>(c) + i);
+    }
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&dot)[2][VEC]) const {
+        const int64_t o = i * KT + col0;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            xv[v] += al[v] * pv[v];
-            rv[v] -= al[v] * qv[v];
-            const TV u = di * rv[v];
-            dot[0][v] += (double)rv[v] * (double)u;
-            dot[1][v] += (double)rv[v] * (double)rv[v];
+            g.x[v] += al[v] * g.p[v];
+            g.r[v] -= al[v] * g.q[v];
+            const TV u = g.di * g.r[v];
+            dot[0][v] += (double)g.r[v] * (double)u;
+            dot[1][v] += (double)g.r[v] * (double)g.r[v];
         }
-        stv(x + o, xv);
-        stv(r + o, rv);
+        stv(x + o, g.x);
+        stv(r + o, g.r);
     }
 };
 
@@ -794,6 +960,7 @@ template <class TV, int KT, class LD = LdPlain>
 struct OpDir {
     static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = true;
+    struct R { TV r[VEC], p[VEC]; TV di; };
     const TV *r;
     TV *p;
     FinNone fin;
@@ -806,15 +973,16 @@ struct OpDir {
             act[v] = __ldcg(c.active + (int64_t)seg * KT + col0 + v) != 0;
         }
     }
-    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&)[1][VEC]) const {
+    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &g) const {
         const int64_t o = i * KT + col0;
-        TV rv[VEC], pv[VEC];
-        ldv<LD, TV, VEC>(r + o, rv);
-        ldv<LD, TV, VEC>(p + o, pv);
-        const TV di = __ldg(dinv_of<TV>(c) + i);
+        ldv<LD, TV, VEC>(r + o, g.r);
+        ldv<LD, TV, VEC>(p + o, g.p);
+        g.di = __ldg(dinv_of<TV>(c) + i);
+    }
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) pv[v] = act[v] ? di * rv[v] + be[v] * pv[v] : pv[v];
-        stv(p + o, pv);
+        for (int v = 0; v < VEC; ++v) g.p[v] = act[v] ? g.di * g.r[v] + be[v] * g.p[v] : g.p[v];
+        stv(p + i * KT + col0, g.p);
     }
 };
 
@@ -823,20 +991,21 @@ template <class TV, int KT, class LD = LdPlain>
 struct OpFinal {
     static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
+    struct R { TV x[VEC]; double d[VEC]; };
     const TV *x;
     const double *delta;
     FinFinal fin;
     __device__ void setup(const Ctx &, int, int) {}
-    __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, double (&dot)[2][VEC]) const {
+    __device__ __forceinline__ void load(const Ctx &, int64_t i, int col0, R &g) const {
         const int64_t o = i * KT + col0;
-        TV xv[VEC];
-        double dl[VEC];
-        ldv<LD, TV, VEC>(x + o, xv);
-        ldv<LD, double, VEC>(delta + o, dl);
+        ldv<LD, TV, VEC>(x + o, g.x);
+        ldv<LD, double, VEC>(delta + o, g.d);
+    }
+    __device__ __forceinline__ void apply(const Ctx &, int64_t, int, R &g, double (&dot)[2][VEC]) const {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            dot[0][v] += (double)xv[v];
-            dot[1][v] += dl[v] * (double)xv[v];
+            dot[0][v] += (double)g.x[v];
+            dot[1][v] += g.d[v] * (double)g.x[v];
         }
     }
 };
@@ -846,6 +1015,7 @@ template <class TS, class TZ, int KT, class LD = LdPlain>
 struct OpZout {
     static constexpr int ND = 0, VEC = VecCfg<TS, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
+    struct R { TS s[VEC]; };
     const TS *src;
     const double *meanv;
     FinNone fin;
@@ -862,15 +1032,16 @@ struct OpZout {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) mu[v] = __ldcg(meanv + (int64_t)seg * KT + col0 + v);
     }
-    __device__ __forceinline__ void elem(const Ctx &c, int64_t i, int col0, double (&)[1][VEC]) const {
+    __device__ __forceinline__ void load(const Ctx &, int64_t i, int col0, R &g) const {
+        ldv<LD, TS, VEC>(src + i * KT + col0, g.s);
+    }
+    __device__ __forceinline__ void apply(const Ctx &c, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
         if (!Z) return;
         const int64_t u = (c.perm ? (int64_t)__ldg(c.perm + i) : i) - base;
-        TS sv[VEC];
-        ldv<LD, TS, VEC>(src + i * KT + col0, sv);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             const int j = col0 + v;
-            if (j < kc) Z[(int64_t)j * ld + u] = (TZ)((double)sv[v] - mu[v]);
+            if (j < kc) Z[(int64_t)j * ld + u] = (TZ)((double)g.s[v] - mu[v]);
         }
     }
 };
@@ -880,19 +1051,20 @@ template <class TV, int KT, class LD = LdPlain>
 struct OpAccum {
     static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
+    struct R { TV x[VEC]; double z[VEC]; };
     const TV *x;
     double *z;
     FinNone fin;
     __device__ void setup(const Ctx &, int, int) {}
-    __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, double (&)[1][VEC]) const {
+    __device__ __forceinline__ void load(const Ctx &, int64_t i, int col0, R &g) const {
         const int64_t o = i * KT + col0;
-        TV xv[VEC];
-        ldv<LD, TV, VEC>(x + o, xv);
-        double zv[VEC];
-        ldv<LD, double, VEC>(z + o, zv);
+        ldv<LD, TV, VEC>(x + o, g.x);
+        ldv<LD, double, VEC>(z + o, g.z);
+    }
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) zv[v] += (double)xv[v];
-        stv(z + o, zv);
+        for (int v = 0; v < VEC; ++v) g.z[v] += (double)g.x[v];
+        stv(z + i * KT + col0, g.z);
     }
 };
 

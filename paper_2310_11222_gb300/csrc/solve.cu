@@ -31,6 +31,7 @@ static int permute_vector(const void *src, void *dst, const int32_t *perm, int64
         k_permute<double><<<grid, 256, 0, s>>>((const double *)src, (double *)dst, perm, n, gather);
     else
         k_permute<float><<<grid, 256, 0, s>>>((const float *)src, (float *)dst, perm, n, gather);
+    note_launch();
     NVD_TRY_CUDA(cudaGetLastError());
     return NVD_OK;
 }
@@ -151,6 +152,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.rtol2 = o.rtol * o.rtol;
         c.max_iter = o.max_iter;
         int steps = 0, conv = 1;
+        const size_t pmark = prof_enabled() ? prof_mark() : 0;
         if (o.mode == NVD_MODE_FP64)
             NVD_TRY(run_tile_fp64(g, c, w, o, io, s, KT, xdt));
         else if (o.mode == NVD_MODE_FP32)
@@ -160,9 +162,16 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         NVD_TRY(run_collect(c, KT, w.res, d2_dev ? d2_out + c0 : nullptr, 0, 1, s));
         if (host_in && z_out)
             NVD_TRY_CUDA(cudaMemcpyAsync((char *)z_out + off, sz, (size_t)kc * g->n * xsz, cudaMemcpyDeviceToHost, s));
-        if (need_host) {
+        if (need_host || prof_enabled()) {
             NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), w.res, KT * sizeof(ColResult), cudaMemcpyDeviceToHost, s));
             NVD_TRY_CUDA(cudaStreamSynchronize(s));
+            if (prof_enabled() && !mixed) {
+                int real = 0;
+                for (int j = 0; j < kc; ++j) real = std::max(real, res[j].iters);
+                prof_keep(pmark, real);
+            }
+        }
+        if (need_host) {
             for (int j = 0; j < kc; ++j) {
                 ColResult &r = res[j];
                 if (mixed) r.status = conv ? NVD_OK : NVD_ERR_NOT_CONVERGED;

@@ -39,6 +39,7 @@ int run_collect(const Ctx &c, int KT, ColResult *res, double *d2dev, int64_t d2_
         case 32: k_collect<32><<<grid, 128, 0, s>>>(c, res, d2dev, d2_stride); break;
         default: set_error("unsupported tile width %d", KT); return NVD_ERR_INVALID_ARG;
     }
+    note_launch();
     NVD_TRY_CUDA(cudaGetLastError());
     return NVD_OK;
 }

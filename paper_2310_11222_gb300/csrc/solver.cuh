@@ -62,6 +62,9 @@ __global__ void k_collect(Ctx c, ColResult *res, double *d2dev, int64_t d2_strid
 bool prof_enabled();
 void prof_begin(cudaStream_t s);
 void prof_end(cudaStream_t s, double bytes);
+size_t prof_mark();
+void prof_keep(size_t mark, int64_t keep);
+void note_launch(int64_t n = 1);
 
 // ------------------------------------------------------------------ workspace
 
@@ -123,6 +126,7 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
     const bool prof = prof_enabled();
     if (prof) prof_begin(s);
     k_spmm<TV, TW, TA, KT, Epi><<<(unsigned)c.n_sblk, NT, 0, s>>>(c, epi, src, dst);
+    note_launch();
     if (prof) prof_end(s, bytes);
     NVD_TRY_CUDA(cudaGetLastError());
     return NVD_OK;
@@ -132,6 +136,7 @@ template <class TV, int KT, class Op>
 inline int launch_vec(const Ctx &c, const Op &op, cudaStream_t s) {
     if (c.n_vblk == 0) return NVD_OK;
     k_vec<TV, KT, Op><<<(unsigned)c.n_vblk, NT, 0, s>>>(c, op);
+    note_launch();
     NVD_TRY_CUDA(cudaGetLastError());
     return NVD_OK;
 }
@@ -294,6 +299,7 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
         oa.x = x; oa.z = w.z64;
         NVD_TRY((launch_vec<float, KT>(c, oa, s)));
         k_collect<KT><<<1, 128, 0, s>>>(c, w.res, nullptr, 0);
+        note_launch();
         NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), w.res, KT * sizeof(ColResult), cudaMemcpyDeviceToHost, s));
         NVD_TRY_CUDA(cudaStreamSynchronize(s));
         for (int j = 0; j < KT; ++j) {
@@ -306,6 +312,7 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
         er.fin.KT = KT;
         NVD_TRY((launch_spmm<double, TWN, double, KT>(cr, er, w.z64, w.r64, s, bytes64)));
         k_collect<KT><<<1, 128, 0, s>>>(c, w.res, nullptr, 0);
+        note_launch();
         NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), w.res, KT * sizeof(ColResult), cudaMemcpyDeviceToHost, s));
         NVD_TRY_CUDA(cudaStreamSynchronize(s));
         ++step;
