@@ -121,4 +121,13 @@ struct ColResult {
     int32_t status;
 };
 
+// Buffers of one persistent (single-launch) tile solve.
+struct PersistArgs {
+    double *delta;
+    void *x, *r, *p, *q;
+    ColResult *res;      // [n_owner][KT]
+    int n_owner;
+    int write_z;
+};
+
 }  // namespace nvd

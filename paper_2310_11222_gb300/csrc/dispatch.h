@@ -22,6 +22,10 @@ int run_tile_fp32(nvd_graph_s *g, const Ctx &c, SolveWs &w, const nvd_solve_opts
 int run_tile_mixed(nvd_graph_s *g, const Ctx &c, const Plan *pl64, SolveWs &w, const nvd_solve_opts &o,
                    const TileIO &io, cudaStream_t s, int KT, int xdt, std::vector<int> &iters,
                    std::vector<double> &relres, int *steps, int *conv);
+// One persistent cooperative launch solving a whole tile (FP64 or FP32 mode);
+// c.owners / c.own0 describe the owners, a the buffers.
+int run_persistent(nvd_graph_s *g, const Ctx &c, const PersistArgs &a, int mode, int KT, int xdt,
+                   cudaStream_t s);
 // k_collect<KT> launch.
 int run_collect(const Ctx &c, int KT, ColResult *res, double *d2dev, int64_t d2_stride,
                 int n_owner, cudaStream_t s);

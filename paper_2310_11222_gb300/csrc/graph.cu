@@ -8,6 +8,7 @@
 // node range, relabels the nodes so that every component is one -- the solver
 // then treats each component as an independent "segment".
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -344,6 +345,11 @@ int run_components(nvd_graph_s *g, std::vector<int32_t> &root, cudaStream_t s) {
 
 int target_blocks(const nvd_graph_s *g) { return 2 * g->num_sms * 8; }
 
+uint64_t next_graph_id() {
+    static std::atomic<uint64_t> ctr{1};
+    return ctr.fetch_add(1);
+}
+
 // ------------------------------------------------------------------ plans
 
 int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
@@ -589,6 +595,7 @@ static int graph_create_impl(nvd_graph_t *out, int64_t n, int64_t nnz, const int
     }
     const bool dev = flags & NVD_GRAPH_DEVICE_PTRS;
     std::unique_ptr<nvd_graph_s> g(new nvd_graph_s());
+    g->id = next_graph_id();
     NVD_TRY_CUDA(cudaGetDevice(&g->device));
     NVD_TRY_CUDA(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
     g->n = n;

@@ -67,6 +67,7 @@ struct Plan {
 }  // namespace nvd
 
 struct nvd_graph_s {
+    uint64_t id = 0;             // unique per handle (cache keys)
     int device = 0;
     int num_sms = 0;
     int64_t n = 0, nnz = 0;      // after cleaning (self-loops dropped, repeats merged)
@@ -102,5 +103,7 @@ void set_sp_plan(Ctx *c, const Plan *pl);
 
 // Blocks per kernel launch the planner aims for (about two waves of 8 CTAs per SM).
 int target_blocks(const nvd_graph_s *g);
+// Fresh handle id.
+uint64_t next_graph_id();
 
 }  // namespace nvd

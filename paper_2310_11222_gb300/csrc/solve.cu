@@ -113,6 +113,17 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.part = w.part;
         c.hsum = w.hsum;
     }
+    // persistent single-launch solve (FP64/FP32 modes; the launch timer needs the host loop)
+    const bool persistent = (o.flags & NVD_SOLVE_PERSISTENT) && !mixed && !prof_enabled();
+    const int64_t sk = (int64_t)std::max(g->nseg, 1) * KT;
+    unsigned *bar = nullptr;
+    if (persistent) {
+        int st = NVD_OK;
+        bar = (unsigned *)g->wsp("bar", 16, &st);
+        if (st) return st;
+        c.bar_count = bar;
+        c.bar_gen = bar + 1;
+    }
     // staging for host inputs/outputs
     void *sx = nullptr, *sy = nullptr, *sz = nullptr;
     if (host_in) {
@@ -153,7 +164,12 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.max_iter = o.max_iter;
         int steps = 0, conv = 1;
         const size_t pmark = prof_enabled() ? prof_mark() : 0;
-        if (o.mode == NVD_MODE_FP64)
+        if (persistent) {
+            NVD_TRY_CUDA(cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 8) * 4, s));
+            NVD_TRY_CUDA(cudaMemsetAsync(bar, 0, 16, s));
+            PersistArgs a{w.delta, w.x, w.r, w.p, w.q, w.res, 1, io.z ? 1 : 0};
+            NVD_TRY(run_persistent(g, c, a, o.mode, KT, xdt, s));
+        } else if (o.mode == NVD_MODE_FP64)
             NVD_TRY(run_tile_fp64(g, c, w, o, io, s, KT, xdt));
         else if (o.mode == NVD_MODE_FP32)
             NVD_TRY(run_tile_fp32(g, c, w, o, io, s, KT, xdt));

@@ -1,0 +1,122 @@
+"""Batched persistent solve (many graphs, one cooperative launch in a CUDA graph) and
+the persistent single-graph solve, against the oracle and the host-driven path."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cg as ocg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def nvd():
+    import paper_2310_11222_gb300 as m
+    m.load_library()
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
+
+
+def on(x, dtype=torch.float64):
+    return torch.as_tensor(x, dtype=dtype, device=DEV)
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    graphs = [synth.workloads.batched_graph(gi, scale=0.02) for gi in list(range(4)) + list(range(32, 36))]
+    pairs = []
+    for gi, g in zip(list(range(4)) + list(range(32, 36)), graphs):
+        pairs.append(synth.workloads.batched_pairs(g, gi))
+    want = []
+    for g, (X, Y) in zip(graphs, pairs):
+        d2, it, _ = ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X, Y, rtol=1e-12)
+        assert np.all(it >= 0)
+        want.append(d2)
+    return graphs, pairs, want
+
+
+@pytest.mark.parametrize("mode,rtol,tol", [(0, 1e-10, 1e-8), (1, 1e-6, 1e-4)])
+def test_batched_matches_oracle(nvd, small_batch, mode, rtol, tol):
+    graphs, pairs, want = small_batch
+    G = [nvd.Graph.from_csr(g) for g in graphs]
+    xs = [on(X) for X, _ in pairs]
+    ys = [on(Y) for _, Y in pairs]
+    d2, st = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, return_stats=True)
+    d2 = d2.numpy()
+    off = 0
+    for w in want:
+        assert rel(d2[off:off + len(w)], w) < tol
+        off += len(w)
+    assert all(s["status"] == 0 for s in st)
+    # replaying the captured launch gives the identical answer
+    d2b = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol).numpy()
+    assert np.array_equal(d2, d2b)
+
+
+def test_batched_equals_independent_solves(nvd, small_batch):
+    graphs, pairs, _ = small_batch
+    G = [nvd.Graph.from_csr(g) for g in graphs]
+    xs = [on(X) for X, _ in pairs]
+    ys = [on(Y) for _, Y in pairs]
+    d2 = nvd.ge_distance_batched(G, xs, ys, mode=nvd.MODE_FP64, rtol=1e-10).numpy()
+    off = 0
+    for g, x, y in zip(G, xs, ys):
+        one = nvd.ge_distance(g, x, y, rtol=1e-10, kt=32 if False else 16).cpu().numpy()
+        assert rel(d2[off:off + len(one)], one) < 1e-9
+        off += len(one)
+
+
+def test_batched_uneven_pair_counts_and_multiple_tiles(nvd, small_batch):
+    graphs, pairs, want = small_batch
+    G = [nvd.Graph.from_csr(g) for g in graphs[:3]]
+    ks = [5, 32, 17]
+    xs = [on(pairs[i][0][:k]) for i, k in enumerate(ks)]
+    ys = [on(pairs[i][1][:k]) for i, k in enumerate(ks)]
+    for kt in (0, 8):
+        import ctypes  # noqa: F401
+        d2 = nvd.ge_distance_batched(G, xs, ys, mode=nvd.MODE_FP64, rtol=1e-10).numpy()
+        off = 0
+        for i, k in enumerate(ks):
+            assert rel(d2[off:off + k], want[i][:k]) < 1e-8
+            off += k
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("kt", [1, 8, 32])
+def test_persistent_single_graph_bitwise_equals_host_loop(nvd, mode, kt):
+    wl = synth.workload_ba_small()
+    g = wl.graph
+    X, Y = wl.pairs(0, 12)
+    G = nvd.Graph.from_csr(g)
+    if mode == 0 and kt == 32:
+        kt = 16
+    a, za = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, return_z=True)
+    b, zb = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, persistent=True, return_z=True)
+    assert torch.equal(a, b)
+    assert torch.equal(za, zb)
+
+
+@pytest.mark.slow
+def test_batched_full_size_sampled(nvd):
+    """The 64-graph batch (node counts log-uniform in [1e3, 2e5]; 32 BA, 32 WS), 32 pairs
+    each, FP32 vectors with FP64 reductions: every d^2 finite and positive, and a sample
+    of graphs against the FP64 oracle at the unrefined-FP32 tolerance 1e-4."""
+    wl = synth.workload_batched()
+    X, Y = wl.pairs(0, 32)
+    G = [nvd.Graph.from_csr(g) for g in wl.graphs]
+    xs = [on(x) for x in X]
+    ys = [on(y) for y in Y]
+    d2, st = nvd.ge_distance_batched(G, xs, ys, mode=nvd.MODE_FP32, rtol=1e-6, return_stats=True)
+    d2 = d2.numpy()
+    assert np.all(np.isfinite(d2)) and np.all(d2 > 0)
+    for gi in (0, 7, 33, 63):
+        g = wl.graphs[gi]
+        want, it, _ = ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), X[gi], Y[gi], rtol=1e-10)
+        assert rel(d2[32 * gi:32 * gi + 32], want) < 1e-4
