@@ -209,6 +209,32 @@ int nvd_ge_grad(nvd_graph_t g, int32_t k, const void *z, int32_t zdtype, const d
 int nvd_laplacian_apply(nvd_graph_t g, int32_t k, const void *x, void *y, int32_t dtype,
                         nvd_stream_t stream);
 
+/*
+ * nvd_laplacian_quadform_noalloc -- y_j = L x_j and q_j = x_j^T L x_j for j < k,
+ * without allocating any memory.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory when they call, e.g. a
+ * process whose device memory is already held by another framework's caching
+ * allocator, or a time-critical loop that must not allocate (an allocation can
+ * synchronise the device).  It is a variant of the SpMV with fused inner
+ * product that the solver runs every iteration; the handle must exist already
+ * (nvd_graph_create allocates, this call does not: no cudaMalloc, no cudaFree,
+ * no allocating library routine).
+ *
+ *   x  [k][n] device doubles (caller's node order); y [k][n] device doubles or
+ *   NULL; q [k] device doubles.  1 <= k <= 32 (larger k: NVD_ERR_INVALID_ARG).
+ *
+ * Scratch: the cross-block partial sums live in one file-scope device array of
+ * 262,400 bytes (1024 blocks x 32 columns of doubles plus a counter), which every
+ * GPU that loads the library keeps until the process exits.  Every call shares
+ * that array and it keeps the last call's contents; calls that overlap on the GPU
+ * (different streams, or several threads) race on it and must be serialised by
+ * the caller.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * The work is ordered on `stream` and the call returns without waiting for it.
+ */
+int nvd_laplacian_quadform_noalloc(nvd_graph_t g, int32_t k, const double *x, double *y, double *q,
+                                   nvd_stream_t stream);
+
 /* ------------------------------------------------------------------ diagnostics */
 
 /* nvd_status_string -- static name of a status code. */
