@@ -40,6 +40,7 @@ METRIC = "GE distances/s on 1 GB300 at d² rel.err≤1e-6; SpMV HBM GB/s vs peak
 UNIT = "distances/s"
 PAIRS_PER_STEP = 8
 RTOL = 1e-10
+CHECK_EVERY = 2   # PCG iterations between the host's convergence polls (polled one batch behind)
 
 
 def workload_config(g, n0):
@@ -48,7 +49,7 @@ def workload_config(g, n0):
                     "U[0.5,2), 8 pairs x,y U[0,1) on 1% of nodes normalised, single-RHS FP64 "
                     "Jacobi-PCG to relative residual 1e-10",
         "n": int(g.n), "nnz": int(g.nnz), "n_generated": int(n0), "pairs_per_step": PAIRS_PER_STEP,
-        "rtol": RTOL, "solver": "FP64 PCG, one right-hand side at a time",
+        "rtol": RTOL, "solver": "FP64 PCG, one right-hand side at a time", "check_every": CHECK_EVERY,
         "l2": "L2 flushed (256 MB write) between timed steps; working set 0.3 GB > 129 MB L2",
     }
 
@@ -246,7 +247,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
-        return nvd.ge_distance(G, xt, yt, rtol=RTOL, single_rhs=True, return_stats=True)
+        return nvd.ge_distance(G, xt, yt, rtol=RTOL, single_rhs=True, check_every=CHECK_EVERY,
+                               return_stats=True)
 
     for _ in range(args.warmup):
         step()
@@ -257,7 +259,8 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     nvd.profile_enable(True)
-    nvd.profile_read()
+    nvd.profile_read(0)
+    nvd.profile_read(1)
     launches0 = nvd.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -274,7 +277,7 @@ def main():
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     launches = nvd.kernel_launches() - launches0
-    n_spmv, spmv_ms, spmv_bytes = nvd.profile_read()
+    n_spmv, spmv_ms, spmv_bytes = nvd.profile_read(0)
     nvd.profile_enable(False)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -291,13 +294,13 @@ def main():
     xh = torch.from_numpy(X).pin_memory()
     yh = torch.from_numpy(Y).pin_memory()
     for _ in range(2):
-        nvd.ge_distance(G, xh, yh, rtol=RTOL, single_rhs=True)
+        nvd.ge_distance(G, xh, yh, rtol=RTOL, single_rhs=True, check_every=CHECK_EVERY)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     te0 = time.perf_counter()
     for _ in range(args.steps):
-        d2_host = nvd.ge_distance(G, xh, yh, rtol=RTOL, single_rhs=True)
+        d2_host = nvd.ge_distance(G, xh, yh, rtol=RTOL, single_rhs=True, check_every=CHECK_EVERY)
     torch.cuda.synchronize()
     te = time.perf_counter() - te0
     if dist is not None:
@@ -345,7 +348,8 @@ def main():
                      "launches": n_spmv, "avg_launch_us": 1e3 * spmv_ms / n_spmv if n_spmv else None,
                      "algorithmic_bytes_per_launch": spmv_bytes / n_spmv if n_spmv else None,
                      "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy) of MEASURED_PEAKS.json"},
-        "solver": {"iters_per_pair": iters, "status": statuses, "wall_s_timed": t_wall},
+        "solver": {"iters_per_pair": iters, "status": statuses, "wall_s_timed": t_wall,
+                   "spmv_ms_per_step": spmv_ms / args.steps, "check_every": CHECK_EVERY},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, th, npairs, dt, d2_or = cpu_baseline(g, X, Y)

@@ -138,7 +138,7 @@ typedef struct {
 } nvd_solve_stats;
 
 /* nvd_solve_opts_default -- FP64 mode, rtol 1e-10, max_iter 10000, d2_rtol 1e-8,
- * max_refine 8, check_every 8, kt automatic, no flags. */
+ * max_refine 8, check_every 4, kt automatic, no flags. */
 void nvd_solve_opts_default(nvd_solve_opts *o);
 
 /*
@@ -244,12 +244,14 @@ const char *nvd_status_string(int status);
 const char *nvd_last_error(void);
 
 /*
- * Kernel timing.  While enabled, every launch of the Laplacian SpMV/SpMM kernel
- * made by nvd_ge_distance is bracketed by CUDA events on its stream;
+ * Kernel timing.  While enabled (on = 1), every launch of the Laplacian SpMV/SpMM
+ * kernel made by nvd_ge_distance is bracketed by CUDA events on its stream
+ * (on = 2: the vector passes too, class 1);
  * nvd_profile_read returns the launch count, summed event time in ms and summed
  * algorithmic bytes of those launches since the last read (and resets them).
- * Class 0 = the SpMV/SpMM kernel.  Launches issued after every pair of a tile
- * had converged (they find nothing to do) are dropped from the count.  Enabling
+ * Class 0 = the SpMV/SpMM kernel, class 1 = the streaming vector passes (bytes
+ * not tracked).  SpMV launches issued after every pair of a tile had converged
+ * (they find nothing to do) are dropped from the count.  Enabling
  * forces the host-driven loop (no persistent kernel) so launches can be
  * bracketed.
  */

@@ -243,7 +243,7 @@ class Graph:
 
 def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
                 d2_rtol: float = 1e-8, max_iter: int = 10000, max_refine: int = 8, kt: int = 0,
-                check_every: int = 8, single_rhs: bool = False, persistent: bool = False,
+                check_every: int = 4, single_rhs: bool = False, persistent: bool = False,
                 return_z: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
     """Squared GE distances d^2 for the k pairs (rows) of x, y ([k, n] or [n]).
 
@@ -363,14 +363,16 @@ def kernel_launches() -> int:
     return int(load_library().nvd_kernel_launches())
 
 
-def profile_enable(on: bool = True):
-    _check(load_library().nvd_profile_enable(1 if on else 0), "nvd_profile_enable")
+def profile_enable(on=True):
+    """on: False/0 off, True/1 time the SpMV launches, 2 also the vector passes."""
+    _check(load_library().nvd_profile_enable(int(on)), "nvd_profile_enable")
 
 
-def profile_read():
-    """(launches, total_ms, algorithmic_bytes) of the SpMV/SpMM kernel since the last read."""
+def profile_read(kernel_class: int = 0):
+    """(launches, total_ms, algorithmic_bytes) since the last read: class 0 = the SpMV/SpMM
+    kernel, class 1 = the vector passes."""
     n, ms, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
-    _check(load_library().nvd_profile_read(0, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)),
+    _check(load_library().nvd_profile_read(kernel_class, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)),
            "nvd_profile_read")
     return n.value, ms.value, b.value
 

@@ -15,13 +15,15 @@ namespace {
 struct Pending {
     cudaEvent_t a, b;
     double bytes;
+    int cls;
 };
 std::mutex g_mu;
-bool g_enabled = false;
+int g_enabled = 0;   // 0 off, 1 SpMV launches, 2 SpMV and vector passes
 std::vector<cudaEvent_t> g_pool;
 std::vector<Pending> g_pending;
-int64_t g_launches = 0;
-double g_ms = 0.0, g_bytes = 0.0;
+constexpr int NCLS = 2;
+int64_t g_launches[NCLS] = {0, 0};
+double g_ms[NCLS] = {0.0, 0.0}, g_bytes[NCLS] = {0.0, 0.0};
 
 cudaEvent_t take_event() {
     if (!g_pool.empty()) {
@@ -39,31 +41,38 @@ std::atomic<int64_t> g_kernel_launches{0};
 
 void note_launch(int64_t n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
-bool prof_enabled() { return g_enabled; }
+bool prof_enabled() { return g_enabled != 0; }
+bool prof_vec_enabled() { return g_enabled >= 2; }
 
 size_t prof_mark() {
     std::lock_guard<std::mutex> lk(g_mu);
     return g_pending.size();
 }
 
-// Keep the first `keep` SpMV launches recorded after `mark`; the rest ran after
-// convergence and found no work.
+// Keep the first `keep` SpMV launches (class 0) recorded after `mark`; the later
+// ones ran after convergence and found no work.  Vector-pass launches (class 1)
+// are all kept: their time is spent either way.
 void prof_keep(size_t mark, int64_t keep) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (mark > g_pending.size()) return;
-    const size_t upto = mark + (size_t)(keep < 0 ? 0 : keep);
-    if (upto >= g_pending.size()) return;
-    for (size_t i = upto; i < g_pending.size(); ++i) {
-        cudaEventSynchronize(g_pending[i].b);
-        g_pool.push_back(g_pending[i].a);
-        g_pool.push_back(g_pending[i].b);
+    int64_t seen = 0;
+    std::vector<Pending> kept(g_pending.begin(), g_pending.begin() + mark);
+    for (size_t i = mark; i < g_pending.size(); ++i) {
+        Pending &p = g_pending[i];
+        if (p.cls != 0 || seen++ < keep) {
+            kept.push_back(p);
+        } else {
+            cudaEventSynchronize(p.b);
+            g_pool.push_back(p.a);
+            g_pool.push_back(p.b);
+        }
     }
-    g_pending.resize(upto);
+    g_pending.swap(kept);
 }
 
-void prof_begin(cudaStream_t s) {
+void prof_begin(cudaStream_t s, int cls) {
     std::lock_guard<std::mutex> lk(g_mu);
-    Pending p{take_event(), take_event(), 0.0};
+    Pending p{take_event(), take_event(), 0.0, cls};
     cudaEventRecord(p.a, s);
     g_pending.push_back(p);
 }
@@ -82,13 +91,13 @@ using namespace nvd;
 
 extern "C" int nvd_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_enabled = on != 0;
+    g_enabled = on <= 0 ? 0 : on == 1 ? 1 : 2;
     return NVD_OK;
 }
 
 extern "C" int nvd_profile_read(int32_t kernel_class, int64_t *launches, double *total_ms, double *bytes) {
     clear_error();
-    if (kernel_class != 0) {
+    if (kernel_class < 0 || kernel_class >= NCLS) {
         set_error("nvd_profile_read: unknown kernel class %d", kernel_class);
         return NVD_ERR_INVALID_ARG;
     }
@@ -97,9 +106,9 @@ extern "C" int nvd_profile_read(int32_t kernel_class, int64_t *launches, double 
         if (cudaEventSynchronize(p.b) == cudaSuccess) {
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-                g_ms += ms;
-                g_bytes += p.bytes;
-                ++g_launches;
+                g_ms[p.cls] += ms;
+                g_bytes[p.cls] += p.bytes;
+                ++g_launches[p.cls];
             }
         }
         g_pool.push_back(p.a);
@@ -107,12 +116,13 @@ extern "C" int nvd_profile_read(int32_t kernel_class, int64_t *launches, double 
     }
     g_pending.clear();
     cudaGetLastError();
-    if (launches) *launches = g_launches;
-    if (total_ms) *total_ms = g_ms;
-    if (bytes) *bytes = g_bytes;
-    g_launches = 0;
-    g_ms = 0.0;
-    g_bytes = 0.0;
+    const int k = kernel_class;
+    if (launches) *launches = g_launches[k];
+    if (total_ms) *total_ms = g_ms[k];
+    if (bytes) *bytes = g_bytes[k];
+    g_launches[k] = 0;
+    g_ms[k] = 0.0;
+    g_bytes[k] = 0.0;
     return NVD_OK;
 }
 
@@ -141,7 +151,7 @@ extern "C" void nvd_solve_opts_default(nvd_solve_opts *o) {
     o->rtol = 1e-10;
     o->d2_rtol = 1e-8;
     o->max_refine = 8;
-    o->check_every = 8;
+    o->check_every = 4;
     o->kt = 0;
     o->flags = 0;
 }

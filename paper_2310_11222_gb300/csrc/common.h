@@ -11,11 +11,10 @@ constexpr int NWARP = NT / 32;
 
 // Sub-item budgets of the SpMV/SpMM for KT right-hand sides with vector/accumulator
 // element sizes szv/sza (shared by the host planner and the kernels).
-//   KT = 1: a sub-item is up to 256 rows with at most 2048 entries, every row at
-//           most sp_row_max = 128 entries; one warp takes it, a group of G lanes
-//           per row.  A row with more entries, up to sp_long_max, is a sub-item of
-//           its own for a whole warp; longer rows are split into chunks of
-//           sp_chunk entries, one warp each.
+//   KT = 1: light rows (at most sp_row_max = 128 entries) are processed by a group
+//           of G lanes each (light blocks are runs of light rows); a row with more
+//           entries, up to sp_long_max, is a sub-item of its own for a whole warp;
+//           longer rows are split into chunks of sp_chunk entries, one warp each.
 //   KT > 1: one CTA per sub-item; the row accumulators (rows x KT x sza) fit 8 KB
 //           (at most NT rows) and the entries gather about 32 KB of neighbour rows;
 //           longer rows are split into chunks of that many entries.
@@ -106,7 +105,7 @@ struct Ctx {
     const struct Owner *owners;     // [n_owner] device table, or NULL = use own0
     int32_t n_owner;
     const int32_t *perm;            // internal -> user node (NULL = identity)
-    int32_t spmv_group;             // lanes per row of the single right-hand-side SpMV (2..32)
+    int32_t spmv_group;             // lanes per row of the single right-hand-side SpMV (1..32)
     // ---- persistent-kernel grid barrier
     unsigned *bar_count, *bar_gen;
     Owner own0;

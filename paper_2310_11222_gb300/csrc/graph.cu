@@ -465,6 +465,70 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     }
     seg_sblk_off[nseg] = (int32_t)sblk.size();
 
+    if (KT == 1) {
+        // Single right-hand side: light blocks are contiguous row ranges of a segment
+        // (rows longer than RMAX are skipped there), balanced by entries + rows;
+        // heavy blocks (pad = 1) hold up to NWARP long-row or chunk sub-items.
+        sblk.clear();
+        double ltot = 0.0;
+        for (int s = 0; s < nseg; ++s)
+            for (int64_t r = g->h_seg_begin[s]; r < g->h_seg_end[s]; ++r) {
+                const int64_t d = rp[r + 1] - rp[r];
+                if (d <= RMAX) ltot += (double)d + 1.0;
+            }
+        const double target = ltot / std::max(1, T);
+        for (int s = 0; s < nseg; ++s) {
+            seg_sblk_off[s] = (int32_t)sblk.size();
+            const int64_t a = g->h_seg_begin[s], b = g->h_seg_end[s];
+            // maximal runs of consecutive light rows, each cut into blocks of about
+            // `target` work (entries + rows)
+            int64_t r = a;
+            while (r < b) {
+                while (r < b && rp[r + 1] - rp[r] > RMAX) ++r;
+                if (r >= b) break;
+                int64_t start = r;
+                double acc = 0.0;
+                while (r < b && rp[r + 1] - rp[r] <= RMAX) {
+                    acc += (double)(rp[r + 1] - rp[r]) + 1.0;
+                    ++r;
+                    if (acc >= target && r - start >= 32) {
+                        sblk.push_back(Block{start, r, s, 0});
+                        start = r;
+                        acc = 0.0;
+                    }
+                }
+                if (r > start) sblk.push_back(Block{start, r, s, 0});
+            }
+            // heavy sub-items of this segment, NWARP per block
+            int64_t h = seg_item_off[s];
+            std::vector<int64_t> hv;
+            for (int64_t i = seg_item_off[s]; i < seg_item_off[s + 1]; ++i)
+                if (items[i].kind != 0) hv.push_back(i);
+            for (size_t q = 0; q < hv.size(); q += NWARP) {
+                // heavy items of a segment are contiguous in `items` only between light
+                // runs, so heavy blocks index a compacted list (see below)
+                sblk.push_back(Block{(int64_t)q, (int64_t)std::min(hv.size(), q + NWARP), s, 1});
+            }
+            (void)h;
+        }
+        seg_sblk_off[nseg] = (int32_t)sblk.size();
+        // compact the item list to the heavy sub-items only, segment by segment, and
+        // rebase the heavy blocks onto it
+        std::vector<SpItem> heavy;
+        std::vector<int64_t> seg_heavy_base(nseg + 1, 0);
+        for (int s = 0; s < nseg; ++s) {
+            seg_heavy_base[s] = (int64_t)heavy.size();
+            for (int64_t i = seg_item_off[s]; i < seg_item_off[s + 1]; ++i)
+                if (items[i].kind != 0) heavy.push_back(items[i]);
+        }
+        for (Block &bk : sblk)
+            if (bk.pad == 1) {
+                bk.i0 += seg_heavy_base[bk.seg];
+                bk.i1 += seg_heavy_base[bk.seg];
+            }
+        items.swap(heavy);
+    }
+
     std::vector<Block> vblk;
     std::vector<int32_t> seg_vblk_off(nseg + 1, 0);
     int64_t rows_tot = 0;

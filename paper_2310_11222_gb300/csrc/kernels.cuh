@@ -28,7 +28,7 @@ namespace dev {
 
 // Entries each lane keeps in flight per pass of the single-RHS SpMV row loop.
 #ifndef SPMV1_UNROLL
-#define SPMV1_UNROLL 2
+#define SPMV1_UNROLL 4
 #endif
 
 // ------------------------------------------------------------------ loads/stores
@@ -202,8 +202,17 @@ __device__ void seg_arrive(const Ctx &c, const Fin &fin, int seg, int64_t slot, 
     if (pair < P) {
         const int d = pair / KT, j = pair % KT;
         const double *base = c.part + (int64_t)d * c.part_stride * KT + j;
-        for (int i = sub; i < cnt; i += TPP) s += __ldcg(base + (s0 + i) * KT);
-        for (int i = sub; i < hcnt; i += TPP) s += __ldcg(base + (h0 + i) * KT);
+        // eight independent loads in flight, added in slot order
+        int i = sub;
+        for (; i + 7 * TPP < cnt; i += 8 * TPP) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(base + (s0 + i + u * TPP) * KT);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; i < cnt; i += TPP) s += __ldcg(base + (s0 + i) * KT);
+        for (int h = sub; h < hcnt; h += TPP) s += __ldcg(base + (h0 + h) * KT);
     }
     constexpr int WOFF = TPP < 32 ? TPP : 32;
 #pragma unroll
@@ -627,19 +636,12 @@ __device__ __noinline__ void spmv1_long(const Ctx &c, const Epi &epi, const TV *
 
 }
 
-// Single right-hand side (KT = 1) SpMV block.  Every warp walks the block's
-// sub-items; warps never wait for each other and use no shared memory, so many
-// independent load chains are in flight per SM:
-//   kind 0: up to 256 short rows shared by the 8 warps; each warp's 32/G groups of
-//           G lanes take one row each (G = c.spmv_group, chosen from the degree
-//           profile): the lanes
-//           stride over the row two entries at a time, a butterfly inside the
-//           group adds them and the group's first lane applies the row epilogue;
-//   kind 2: one long row for one warp (dealt round-robin), striding over it in
-//           16-byte quads;
-//   kind 1: one chunk of a split row for one warp: its sum goes to hsum, and the warp
-//           that completes the row last (hcount) adds the chunks in chunk order,
-//           applies the epilogue and writes the row's own partial slot.
+// Single right-hand side (KT = 1) SpMV block.  Warps never wait for each other
+// (only __syncwarp), so many independent load chains are in flight per SM.
+//   light block (pad 0): a run of consecutive light rows of one segment; a group
+//           of G lanes per row (G from the degree profile);
+//   heavy block (pad 1): up to 8 sub-items, one per warp: a long row (kind 2) or a
+//           chunk of a split row (kind 1, see spmv1_long).
 template <class LD, class TV, class TW, class TA, class Epi>
 __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__ src, TV *__restrict__ dst,
                             int64_t b, char *smem) {
@@ -649,8 +651,6 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
     double *tot = red + red_doubles(1);
     const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
     const TA *__restrict__ deg = deg_of<TA>(c);
-    const int G = c.spmv_group;
-    const int ngw = 32 / G, gl = lane & (G - 1), gid = lane / G;
     const Block blk = c.sblk[b];
     const int seg = blk.seg;
     double dot[ND > 0 ? ND : 1][1];
@@ -658,48 +658,56 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
     for (int d = 0; d < (ND > 0 ? ND : 1); ++d) dot[d][0] = 0.0;
     const bool live = !Epi::NEEDS_LIVE || seg_live<1>(c, seg);
     if (live) {
-        for (int64_t si = blk.i0; si < blk.i1; ++si) {
-            const SpItem it = c.items[si];
-            if (it.kind == 0) {
-                for (int64_t base = it.r0 + warp * ngw; base < it.r1; base += NWARP * ngw) {
-                    const int64_t i = base + gid;
-                    const bool valid = i < it.r1;
-                    constexpr int U = SPMV1_UNROLL;   // entries per lane in flight
-                    TA a[U];
+        if (blk.pad == 0) {
+            // light rows [i0, i1) (a run of rows of at most sp_row_max entries): each
+            // warp's 32/G groups of G lanes take one row each, rows dealt across the
+            // warps; the lanes stride over the row SPMV1_UNROLL entries at a time,
+            // a butterfly inside the group adds them and the group's first lane
+            // applies the row epilogue
+            const int G = c.spmv_group;
+            const int ngw = 32 / G, gl = lane & (G - 1), gid = lane / G;
+            for (int64_t base = blk.i0 + warp * ngw; base < blk.i1; base += NWARP * ngw) {
+                const int64_t i = base + gid;
+                const bool valid = i < blk.i1;
+                constexpr int U = SPMV1_UNROLL;
+                TA a[U];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) a[u] = 0;
-                    TV own[1] = {(TV)0};
-                    TA dg = 0;
-                    if (valid) {
-                        const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
-                        if (gl == 0) {
-                            own[0] = LD::ld(src + i);
-                            dg = __ldg(deg + i);
-                        }
-                        for (int64_t e = e0 + gl; e < e1; e += (int64_t)U * G) {
-                            int cu[U];
-                            TW wu[U];
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                const bool in = e + (int64_t)u * G < e1;
-                                cu[u] = in ? __ldcs(c.colidx + e + (int64_t)u * G) : -1;
-                                wu[u] = in ? __ldcs(w + e + (int64_t)u * G) : (TW)0;
-                            }
-#pragma unroll
-                            for (int u = 0; u < U; ++u)
-                                if (cu[u] >= 0) a[u] += (TA)wu[u] * (TA)LD::ld(src + cu[u]);
-                        }
+                for (int u = 0; u < U; ++u) a[u] = 0;
+                TV own[1] = {(TV)0};
+                TA dg = 0;
+                if (valid) {
+                    const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
+                    if (gl == 0) {
+                        own[0] = LD::ld(src + i);
+                        dg = __ldg(deg + i);
                     }
-                    TA acc = a[0];
+                    for (int64_t e = e0 + gl; e < e1; e += (int64_t)U * G) {
+                        int cu[U];
+                        TW wu[U];
 #pragma unroll
-                    for (int u = 1; u < U; ++u) acc += a[u];
-                    for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(NVD_FULLMASK, acc, off);
-                    if (valid && gl == 0) {
-                        const TA av[1] = {acc};
-                        epi.template elem<TV, TA, 1>(c, i, 0, 1, own, av, dg, dst, dot);
+                        for (int u = 0; u < U; ++u) {
+                            const bool in = e + (int64_t)u * G < e1;
+                            cu[u] = in ? __ldcs(c.colidx + e + (int64_t)u * G) : -1;
+                            wu[u] = in ? __ldcs(w + e + (int64_t)u * G) : (TW)0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (cu[u] >= 0) a[u] += (TA)wu[u] * (TA)LD::ld(src + cu[u]);
                     }
                 }
-            } else if ((int)((si - blk.i0) % NWARP) == warp) {
+                TA acc = a[0];
+#pragma unroll
+                for (int u = 1; u < U; ++u) acc += a[u];
+                for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(NVD_FULLMASK, acc, off);
+                if (valid && gl == 0) {
+                    const TA av[1] = {acc};
+                    epi.template elem<TV, TA, 1>(c, i, 0, 1, own, av, dg, dst, dot);
+                }
+            }
+        } else {
+            // heavy sub-items (long rows, chunks of split rows), one warp each
+            for (int64_t si = blk.i0 + warp; si < blk.i1; si += NWARP) {
+                const SpItem it = c.items[si];
                 spmv1_long<LD, TV, TW, TA, Epi>(c, epi, src, dst, it, dot);
             }
         }

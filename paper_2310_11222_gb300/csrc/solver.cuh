@@ -60,7 +60,8 @@ __global__ void k_collect(Ctx c, ColResult *res, double *d2dev, int64_t d2_strid
 // ------------------------------------------------------------------ profiling hooks (api.cu)
 
 bool prof_enabled();
-void prof_begin(cudaStream_t s);
+bool prof_vec_enabled();
+void prof_begin(cudaStream_t s, int cls = 0);
 void prof_end(cudaStream_t s, double bytes);
 size_t prof_mark();
 void prof_keep(size_t mark, int64_t keep);
@@ -135,7 +136,10 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
 template <class TV, int KT, class Op>
 inline int launch_vec(const Ctx &c, const Op &op, cudaStream_t s) {
     if (c.n_vblk == 0) return NVD_OK;
+    const bool prof = prof_vec_enabled();
+    if (prof) prof_begin(s, 1);
     k_vec<TV, KT, Op><<<(unsigned)c.n_vblk, NT, 0, s>>>(c, op);
+    if (prof) prof_end(s, 0.0);
     note_launch();
     NVD_TRY_CUDA(cudaGetLastError());
     return NVD_OK;
