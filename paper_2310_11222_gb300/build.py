@@ -74,6 +74,12 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     jobs = jobs or max(1, min(len(srcs), os.cpu_count() or 4))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
+    # objects of earlier source versions are never linked again
+    keep = {os.path.basename(o) for o in objs}
+    obj_dir = os.path.join(OUT, "obj")
+    for f in os.listdir(obj_dir):
+        if f.endswith(".o") and f not in keep:
+            os.remove(os.path.join(obj_dir, f))
     key = hashlib.sha256("".join(objs).encode()).hexdigest()[:16]
     stamp = os.path.join(OUT, "libnvd.stamp")
     if os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == key:

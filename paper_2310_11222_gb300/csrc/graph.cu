@@ -465,10 +465,11 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     }
     seg_sblk_off[nseg] = (int32_t)sblk.size();
 
-    if (KT == 1) {
-        // Single right-hand side: light blocks are contiguous row ranges of a segment
-        // (rows longer than RMAX are skipped there), balanced by entries + rows;
-        // heavy blocks (pad = 1) hold up to NWARP long-row or chunk sub-items.
+    {
+        // Light blocks (pad = 0) are runs of consecutive rows of at most RMAX entries,
+        // cut to about `target` work; heavy blocks (pad = 1) hold the long-row and
+        // chunk sub-items (KT = 1: up to NWARP, one per warp; KT > 1: up to 4, each
+        // taken by the whole CTA).
         sblk.clear();
         double ltot = 0.0;
         for (int s = 0; s < nseg; ++s)
@@ -504,10 +505,11 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
             std::vector<int64_t> hv;
             for (int64_t i = seg_item_off[s]; i < seg_item_off[s + 1]; ++i)
                 if (items[i].kind != 0) hv.push_back(i);
-            for (size_t q = 0; q < hv.size(); q += NWARP) {
+            const size_t per = KT == 1 ? (size_t)NWARP : 4;
+            for (size_t q = 0; q < hv.size(); q += per) {
                 // heavy items of a segment are contiguous in `items` only between light
                 // runs, so heavy blocks index a compacted list (see below)
-                sblk.push_back(Block{(int64_t)q, (int64_t)std::min(hv.size(), q + NWARP), s, 1});
+                sblk.push_back(Block{(int64_t)q, (int64_t)std::min(hv.size(), q + per), s, 1});
             }
             (void)h;
         }

@@ -30,6 +30,10 @@ namespace dev {
 #ifndef SPMV1_UNROLL
 #define SPMV1_UNROLL 4
 #endif
+// Gathered neighbour rows each lane group keeps in flight in the multi-RHS SpMM.
+#ifndef SPMM_UNROLL
+#define SPMM_UNROLL 4
+#endif
 
 // ------------------------------------------------------------------ loads/stores
 
@@ -748,52 +752,59 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
 
     const bool live = !Epi::NEEDS_LIVE || seg_live<KT>(c, seg);
     if (live) {
-        for (int64_t si = blk.i0; si < blk.i1; ++si) {
-            const SpItem it = c.items[si];
-            if (it.kind == 0) {
-                // ---------------- phase A: neighbour sums of rows [r0, r1) into s_acc
-                {
-                    const int gi = lane / LPR, col0 = (lane % LPR) * VEC;
-                    for (int64_t i = it.r0 + warp; i < it.r1; i += NWARP) {
-                        const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
-                        TA acc[VEC];
+        if (blk.pad == 0) {
+            // light rows [i0, i1): a group of LPR lanes owns one row, lane `sub` of the
+            // group owns columns col0..col0+VEC-1, so a row needs no cross-lane sum;
+            // each warp runs G rows at a time, SPMM_UNROLL gathered neighbour rows in
+            // flight per group, and no CTA barrier until the final reduction
+            const int gid = lane / LPR, col0 = (lane % LPR) * VEC;
+            const TA *__restrict__ deg = deg_of<TA>(c);
+            for (int64_t base = blk.i0 + warp * G; base < blk.i1; base += NWARP * G) {
+                const int64_t i = base + gid;
+                if (i < blk.i1) {
+                    const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
+                    TV own[VEC];
+                    ldv<LD, TV, VEC>(src + i * KT + col0, own);
+                    const TA dg = __ldg(deg + i);
+                    constexpr int U = SPMM_UNROLL;
+                    TA acc[U][VEC];
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[v] = 0;
-                        int64_t e = e0 + gi;
-                        for (; e + G < e1; e += 2 * G) {
-                            const int ca = __ldcs(c.colidx + e), cb = __ldcs(c.colidx + e + G);
-                            const TA wa = (TA)__ldcs(w + e), wb = (TA)__ldcs(w + e + G);
-                            TV pa[VEC], pb[VEC];
-                            ldv<LD, TV, VEC>(src + (int64_t)ca * KT + col0, pa);
-                            ldv<LD, TV, VEC>(src + (int64_t)cb * KT + col0, pb);
+                    for (int u = 0; u < U; ++u)
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[v] += wa * (TA)pa[v];
+                        for (int v = 0; v < VEC; ++v) acc[u][v] = 0;
+                    for (int64_t e = e0; e < e1; e += U) {
+                        int cu[U];
+                        TA wu[U];
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[v] += wb * (TA)pb[v];
-                        }
-                        if (e < e1) {
-                            const int ca = __ldcs(c.colidx + e);
-                            const TA wa = (TA)__ldcs(w + e);
-                            TV pa[VEC];
-                            ldv<LD, TV, VEC>(src + (int64_t)ca * KT + col0, pa);
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[v] += wa * (TA)pa[v];
+                        for (int u = 0; u < U; ++u) {
+                            const bool in = e + u < e1;
+                            cu[u] = in ? __ldcs(c.colidx + e + u) : -1;
+                            wu[u] = in ? (TA)__ldcs(w + e + u) : (TA)0;
                         }
 #pragma unroll
-                        for (int off = LPR; off < 32; off <<= 1)
+                        for (int u = 0; u < U; ++u) {
+                            if (cu[u] >= 0) {
+                                TV pv[VEC];
+                                ldv<LD, TV, VEC>(src + (int64_t)cu[u] * KT + col0, pv);
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(NVD_FULLMASK, acc[v], off);
-                        if (gi == 0) {
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) s_acc[(i - it.r0) * KT + col0 + v] = acc[v];
+                                for (int v = 0; v < VEC; ++v) acc[u][v] += wu[u] * (TA)pv[v];
+                            }
                         }
                     }
+                    TA sum[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        sum[v] = acc[0][v];
+#pragma unroll
+                        for (int u = 1; u < U; ++u) sum[v] += acc[u][v];
+                    }
+                    epi.template elem<TV, TA, VEC>(c, i, col0, KT, own, sum, dg, dst, dot);
                 }
-                __syncthreads();
-                // ---------------- phase B: epilogue, coalesced over rows x columns
-                spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, src, dst, it.r0, it.r1, s_acc, dot);
-                __syncthreads();
-            } else {
+            }
+        } else {
+            // heavy block: chunks of split rows, each taken by the whole CTA
+            for (int64_t si = blk.i0; si < blk.i1; ++si) {
+                const SpItem it = c.items[si];
                 spmm_chunk<LD, TV, TW, TA, KT, Epi>(c, epi, src, dst, it, s_acc, red);
             }
         }

@@ -68,7 +68,7 @@ def test_batched_equals_independent_solves(nvd, small_batch):
     d2 = nvd.ge_distance_batched(G, xs, ys, mode=nvd.MODE_FP64, rtol=1e-10).numpy()
     off = 0
     for g, x, y in zip(G, xs, ys):
-        one = nvd.ge_distance(g, x, y, rtol=1e-10, kt=32 if False else 16).cpu().numpy()
+        one = nvd.ge_distance(g, x, y, rtol=1e-10, kt=16).cpu().numpy()
         assert rel(d2[off:off + len(one)], one) < 1e-9
         off += len(one)
 
@@ -79,13 +79,11 @@ def test_batched_uneven_pair_counts_and_multiple_tiles(nvd, small_batch):
     ks = [5, 32, 17]
     xs = [on(pairs[i][0][:k]) for i, k in enumerate(ks)]
     ys = [on(pairs[i][1][:k]) for i, k in enumerate(ks)]
-    for kt in (0, 8):
-        import ctypes  # noqa: F401
-        d2 = nvd.ge_distance_batched(G, xs, ys, mode=nvd.MODE_FP64, rtol=1e-10).numpy()
-        off = 0
-        for i, k in enumerate(ks):
-            assert rel(d2[off:off + k], want[i][:k]) < 1e-8
-            off += k
+    d2 = nvd.ge_distance_batched(G, xs, ys, mode=nvd.MODE_FP64, rtol=1e-10).numpy()
+    off = 0
+    for i, k in enumerate(ks):
+        assert rel(d2[off:off + k], want[i][:k]) < 1e-8
+        off += k
 
 
 @pytest.mark.parametrize("mode", [0, 1])
