@@ -166,10 +166,6 @@ int build_union(const nvd_graph_t *gs, int G, cudaStream_t s, UnionGraph **out) 
         NVD_TRY_CUDA(cudaMemcpyAsync(U->seg_end.p, U->h_seg_end.data(), U->nseg * 8, cudaMemcpyHostToDevice, s));
     }
     NVD_TRY_CUDA(cudaMemcpyAsync(U->seg_owner.p, owner.data(), ns * 4, cudaMemcpyHostToDevice, s));
-    int64_t rows = 0;
-    for (int sg = 0; sg < U->nseg; ++sg) rows += U->h_seg_end[sg] - U->h_seg_begin[sg];
-    const double mean = rows ? (double)nnz / (double)rows : 0.0;
-    U->spmv_group = mean <= 16 ? 2 : mean <= 32 ? 4 : mean <= 64 ? 8 : 16;
     NVD_TRY_CUDA(cudaStreamCreateWithFlags(&u->cs, cudaStreamNonBlocking));
     NVD_TRY_CUDA(cudaEventCreateWithFlags(&u->ev_in, cudaEventDisableTiming));
     NVD_TRY_CUDA(cudaEventCreateWithFlags(&u->ev_out, cudaEventDisableTiming));

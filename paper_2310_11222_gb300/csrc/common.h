@@ -9,15 +9,18 @@ namespace nvd {
 constexpr int NT = 256;          // threads per CTA for every work kernel
 constexpr int NWARP = NT / 32;
 
-// Sub-item budgets of the SpMV/SpMM for KT right-hand sides with vector/accumulator
+// Work decomposition of the SpMV/SpMM for KT right-hand sides with vector/accumulator
 // element sizes szv/sza (shared by the host planner and the kernels).
-//   KT = 1: light rows (at most sp_row_max = 128 entries) are processed by a group
-//           of G lanes each (light blocks are runs of light rows); a row with more
-//           entries, up to sp_long_max, is a sub-item of its own for a whole warp;
-//           longer rows are split into chunks of sp_chunk entries, one warp each.
-//   KT > 1: one CTA per sub-item; the row accumulators (rows x KT x sza) fit 8 KB
-//           (at most NT rows) and the entries gather about 32 KB of neighbour rows;
-//           longer rows are split into chunks of that many entries.
+//   Light rows (at most sp_row_max entries) are stored a second time in a sliced
+//   layout: a slice holds sp_slice_rows rows (one per lane group of a warp), sorted
+//   by length inside their block, with entry j of all its rows side by side, so one
+//   warp load fetches entry j of every row and every lane of an arithmetic
+//   instruction does useful work.
+//   KT = 1: a row with more entries, up to sp_long_max, is a sub-item of its own for
+//           a whole warp; longer rows are split into chunks of sp_chunk entries,
+//           one warp each.
+//   KT > 1: heavy rows are split into chunks of sp_chunk entries, one CTA each; the
+//           row accumulators (rows x KT x sza) fit 8 KB.
 constexpr int sp_rows_budget(int KT, int sza) {
     return KT == 1 ? 256 : ((8192 / (KT * sza)) > NT ? NT : (8192 / (KT * sza)));
 }
@@ -25,8 +28,16 @@ constexpr int sp_nnz_budget(int KT, int szv) { return KT == 1 ? 2048 : 32768 / (
 constexpr int sp_row_max(int KT, int szv) { return KT == 1 ? 128 : 32768 / (KT * szv); }
 constexpr int sp_long_max(int KT) { return KT == 1 ? 8192 : 0; }
 constexpr int sp_chunk(int KT, int szv) { return KT == 1 ? 4096 : 32768 / (KT * szv); }
-// doubles of reduction scratch per CTA
-constexpr int red_doubles(int KT) { return (NWARP * 4 * KT) > 256 ? NWARP * 4 * KT : 256; }
+// Columns one lane owns (16-byte vectors where the row is that wide), lanes per
+// row, and rows per slice (one row per lane group of a warp).
+constexpr int sp_vec(int KT, int szv) { return KT * szv >= 16 ? 16 / szv : KT; }
+constexpr int sp_lanes_per_row(int KT, int szv) { return KT / sp_vec(KT, szv); }
+constexpr int sp_slice_rows(int KT, int szv) { return 32 / sp_lanes_per_row(KT, szv); }
+// doubles of reduction scratch per CTA (KT = 1: every thread's partial of up to 4
+// sums, added by one warp per sum)
+constexpr int red_doubles(int KT) {
+    return KT == 1 ? 4 * NT : (NWARP * 4 * KT) > 256 ? NWARP * 4 * KT : 256;
+}
 constexpr int vec_smem_bytes(int KT) { return (red_doubles(KT) + 4 * KT) * 8; }
 
 // Sub-item of the Laplacian SpMV/SpMM.
@@ -45,7 +56,8 @@ struct SpItem {
 static_assert(sizeof(SpItem) == 48, "SpItem layout");
 
 // A CTA block: a contiguous run of work inside one segment.
-//   SpMV blocks: sub-items [i0, i1).  Vector blocks: rows [i0, i1).
+//   SpMV light blocks (pad = 0): slices [i0, i1).  SpMV heavy blocks (pad = 1):
+//   sub-items [i0, i1).  Vector blocks: rows [i0, i1).
 struct Block {
     int64_t i0, i1;
     int32_t seg, pad;
@@ -105,7 +117,15 @@ struct Ctx {
     const struct Owner *owners;     // [n_owner] device table, or NULL = use own0
     int32_t n_owner;
     const int32_t *perm;            // internal -> user node (NULL = identity)
-    int32_t spmv_group;             // lanes per row of the single right-hand-side SpMV (1..32)
+    // ---- sliced copy of the light rows: slice s holds H = sp_slice_rows rows
+    //      sl_row[s*H + r] (-1 = empty lane group); entry j of row r sits at
+    //      sl_base[s] + j*H + r of sl_col / sl_w (TW); rows shorter than the slice's
+    //      longest are padded with zero weights on their own column
+    const int64_t *sl_base;         // [n_slices + 1]
+    const int32_t *sl_row;          // [n_slices * H]
+    const int32_t *sl_col;
+    const void *sl_w;
+    int32_t sl_h;                   // H of the plan the pointers above belong to
     // ---- persistent-kernel grid barrier
     unsigned *bar_count, *bar_gen;
     Owner own0;

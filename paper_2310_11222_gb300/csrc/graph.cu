@@ -352,6 +352,35 @@ uint64_t next_graph_id() {
 
 // ------------------------------------------------------------------ plans
 
+// Fill the sliced copy of the light rows from the CSR: thread t is lane group r of
+// slice t / H; entry j of its row goes to sl_base[slice] + j*H + r (consecutive
+// threads write consecutive addresses).  Padding (rows shorter than the slice's
+// longest, and empty lane groups) gets weight 0 on a column the row reads anyway
+// (its own node; for an empty lane group the slice's first row).
+template <class TWI, class TWO>
+__global__ void k_fill_slices(int64_t n_slices, int H, const int64_t *__restrict__ sl_base,
+                              const int32_t *__restrict__ sl_row, const int64_t *__restrict__ rowptr,
+                              const int32_t *__restrict__ colidx, const TWI *__restrict__ w,
+                              int32_t *__restrict__ sl_col, TWO *__restrict__ sl_w) {
+    const int64_t nt = n_slices * H;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = t / H;
+        const int r = (int)(t % H);
+        const int64_t base = sl_base[sl];
+        const int64_t L = (sl_base[sl + 1] - base) / H;
+        const int32_t row = sl_row[t];
+        const int32_t pad = row >= 0 ? row : sl_row[sl * H];
+        const int64_t e0 = row >= 0 ? rowptr[row] : 0;
+        const int64_t d = row >= 0 ? rowptr[row + 1] - e0 : 0;
+        for (int64_t j = 0; j < L; ++j) {
+            const bool in = j < d;
+            sl_col[base + j * H + r] = in ? colidx[e0 + j] : pad;
+            sl_w[base + j * H + r] = in ? (TWO)w[e0 + j] : (TWO)0;
+        }
+    }
+}
+
 int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     const int key = KT * 256 + szv * 16 + sza;
     auto it = g->plans.find(key);
@@ -363,173 +392,109 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     pl->KT = KT;
     pl->szv = szv;
     pl->sza = sza;
-    const int RB = sp_rows_budget(KT, sza);
-    const int64_t NB = sp_nnz_budget(KT, szv);
     const int64_t RMAX = sp_row_max(KT, szv);
     const int64_t LONG = sp_long_max(KT);
     const int64_t CH = sp_chunk(KT, szv);
+    const int H = sp_slice_rows(KT, szv);
     const std::vector<int64_t> &rp = g->h_rowptr;
     const int nseg = g->nseg;
+
+    // heavy rows: a whole-row sub-item (KT = 1, up to LONG entries) or chunks of CH
+    // entries; items are listed segment by segment
     std::vector<SpItem> items;
-    std::vector<int32_t> seg_item_off(nseg + 1, 0), seg_heavy_off(nseg + 1, 0);
+    std::vector<int32_t> seg_heavy_off(nseg + 1, 0);
+    std::vector<int64_t> seg_item_off(nseg + 1, 0);
     int32_t nheavy = 0, nchunks = 0;
+    double ltot = 0.0;
     for (int s = 0; s < nseg; ++s) {
-        seg_item_off[s] = (int32_t)items.size();
+        seg_item_off[s] = (int64_t)items.size();
         seg_heavy_off[s] = nheavy;
-        int64_t r = g->h_seg_begin[s];
-        const int64_t re = g->h_seg_end[s];
-        while (r < re) {
+        for (int64_t r = g->h_seg_begin[s]; r < g->h_seg_end[s]; ++r) {
             const int64_t d = rp[r + 1] - rp[r];
-            if (d > RMAX && d <= LONG) {
-                SpItem it{};
-                it.r0 = (int32_t)r;
-                it.r1 = (int32_t)(r + 1);
-                it.kind = 2;
-                it.e0 = rp[r];
-                it.e1 = rp[r + 1];
-                items.push_back(it);
-                ++r;
-                continue;
-            }
-            if (d > RMAX) {
+            if (d <= RMAX) {
+                ltot += (double)d + 1.0;
+            } else if (d <= LONG) {
+                SpItem si{};
+                si.r0 = (int32_t)r;
+                si.r1 = (int32_t)(r + 1);
+                si.kind = 2;
+                si.e0 = rp[r];
+                si.e1 = rp[r + 1];
+                items.push_back(si);
+            } else {
                 const int32_t nch = (int32_t)((d + CH - 1) / CH);
-                for (int32_t c = 0; c < nch; ++c) {
-                    SpItem it{};
-                    it.r0 = (int32_t)r;
-                    it.r1 = (int32_t)(r + 1);
-                    it.kind = 1;
-                    it.hrow = nheavy;
-                    it.e0 = rp[r] + (int64_t)c * CH;
-                    it.e1 = std::min(rp[r] + (int64_t)(c + 1) * CH, rp[r + 1]);
-                    it.hbase = nchunks;
-                    it.hchunk = c;
-                    it.nchunk = nch;
-                    items.push_back(it);
+                for (int32_t q = 0; q < nch; ++q) {
+                    SpItem si{};
+                    si.r0 = (int32_t)r;
+                    si.r1 = (int32_t)(r + 1);
+                    si.kind = 1;
+                    si.hrow = nheavy;
+                    si.e0 = rp[r] + (int64_t)q * CH;
+                    si.e1 = std::min(rp[r] + (int64_t)(q + 1) * CH, rp[r + 1]);
+                    si.hbase = nchunks;
+                    si.hchunk = q;
+                    si.nchunk = nch;
+                    items.push_back(si);
                 }
                 ++nheavy;
                 nchunks += nch;
-                ++r;
-                continue;
             }
-            const int64_t r0 = r;
-            int64_t cnt = 0;
-            while (r < re && r - r0 < RB) {
-                const int64_t dd = rp[r + 1] - rp[r];
-                if (dd > RMAX) break;
-                if (cnt + dd > NB && r > r0) break;
-                cnt += dd;
-                ++r;
-            }
-            SpItem it{};
-            it.r0 = (int32_t)r0;
-            it.r1 = (int32_t)r;
-            it.kind = 0;
-            it.e0 = rp[r0];
-            it.e1 = rp[r];
-            items.push_back(it);
         }
     }
-    seg_item_off[nseg] = (int32_t)items.size();
+    seg_item_off[nseg] = (int64_t)items.size();
     seg_heavy_off[nseg] = nheavy;
 
-    // blocks: about target_blocks() per launch, split in proportion to work
+    // Light blocks: the light rows of a segment, in order, cut into blocks of whole
+    // warp rounds (NWARP slices of H rows) of about `target` work (entries + rows);
+    // inside a block the rows are sorted by length (longest first, ties by row) and
+    // dealt into slices.  Heavy blocks follow their segment's light blocks.
     const int T = target_blocks(g);
-    double wtot = 0.0;
-    std::vector<double> iw(items.size());
-    for (size_t i = 0; i < items.size(); ++i) {
-        iw[i] = (double)(items[i].e1 - items[i].e0) + (double)(items[i].r1 - items[i].r0);
-        wtot += iw[i];
-    }
+    const double target = ltot / std::max(1, T);
+    const int64_t QR = (int64_t)NWARP * H;
     std::vector<Block> sblk;
     std::vector<int32_t> seg_sblk_off(nseg + 1, 0);
+    std::vector<int64_t> sl_base(1, 0);
+    std::vector<int32_t> sl_row;
+    std::vector<int64_t> rows, lens;
+    auto emit_block = [&](int s) {
+        std::vector<int64_t> ord(rows.size());
+        for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int64_t)q;
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return lens[x] > lens[y]; });
+        const int64_t first = (int64_t)sl_base.size() - 1;
+        for (size_t q0 = 0; q0 < ord.size(); q0 += H) {
+            int64_t L = 0;
+            for (int r = 0; r < H; ++r) {
+                const size_t q = q0 + r;
+                sl_row.push_back(q < ord.size() ? (int32_t)rows[ord[q]] : -1);
+                if (q < ord.size()) L = std::max(L, lens[ord[q]]);
+            }
+            sl_base.push_back(sl_base.back() + L * H);
+        }
+        sblk.push_back(Block{first, (int64_t)sl_base.size() - 1, s, 0});
+        rows.clear();
+        lens.clear();
+    };
     for (int s = 0; s < nseg; ++s) {
         seg_sblk_off[s] = (int32_t)sblk.size();
-        const int64_t a = seg_item_off[s], b = seg_item_off[s + 1];
-        double ws = 0.0;
-        for (int64_t i = a; i < b; ++i) ws += iw[i];
-        int64_t nb = (int64_t)(T * ws / (wtot > 0 ? wtot : 1.0) + 0.5);
-        nb = std::max<int64_t>(1, std::min<int64_t>(nb, b - a));
-        const double target = ws / nb;
         double acc = 0.0;
-        int64_t start = a;
-        int64_t made = 0;
-        for (int64_t i = a; i < b; ++i) {
-            acc += iw[i];
-            const bool last = (i == b - 1);
-            if (last || (acc >= target * (made + 1) && made < nb - 1)) {
-                sblk.push_back(Block{start, i + 1, s, 0});
-                ++made;
-                start = i + 1;
+        for (int64_t r = g->h_seg_begin[s]; r < g->h_seg_end[s]; ++r) {
+            const int64_t d = rp[r + 1] - rp[r];
+            if (d > RMAX) continue;
+            rows.push_back(r);
+            lens.push_back(d);
+            acc += (double)d + 1.0;
+            if ((int64_t)rows.size() % QR == 0 && acc >= target) {
+                emit_block(s);
+                acc = 0.0;
             }
         }
+        if (!rows.empty()) emit_block(s);
+        const size_t per = KT == 1 ? (size_t)NWARP : 4;
+        const int64_t h0 = seg_item_off[s], h1 = seg_item_off[s + 1];
+        for (int64_t q = h0; q < h1; q += (int64_t)per)
+            sblk.push_back(Block{q, std::min<int64_t>(h1, q + (int64_t)per), s, 1});
     }
     seg_sblk_off[nseg] = (int32_t)sblk.size();
-
-    {
-        // Light blocks (pad = 0) are runs of consecutive rows of at most RMAX entries,
-        // cut to about `target` work; heavy blocks (pad = 1) hold the long-row and
-        // chunk sub-items (KT = 1: up to NWARP, one per warp; KT > 1: up to 4, each
-        // taken by the whole CTA).
-        sblk.clear();
-        double ltot = 0.0;
-        for (int s = 0; s < nseg; ++s)
-            for (int64_t r = g->h_seg_begin[s]; r < g->h_seg_end[s]; ++r) {
-                const int64_t d = rp[r + 1] - rp[r];
-                if (d <= RMAX) ltot += (double)d + 1.0;
-            }
-        const double target = ltot / std::max(1, T);
-        for (int s = 0; s < nseg; ++s) {
-            seg_sblk_off[s] = (int32_t)sblk.size();
-            const int64_t a = g->h_seg_begin[s], b = g->h_seg_end[s];
-            // maximal runs of consecutive light rows, each cut into blocks of about
-            // `target` work (entries + rows)
-            int64_t r = a;
-            while (r < b) {
-                while (r < b && rp[r + 1] - rp[r] > RMAX) ++r;
-                if (r >= b) break;
-                int64_t start = r;
-                double acc = 0.0;
-                while (r < b && rp[r + 1] - rp[r] <= RMAX) {
-                    acc += (double)(rp[r + 1] - rp[r]) + 1.0;
-                    ++r;
-                    if (acc >= target && r - start >= 32) {
-                        sblk.push_back(Block{start, r, s, 0});
-                        start = r;
-                        acc = 0.0;
-                    }
-                }
-                if (r > start) sblk.push_back(Block{start, r, s, 0});
-            }
-            // heavy sub-items of this segment, NWARP per block
-            int64_t h = seg_item_off[s];
-            std::vector<int64_t> hv;
-            for (int64_t i = seg_item_off[s]; i < seg_item_off[s + 1]; ++i)
-                if (items[i].kind != 0) hv.push_back(i);
-            const size_t per = KT == 1 ? (size_t)NWARP : 4;
-            for (size_t q = 0; q < hv.size(); q += per) {
-                // heavy items of a segment are contiguous in `items` only between light
-                // runs, so heavy blocks index a compacted list (see below)
-                sblk.push_back(Block{(int64_t)q, (int64_t)std::min(hv.size(), q + per), s, 1});
-            }
-            (void)h;
-        }
-        seg_sblk_off[nseg] = (int32_t)sblk.size();
-        // compact the item list to the heavy sub-items only, segment by segment, and
-        // rebase the heavy blocks onto it
-        std::vector<SpItem> heavy;
-        std::vector<int64_t> seg_heavy_base(nseg + 1, 0);
-        for (int s = 0; s < nseg; ++s) {
-            seg_heavy_base[s] = (int64_t)heavy.size();
-            for (int64_t i = seg_item_off[s]; i < seg_item_off[s + 1]; ++i)
-                if (items[i].kind != 0) heavy.push_back(items[i]);
-        }
-        for (Block &bk : sblk)
-            if (bk.pad == 1) {
-                bk.i0 += seg_heavy_base[bk.seg];
-                bk.i1 += seg_heavy_base[bk.seg];
-            }
-        items.swap(heavy);
-    }
 
     std::vector<Block> vblk;
     std::vector<int32_t> seg_vblk_off(nseg + 1, 0);
@@ -537,12 +502,12 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     for (int s = 0; s < nseg; ++s) rows_tot += g->h_seg_end[s] - g->h_seg_begin[s];
     for (int s = 0; s < nseg; ++s) {
         seg_vblk_off[s] = (int32_t)vblk.size();
-        const int64_t a = g->h_seg_begin[s], b = g->h_seg_end[s], rows = b - a;
-        int64_t nb = (int64_t)((double)T * rows / (rows_tot > 0 ? rows_tot : 1) + 0.5);
-        const int64_t maxb = std::max<int64_t>(1, (rows * KT + 1023) / 1024);
+        const int64_t a = g->h_seg_begin[s], b = g->h_seg_end[s], nr = b - a;
+        int64_t nb = (int64_t)((double)T * nr / (rows_tot > 0 ? rows_tot : 1) + 0.5);
+        const int64_t maxb = std::max<int64_t>(1, (nr * KT + 2047) / 2048);
         nb = std::max<int64_t>(1, std::min<int64_t>(nb, maxb));
         for (int64_t k = 0; k < nb; ++k)
-            vblk.push_back(Block{a + rows * k / nb, a + rows * (k + 1) / nb, s, 0});
+            vblk.push_back(Block{a + nr * k / nb, a + nr * (k + 1) / nb, s, 0});
     }
     seg_vblk_off[nseg] = (int32_t)vblk.size();
 
@@ -551,6 +516,8 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     pl->n_heavy = nheavy;
     pl->n_chunks = nchunks;
     pl->n_vblk = (int64_t)vblk.size();
+    pl->n_slices = (int64_t)sl_base.size() - 1;
+    pl->n_sl_entries = sl_base.back();
     auto up = [&](DevBuf &d, const void *h, size_t bytes) -> int {
         NVD_TRY(d.alloc(bytes));
         if (bytes) NVD_TRY_CUDA(cudaMemcpy(d.p, h, bytes, cudaMemcpyHostToDevice));
@@ -564,6 +531,31 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     NVD_TRY(up(pl->seg_vblk_off, seg_vblk_off.data(), seg_vblk_off.size() * 4));
     NVD_TRY(pl->hcount.alloc((size_t)std::max<int32_t>(nheavy, 1) * 4));
     NVD_TRY_CUDA(cudaMemset(pl->hcount.p, 0, pl->hcount.bytes));
+    NVD_TRY(up(pl->sl_base, sl_base.data(), sl_base.size() * 8));
+    NVD_TRY(up(pl->sl_row, sl_row.data(), sl_row.size() * 4));
+    const bool w64 = szv == 8 && g->wdtype == NVD_F64;
+    const int64_t ne = std::max<int64_t>(pl->n_sl_entries, 1);
+    NVD_TRY(pl->sl_col.alloc((size_t)ne * 4));
+    NVD_TRY(pl->sl_w.alloc((size_t)ne * (w64 ? 8 : 4)));
+    if (pl->n_slices > 0) {
+        const int grid = grid_for(pl->n_slices * H, 1, g->num_sms);
+        const int64_t *rpd = g->rowptr.as<int64_t>();
+        const int32_t *cid = g->colidx.as<int32_t>();
+        const int64_t *sb = pl->sl_base.as<int64_t>();
+        const int32_t *sr = pl->sl_row.as<int32_t>();
+        int32_t *sc = pl->sl_col.as<int32_t>();
+        if (g->wdtype == NVD_F64 && w64)
+            k_fill_slices<double, double><<<grid, 256>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<double>(), sc,
+                                                         pl->sl_w.as<double>());
+        else if (g->wdtype == NVD_F64)
+            k_fill_slices<double, float><<<grid, 256>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<double>(), sc,
+                                                        pl->sl_w.as<float>());
+        else
+            k_fill_slices<float, float><<<grid, 256>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<float>(), sc,
+                                                       pl->sl_w.as<float>());
+        NVD_TRY_CUDA(cudaGetLastError());
+        NVD_TRY_CUDA(cudaDeviceSynchronize());
+    }
     *out = pl.get();
     g->plans[key] = std::move(pl);
     return NVD_OK;
@@ -593,6 +585,11 @@ void set_sp_plan(Ctx *c, const Plan *pl) {
     c->seg_sblk_off = pl->seg_sblk_off.as<int32_t>();
     c->seg_heavy_off = pl->seg_heavy_off.as<int32_t>();
     c->hcount = pl->hcount.as<int32_t>();
+    c->sl_base = pl->sl_base.as<int64_t>();
+    c->sl_row = pl->sl_row.as<int32_t>();
+    c->sl_col = pl->sl_col.as<int32_t>();
+    c->sl_w = pl->sl_w.p;
+    c->sl_h = sp_slice_rows(pl->KT, pl->szv);
 }
 
 void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c) {
@@ -609,7 +606,6 @@ void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c) {
     c->seg_end = g->seg_end.as<int64_t>();
     c->seg_owner = g->seg_owner.as<int32_t>();
     c->perm = g->perm.as<int32_t>();
-    c->spmv_group = g->spmv_group;
     if (pl) {
         set_sp_plan(c, pl);
         c->vblk = pl->vblk.as<Block>();
@@ -639,7 +635,8 @@ int64_t nvd_graph_s::device_bytes() const {
     for (auto &kv : plans)
         for (const nvd::DevBuf *d : {&kv.second->items, &kv.second->sblk, &kv.second->vblk,
                                      &kv.second->seg_sblk_off, &kv.second->seg_heavy_off,
-                                     &kv.second->seg_vblk_off, &kv.second->hcount})
+                                     &kv.second->seg_vblk_off, &kv.second->hcount, &kv.second->sl_base,
+                                     &kv.second->sl_row, &kv.second->sl_col, &kv.second->sl_w})
             b += (int64_t)d->bytes;
     for (auto &kv : ws) b += (int64_t)kv.second->bytes;
     return b;
@@ -848,14 +845,6 @@ static int graph_create_impl(nvd_graph_t *out, int64_t n, int64_t nnz, const int
     }
     NVD_TRY(run_degree(g.get(), s));
     NVD_TRY_CUDA(cudaStreamSynchronize(s));
-    // default group size of the single-RHS SpMV from the mean row length of the
-    // rows that belong to a segment (two entries per lane per pass)
-    {
-        int64_t rows = 0;
-        for (int s2 = 0; s2 < g->nseg; ++s2) rows += g->h_seg_end[s2] - g->h_seg_begin[s2];
-        const double mean = rows ? (double)g->nnz / (double)rows : 0.0;
-        g->spmv_group = mean <= 8 ? 1 : mean <= 16 ? 2 : mean <= 32 ? 4 : mean <= 64 ? 8 : 16;
-    }
     *out = g.release();
     return NVD_OK;
 }

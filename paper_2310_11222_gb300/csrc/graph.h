@@ -57,7 +57,9 @@ struct DevBuf {
 struct Plan {
     int KT = 0, szv = 0, sza = 0;
     int64_t n_items = 0, n_sblk = 0, n_heavy = 0, n_chunks = 0, n_vblk = 0;
+    int64_t n_slices = 0, n_sl_entries = 0;
     DevBuf items, sblk, vblk, seg_sblk_off, seg_heavy_off, seg_vblk_off, hcount;
+    DevBuf sl_base, sl_row, sl_col, sl_w;   // sliced light rows (weights in the plan's TW)
     int64_t part_slots() const {
         int64_t a = n_sblk + n_heavy;
         return a > n_vblk ? a : n_vblk;
@@ -79,7 +81,6 @@ struct nvd_graph_s {
     nvd::DevBuf perm;            // int32 internal -> user node; empty when identity
     nvd::DevBuf uent;            // int64 user entry -> internal entry (-1 dropped); empty when identity
     int32_t ncomp = 0, nseg = 0;
-    int32_t spmv_group = 4;      // lanes per row of the single-RHS SpMV (autotuned, see tune.cu)
     int64_t n_singleton = 0;
     std::vector<int64_t> h_rowptr, h_seg_begin, h_seg_end;
     nvd::DevBuf seg_begin, seg_end, seg_owner;

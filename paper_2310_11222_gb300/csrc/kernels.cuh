@@ -144,11 +144,30 @@ template <> __device__ __forceinline__ const double *deg_of<double>(const Ctx &c
 
 // Block-wide per-column sums.  Thread t holds acc[d][v] for column
 // (t % CG) * VEC + v.  On return tot[d * KT + j] (shared) holds the block total,
-// summed in a fixed order (warp butterfly, then warps 0..7).
+// summed in a fixed order (KT = 1: per lane over the warps, then a butterfly;
+// KT > 1: warp butterfly, then warps 0..7).
 template <int ND, int KT, int VEC>
 __device__ __forceinline__ void block_reduce_cols(double (&acc)[ND > 0 ? ND : 1][VEC], double *red,
                                                   double *tot) {
-    if constexpr (ND > 0) {
+    if constexpr (ND > 0 && KT == 1) {
+        // one column: each sum's NT partials go to shared memory and warp d adds
+        // sum d (lane l: partials l, l+32, ... in order, then a butterfly), which
+        // takes far fewer FP64 instructions than a butterfly in every warp
+        static_assert(ND <= 4, "reduction scratch holds 4 sums");
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) red[d * NT + threadIdx.x] = acc[d][0];
+        __syncthreads();
+        if (warp < ND) {
+            double s = red[warp * NT + lane];
+#pragma unroll
+            for (int k = 1; k < NWARP; ++k) s += red[warp * NT + k * 32 + lane];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(NVD_FULLMASK, s, off);
+            if (lane == 0) tot[warp] = s;
+        }
+        __syncthreads();
+    } else if constexpr (ND > 0) {
         constexpr int CG = KT / VEC;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -653,7 +672,6 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double *red = reinterpret_cast<double *>(smem);
     double *tot = red + red_doubles(1);
-    const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
     const TA *__restrict__ deg = deg_of<TA>(c);
     const Block blk = c.sblk[b];
     const int seg = blk.seg;
@@ -663,47 +681,68 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
     const bool live = !Epi::NEEDS_LIVE || seg_live<1>(c, seg);
     if (live) {
         if (blk.pad == 0) {
-            // light rows [i0, i1) (a run of rows of at most sp_row_max entries): each
-            // warp's 32/G groups of G lanes take one row each, rows dealt across the
-            // warps; the lanes stride over the row SPMV1_UNROLL entries at a time,
-            // a butterfly inside the group adds them and the group's first lane
-            // applies the row epilogue
-            const int G = c.spmv_group;
-            const int ngw = 32 / G, gl = lane & (G - 1), gid = lane / G;
-            for (int64_t base = blk.i0 + warp * ngw; base < blk.i1; base += NWARP * ngw) {
-                const int64_t i = base + gid;
-                const bool valid = i < blk.i1;
-                constexpr int U = SPMV1_UNROLL;
-                TA a[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) a[u] = 0;
+            // light slices [i0, i1): a warp takes one slice of 32 rows at a time, one
+            // row per lane; entry j of the 32 rows is one coalesced load of columns
+            // and of weights, the gathers of SPMV1_UNROLL entries are in flight
+            // before their products, and each lane adds its row's products in entry
+            // order into one accumulator (no cross-lane sum)
+            const TW *__restrict__ slw = reinterpret_cast<const TW *>(c.sl_w);
+            const int64_t ns = blk.i1 - blk.i0;
+            for (int64_t round = 0; round * NWARP < ns; ++round) {
+                // longest slices first; alternate rounds reverse the warp order so
+                // the warps' totals even out
+                const int64_t q = round * NWARP + ((round & 1) ? NWARP - 1 - warp : warp);
+                if (q >= ns) continue;
+                const int64_t sl = blk.i0 + q;
+                const int64_t base = __ldg(c.sl_base + sl);
+                const int L = (int)((__ldg(c.sl_base + sl + 1) - base) >> 5);
+                const int32_t i = __ldg(c.sl_row + sl * 32 + lane);
                 TV own[1] = {(TV)0};
                 TA dg = 0;
-                if (valid) {
-                    const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
-                    if (gl == 0) {
-                        own[0] = LD::ld(src + i);
-                        dg = __ldg(deg + i);
+                if (i >= 0) {
+                    own[0] = LD::ld(src + i);
+                    dg = __ldg(deg + i);
+                }
+                const int32_t *__restrict__ cp = c.sl_col + base + lane;
+                const TW *__restrict__ wp = slw + base + lane;
+                // L is the same for the whole warp, so the bounds tests below are
+                // uniform branches (the last step issues only its valid entries,
+                // all of them in flight together)
+                constexpr int U = SPMV1_UNROLL;
+                TA acc = 0;
+                int cu[U] = {};
+                TW wu[U] = {};
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (u < L) {
+                        cu[u] = __ldcs(cp + u * 32);
+                        wu[u] = __ldcs(wp + u * 32);
                     }
-                    for (int64_t e = e0 + gl; e < e1; e += (int64_t)U * G) {
-                        int cu[U];
-                        TW wu[U];
+                for (int j = 0; j < L; j += U) {
+                    // the next step's columns and weights are loaded while this
+                    // step's gathers are in flight
+                    int cn[U] = {};
+                    TW wn[U] = {};
 #pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            const bool in = e + (int64_t)u * G < e1;
-                            cu[u] = in ? __ldcs(c.colidx + e + (int64_t)u * G) : -1;
-                            wu[u] = in ? __ldcs(w + e + (int64_t)u * G) : (TW)0;
+                    for (int u = 0; u < U; ++u)
+                        if (j + U + u < L) {
+                            cn[u] = __ldcs(cp + (j + U + u) * 32);
+                            wn[u] = __ldcs(wp + (j + U + u) * 32);
                         }
+                    TV pv[U];
 #pragma unroll
-                        for (int u = 0; u < U; ++u)
-                            if (cu[u] >= 0) a[u] += (TA)wu[u] * (TA)LD::ld(src + cu[u]);
+                    for (int u = 0; u < U; ++u)
+                        if (j + u < L) pv[u] = LD::ld(src + cu[u]);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (j + u < L) acc += (TA)wu[u] * (TA)pv[u];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        cu[u] = cn[u];
+                        wu[u] = wn[u];
                     }
                 }
-                TA acc = a[0];
-#pragma unroll
-                for (int u = 1; u < U; ++u) acc += a[u];
-                for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(NVD_FULLMASK, acc, off);
-                if (valid && gl == 0) {
+                if (i >= 0) {
                     const TA av[1] = {acc};
                     epi.template elem<TV, TA, 1>(c, i, 0, 1, own, av, dg, dst, dot);
                 }
@@ -739,7 +778,6 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
     TA *s_acc = reinterpret_cast<TA *>(smem);
     double *red = reinterpret_cast<double *>(smem + C::RB * KT * sizeof(TA));
     double *tot = red + C::RED;
-    const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Block blk = c.sblk[b];
     const int seg = blk.seg;
@@ -753,53 +791,54 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
     const bool live = !Epi::NEEDS_LIVE || seg_live<KT>(c, seg);
     if (live) {
         if (blk.pad == 0) {
-            // light rows [i0, i1): a group of LPR lanes owns one row, lane `sub` of the
-            // group owns columns col0..col0+VEC-1, so a row needs no cross-lane sum;
-            // each warp runs G rows at a time, SPMM_UNROLL gathered neighbour rows in
-            // flight per group, and no CTA barrier until the final reduction
+            // light slices [i0, i1): a warp takes one slice of G rows at a time; the
+            // LPR lanes of group `gid` own its row gid, lane `sub` of the group
+            // columns col0..col0+VEC-1, so a row needs no cross-lane sum; entry j of
+            // the G rows is one load of columns and of weights, SPMM_UNROLL gathered
+            // neighbour rows are in flight, products are added in entry order
             const int gid = lane / LPR, col0 = (lane % LPR) * VEC;
             const TA *__restrict__ deg = deg_of<TA>(c);
-            for (int64_t base = blk.i0 + warp * G; base < blk.i1; base += NWARP * G) {
-                const int64_t i = base + gid;
-                if (i < blk.i1) {
-                    const int64_t e0 = __ldg(c.rowptr + i), e1 = __ldg(c.rowptr + i + 1);
-                    TV own[VEC];
-                    ldv<LD, TV, VEC>(src + i * KT + col0, own);
-                    const TA dg = __ldg(deg + i);
-                    constexpr int U = SPMM_UNROLL;
-                    TA acc[U][VEC];
+            const TW *__restrict__ slw = reinterpret_cast<const TW *>(c.sl_w);
+            const int64_t ns = blk.i1 - blk.i0;
+            for (int64_t round = 0; round * NWARP < ns; ++round) {
+                const int64_t q = round * NWARP + ((round & 1) ? NWARP - 1 - warp : warp);
+                if (q >= ns) continue;
+                const int64_t sl = blk.i0 + q;
+                const int64_t base = __ldg(c.sl_base + sl);
+                const int L = (int)((__ldg(c.sl_base + sl + 1) - base) / G);
+                const int32_t i = __ldg(c.sl_row + sl * G + gid);
+                TV own[VEC];
+                TA dg = 0;
+                if (i >= 0) {
+                    ldv<LD, TV, VEC>(src + (int64_t)i * KT + col0, own);
+                    dg = __ldg(deg + i);
+                }
+                const int32_t *__restrict__ cp = c.sl_col + base + gid;
+                const TW *__restrict__ wp = slw + base + gid;
+                constexpr int U = SPMM_UNROLL;
+                TA acc[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] = 0;
+                for (int j = 0; j < L; j += U) {   // uniform bounds tests, as for KT = 1
+                    int cu[U];
+                    TA wu[U];
+                    TV pv[U][VEC];
 #pragma unroll
                     for (int u = 0; u < U; ++u)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[u][v] = 0;
-                    for (int64_t e = e0; e < e1; e += U) {
-                        int cu[U];
-                        TA wu[U];
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            const bool in = e + u < e1;
-                            cu[u] = in ? __ldcs(c.colidx + e + u) : -1;
-                            wu[u] = in ? (TA)__ldcs(w + e + u) : (TA)0;
+                        if (j + u < L) {
+                            cu[u] = __ldcs(cp + (j + u) * G);
+                            wu[u] = (TA)__ldcs(wp + (j + u) * G);
                         }
 #pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            if (cu[u] >= 0) {
-                                TV pv[VEC];
-                                ldv<LD, TV, VEC>(src + (int64_t)cu[u] * KT + col0, pv);
+                    for (int u = 0; u < U; ++u)
+                        if (j + u < L) ldv<LD, TV, VEC>(src + (int64_t)cu[u] * KT + col0, pv[u]);
 #pragma unroll
-                                for (int v = 0; v < VEC; ++v) acc[u][v] += wu[u] * (TA)pv[v];
-                            }
-                        }
-                    }
-                    TA sum[VEC];
+                    for (int u = 0; u < U; ++u)
+                        if (j + u < L)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        sum[v] = acc[0][v];
-#pragma unroll
-                        for (int u = 1; u < U; ++u) sum[v] += acc[u][v];
-                    }
-                    epi.template elem<TV, TA, VEC>(c, i, col0, KT, own, sum, dg, dst, dot);
+                            for (int v = 0; v < VEC; ++v) acc[v] += wu[u] * (TA)pv[u][v];
                 }
+                if (i >= 0) epi.template elem<TV, TA, VEC>(c, i, col0, KT, own, acc, dg, dst, dot);
             }
         } else {
             // heavy block: chunks of split rows, each taken by the whole CTA

@@ -10,6 +10,10 @@ namespace nvd {
 template <class TV, class TW, class TA, int KT, class TX>
 static int launch_persistent(nvd_graph_s *g, const Ctx &c, const PersistArgs &a, cudaStream_t s) {
     auto kern = k_persistent<TV, TW, TA, KT, TX>;
+    if (c.sl_h != sp_slice_rows(KT, (int)sizeof(TV))) {
+        set_error("internal: SpMV plan built for another tile width or precision");
+        return NVD_ERR_UNSUPPORTED;
+    }
     int per_sm = 0;
     NVD_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0));
     if (per_sm < 1) {

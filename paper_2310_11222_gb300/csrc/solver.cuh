@@ -22,14 +22,26 @@ namespace nvd {
 
 // ------------------------------------------------------------------ kernels
 
+// Resident CTAs per SM the register allocation must allow (the SpMV and the vector
+// passes are latency bound: more resident warps keep more loads in flight).
+#ifndef NVD_SPMV1_MINB
+#define NVD_SPMV1_MINB 4
+#endif
+#ifndef NVD_SPMM_MINB
+#define NVD_SPMM_MINB 4
+#endif
+#ifndef NVD_VEC_MINB
+#define NVD_VEC_MINB 4
+#endif
+
 template <class TV, class TW, class TA, int KT, class Epi>
-__global__ void __launch_bounds__(NT) k_spmm(Ctx c, Epi epi, const TV *src, TV *dst) {
+__global__ void __launch_bounds__(NT, KT == 1 ? NVD_SPMV1_MINB : NVD_SPMM_MINB) k_spmm(Ctx c, Epi epi, const TV *src, TV *dst) {
     __shared__ __align__(16) char smem[dev::SpCfg<TV, TA, KT>::SMEM];
     dev::spmm_block<dev::LdRO, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, smem);
 }
 
 template <class TV, int KT, class Op>
-__global__ void __launch_bounds__(NT) k_vec(Ctx c, Op op) {
+__global__ void __launch_bounds__(NT, NVD_VEC_MINB) k_vec(Ctx c, Op op) {
     __shared__ __align__(16) char smem[vec_smem_bytes(KT)];
     dev::vec_block<TV, KT, Op>(c, op, blockIdx.x, smem);
 }
@@ -124,6 +136,10 @@ template <class TV, class TW, class TA, int KT, class Epi>
 inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cudaStream_t s,
                        double bytes) {
     if (c.n_sblk == 0) return NVD_OK;
+    if (c.sl_h != sp_slice_rows(KT, (int)sizeof(TV))) {
+        set_error("internal: SpMV plan built for another tile width or precision");
+        return NVD_ERR_UNSUPPORTED;
+    }
     const bool prof = prof_enabled();
     if (prof) prof_begin(s);
     k_spmm<TV, TW, TA, KT, Epi><<<(unsigned)c.n_sblk, NT, 0, s>>>(c, epi, src, dst);
