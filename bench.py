@@ -68,8 +68,10 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources that decide the SpMV kernel's code and its work layout."""
     h = hashlib.sha256()
-    for rel in ("paper_2310_11222_gb300/csrc/kernels.cuh", "paper_2310_11222_gb300/csrc/common.h"):
+    for rel in ("paper_2310_11222_gb300/csrc/kernels.cuh", "paper_2310_11222_gb300/csrc/common.h",
+                "paper_2310_11222_gb300/csrc/solver.cuh", "paper_2310_11222_gb300/csrc/graph.cu"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -78,14 +80,21 @@ def kernel_source_hash():
 def ncu_traffic():
     """DRAM bytes per SpMV launch from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "spmv_er_large_traffic.json")
+    p = os.path.join(ROOT, "profiles", "spmv_er_large_traffic.txt")
     if not os.path.exists(p):
         return None
+    d = {}
     with open(p) as f:
-        d = json.load(f)
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                d[k.strip()] = v.strip()
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    try:
+        return float(d["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 class ClockSampler:

@@ -345,6 +345,11 @@ int run_components(nvd_graph_s *g, std::vector<int32_t> &root, cudaStream_t s) {
 
 int target_blocks(const nvd_graph_s *g) { return 2 * g->num_sms * 8; }
 
+// CTAs per SM of one vector pass.
+#ifndef VEC_PER_SM
+#define VEC_PER_SM 2
+#endif
+
 uint64_t next_graph_id() {
     static std::atomic<uint64_t> ctr{1};
     return ctr.fetch_add(1);
@@ -496,15 +501,19 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     }
     seg_sblk_off[nseg] = (int32_t)sblk.size();
 
+    // Vector blocks: one wave of equal blocks, VEC_PER_SM per SM (the FP64 units
+    // are per SM, so every SM gets the same share), at least 1024 row-columns each,
+    // split over the segments in proportion to their rows.
     std::vector<Block> vblk;
     std::vector<int32_t> seg_vblk_off(nseg + 1, 0);
     int64_t rows_tot = 0;
     for (int s = 0; s < nseg; ++s) rows_tot += g->h_seg_end[s] - g->h_seg_begin[s];
+    const int64_t TV = (int64_t)VEC_PER_SM * g->num_sms;
     for (int s = 0; s < nseg; ++s) {
         seg_vblk_off[s] = (int32_t)vblk.size();
         const int64_t a = g->h_seg_begin[s], b = g->h_seg_end[s], nr = b - a;
-        int64_t nb = (int64_t)((double)T * nr / (rows_tot > 0 ? rows_tot : 1) + 0.5);
-        const int64_t maxb = std::max<int64_t>(1, (nr * KT + 2047) / 2048);
+        int64_t nb = (int64_t)((double)TV * nr / (rows_tot > 0 ? rows_tot : 1) + 0.5);
+        const int64_t maxb = std::max<int64_t>(1, (nr * KT + 1023) / 1024);
         nb = std::max<int64_t>(1, std::min<int64_t>(nb, maxb));
         for (int64_t k = 0; k < nb; ++k)
             vblk.push_back(Block{a + nr * k / nb, a + nr * (k + 1) / nb, s, 0});

@@ -858,273 +858,5 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
     }
 }
 
-// ------------------------------------------------------------------ vector passes
-
-// Generic streaming pass over rows [i0, i1) of one segment.  Op provides ND,
-// NEEDS_LIVE, a register type R, setup(c, seg, col0), load(c, i, col0, R&) and
-// apply(c, i, col0, R&, dot).  Each thread handles U lane-vectors per trip with all
-// U loads issued before the first use.
-template <class TV, int KT, class Op>
-__device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
-    constexpr int VEC = VecCfg<TV, KT>::VEC, CG = KT / VEC, ND = Op::ND, U = 4;
-    double *red = reinterpret_cast<double *>(smem);
-    double *tot = red + red_doubles(KT);
-    const Block blk = c.vblk[b];
-    const int seg = blk.seg;
-    const int col0 = (int)(threadIdx.x % CG) * VEC;
-    double dot[ND > 0 ? ND : 1][VEC];
-#pragma unroll
-    for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) dot[d][v] = 0.0;
-    if (!Op::NEEDS_LIVE || seg_live<KT>(c, seg)) {
-        op.setup(c, seg, col0);
-        const int64_t t1 = blk.i1 * CG;
-        for (int64_t t = blk.i0 * CG + threadIdx.x; t < t1; t += (int64_t)NT * U) {
-            typename Op::R regs[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t tu = t + (int64_t)u * NT;
-                if (tu < t1) op.load(c, tu / CG, col0, regs[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t tu = t + (int64_t)u * NT;
-                if (tu < t1) op.apply(c, tu / CG, col0, regs[u], dot);
-            }
-        }
-    }
-    if constexpr (ND > 0) {
-        block_reduce_cols<ND, KT, VEC>(dot, red, tot);
-        const int64_t s0 = c.seg_vblk_off[seg];
-        const int32_t cnt = c.seg_vblk_off[seg + 1] - (int32_t)s0;
-        seg_arrive<ND, KT>(c, op.fin, seg, b, tot, s0, cnt, 0, 0, red);
-    }
-}
-
-// delta = x - y for this tile (user layout [k][n], optional node permutation) into
-// [n][KT] FP64; per-segment sums for the projection.
-template <class TX, int KT>
-struct OpFormDelta {
-    static constexpr int ND = 1, VEC = VecCfg<double, KT>::VEC;
-    static constexpr bool NEEDS_LIVE = false;
-    struct R { double d[VEC]; };
-    double *delta;
-    FinMean fin;
-    const TX *X, *Y;
-    int64_t base, ld;
-    int kc;
-    __device__ void setup(const Ctx &c, int seg, int) {
-        const Owner &o = owner_of(c, seg);
-        X = reinterpret_cast<const TX *>(o.x);
-        Y = reinterpret_cast<const TX *>(o.y);
-        base = o.base;
-        ld = o.ld;
-        kc = o.kc;
-    }
-    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &r) const {
-        const int64_t u = (c.perm ? (int64_t)__ldg(c.perm + i) : i) - base;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            const int j = col0 + v;
-            r.d[v] = j < kc ? (double)__ldg(X + (int64_t)j * ld + u) - (double)__ldg(Y + (int64_t)j * ld + u) : 0.0;
-        }
-    }
-    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &r, double (&dot)[1][VEC]) const {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) dot[0][v] += r.d[v];
-        stv(delta + i * KT + col0, r.d);
-    }
-};
-
-// PCG start from x = 0: r = P src (src minus its segment mean, optionally written
-// back), u = D^-1 r, p = u; r^T u and |r|^2.
-template <class TV, int KT, class LD = LdPlain>
-struct OpInit {
-    static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
-    static constexpr bool NEEDS_LIVE = false;
-    struct R { double s[VEC]; TV di; };
-    const double *src;
-    double *writeback;
-    TV *x, *r, *p;
-    FinInit fin;
-    double mu[VEC];
-    __device__ void setup(const Ctx &c, int seg, int col0) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) mu[v] = __ldcg(c.mean + (int64_t)seg * KT + col0 + v);
-    }
-    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &q) const {
-        ldv<LD, double, VEC>(src + i * KT + col0, q.s);
-        q.di = __ldg(dinv_of<TV>(c) + i);
-    }
-    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &q, double (&dot)[2][VEC]) const {
-        const int64_t o = i * KT + col0;
-        TV rv[VEC], uv[VEC], zv[VEC];
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            q.s[v] -= mu[v];
-            rv[v] = (TV)q.s[v];
-            uv[v] = q.di * rv[v];
-            zv[v] = (TV)0;
-            dot[0][v] += (double)rv[v] * (double)uv[v];
-            dot[1][v] += (double)rv[v] * (double)rv[v];
-        }
-        if (writeback) stv(writeback + o, q.s);
-        stv(r + o, rv);
-        stv(p + o, uv);
-        stv(x + o, zv);
-    }
-};
-
-// x += alpha p, r -= alpha q, u = D^-1 r; r^T u and |r|^2.
-template <class TV, int KT, class LD = LdPlain>
-struct OpUpdate {
-    static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
-    static constexpr bool NEEDS_LIVE = true;
-    struct R { TV x[VEC], r[VEC], p[VEC], q[VEC]; TV di; };
-    TV *x, *r;
-    const TV *p, *q;
-    FinBeta fin;
-    TV al[VEC];
-    __device__ void setup(const Ctx &c, int seg, int col0) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) al[v] = (TV)__ldcg(c.alpha + (int64_t)seg * KT + col0 + v);
-    }
-    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &g) const {
-        const int64_t o = i * KT + col0;
-        ldv<LD, TV, VEC>(x + o, g.x);
-        ldv<LD, TV, VEC>(r + o, g.r);
-        ldv<LD, TV, VEC>(p + o, g.p);
-        ldv<LD, TV, VEC>(q + o, g.q);
-        g.di = __ldg(dinv_of<TV>(c) + i);
-    }
-    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&dot)[2][VEC]) const {
-        const int64_t o = i * KT + col0;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            g.x[v] += al[v] * g.p[v];
-            g.r[v] -= al[v] * g.q[v];
-            const TV u = g.di * g.r[v];
-            dot[0][v] += (double)g.r[v] * (double)u;
-            dot[1][v] += (double)g.r[v] * (double)g.r[v];
-        }
-        stv(x + o, g.x);
-        stv(r + o, g.r);
-    }
-};
-
-// p = D^-1 r + beta p on the columns still iterating.
-template <class TV, int KT, class LD = LdPlain>
-struct OpDir {
-    static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
-    static constexpr bool NEEDS_LIVE = true;
-    struct R { TV r[VEC], p[VEC]; TV di; };
-    const TV *r;
-    TV *p;
-    FinNone fin;
-    TV be[VEC];
-    bool act[VEC];
-    __device__ void setup(const Ctx &c, int seg, int col0) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            be[v] = (TV)__ldcg(c.beta + (int64_t)seg * KT + col0 + v);
-            act[v] = __ldcg(c.active + (int64_t)seg * KT + col0 + v) != 0;
-        }
-    }
-    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &g) const {
-        const int64_t o = i * KT + col0;
-        ldv<LD, TV, VEC>(r + o, g.r);
-        ldv<LD, TV, VEC>(p + o, g.p);
-        g.di = __ldg(dinv_of<TV>(c) + i);
-    }
-    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) g.p[v] = act[v] ? g.di * g.r[v] + be[v] * g.p[v] : g.p[v];
-        stv(p + i * KT + col0, g.p);
-    }
-};
-
-// sum of x and delta^T x per segment (end of solve).
-template <class TV, int KT, class LD = LdPlain>
-struct OpFinal {
-    static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
-    static constexpr bool NEEDS_LIVE = false;
-    struct R { TV x[VEC]; double d[VEC]; };
-    const TV *x;
-    const double *delta;
-    FinFinal fin;
-    __device__ void setup(const Ctx &, int, int) {}
-    __device__ __forceinline__ void load(const Ctx &, int64_t i, int col0, R &g) const {
-        const int64_t o = i * KT + col0;
-        ldv<LD, TV, VEC>(x + o, g.x);
-        ldv<LD, double, VEC>(delta + o, g.d);
-    }
-    __device__ __forceinline__ void apply(const Ctx &, int64_t, int, R &g, double (&dot)[2][VEC]) const {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            dot[0][v] += (double)g.x[v];
-            dot[1][v] += g.d[v] * (double)g.x[v];
-        }
-    }
-};
-
-// z_out = src - mean_seg(src) in the user layout [k][n] (optionally permuted).
-template <class TS, class TZ, int KT, class LD = LdPlain>
-struct OpZout {
-    static constexpr int ND = 0, VEC = VecCfg<TS, KT>::VEC;
-    static constexpr bool NEEDS_LIVE = false;
-    struct R { TS s[VEC]; };
-    const TS *src;
-    const double *meanv;
-    FinNone fin;
-    TZ *Z;
-    int64_t base, ld;
-    int kc;
-    double mu[VEC];
-    __device__ void setup(const Ctx &c, int seg, int col0) {
-        const Owner &o = owner_of(c, seg);
-        Z = reinterpret_cast<TZ *>(o.z);
-        base = o.base;
-        ld = o.ld;
-        kc = o.kc;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) mu[v] = __ldcg(meanv + (int64_t)seg * KT + col0 + v);
-    }
-    __device__ __forceinline__ void load(const Ctx &, int64_t i, int col0, R &g) const {
-        ldv<LD, TS, VEC>(src + i * KT + col0, g.s);
-    }
-    __device__ __forceinline__ void apply(const Ctx &c, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
-        if (!Z) return;
-        const int64_t u = (c.perm ? (int64_t)__ldg(c.perm + i) : i) - base;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            const int j = col0 + v;
-            if (j < kc) Z[(int64_t)j * ld + u] = (TZ)((double)g.s[v] - mu[v]);
-        }
-    }
-};
-
-// z64 += x (FP32 correction of one refinement step, accumulated in FP64).
-template <class TV, int KT, class LD = LdPlain>
-struct OpAccum {
-    static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
-    static constexpr bool NEEDS_LIVE = false;
-    struct R { TV x[VEC]; double z[VEC]; };
-    const TV *x;
-    double *z;
-    FinNone fin;
-    __device__ void setup(const Ctx &, int, int) {}
-    __device__ __forceinline__ void load(const Ctx &, int64_t i, int col0, R &g) const {
-        const int64_t o = i * KT + col0;
-        ldv<LD, TV, VEC>(x + o, g.x);
-        ldv<LD, double, VEC>(z + o, g.z);
-    }
-    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) g.z[v] += (double)g.x[v];
-        stv(z + i * KT + col0, g.z);
-    }
-};
-
 }  // namespace dev
 }  // namespace nvd

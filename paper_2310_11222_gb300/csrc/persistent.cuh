@@ -9,7 +9,7 @@
 // Laplacian of G graphs, each (graph, pair) with its own CG scalars.
 #pragma once
 
-#include "kernels.cuh"
+#include "vecops.cuh"
 
 namespace nvd {
 namespace dev {

@@ -13,10 +13,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "graph.h"
-#include "kernels.cuh"
+#include "vecops.cuh"
 
 namespace nvd {
 
@@ -34,16 +35,48 @@ namespace nvd {
 #define NVD_VEC_MINB 4
 #endif
 
+// The iteration's kernels are launched with programmatic dependent launch: each
+// lets the next kernel in the stream be scheduled as soon as all its own CTAs are
+// running (so the next kernel's CTAs fill the SMs its tail leaves idle), and each
+// waits for the previous kernel to complete, with its writes visible, before it
+// touches any data (griddepcontrol; a no-op for a plain launch).
+#ifndef NVD_USE_PDL
+#define NVD_USE_PDL 1
+#endif
+__device__ __forceinline__ void pdl_trigger_and_wait() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <class TV, class TW, class TA, int KT, class Epi>
 __global__ void __launch_bounds__(NT, KT == 1 ? NVD_SPMV1_MINB : NVD_SPMM_MINB) k_spmm(Ctx c, Epi epi, const TV *src, TV *dst) {
     __shared__ __align__(16) char smem[dev::SpCfg<TV, TA, KT>::SMEM];
+    pdl_trigger_and_wait();
     dev::spmm_block<dev::LdRO, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, smem);
 }
 
 template <class TV, int KT, class Op>
 __global__ void __launch_bounds__(NT, NVD_VEC_MINB) k_vec(Ctx c, Op op) {
     __shared__ __align__(16) char smem[vec_smem_bytes(KT)];
+    pdl_trigger_and_wait();
     dev::vec_block<TV, KT, Op>(c, op, blockIdx.x, smem);
+}
+
+// Launch one of the kernels above on NT threads, with the programmatic-dependent-
+// launch attribute when enabled.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = NVD_USE_PDL ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 // Per (owner, column): sum d^2 and residual norms over the owner's segments, the
@@ -142,10 +175,9 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
     }
     const bool prof = prof_enabled();
     if (prof) prof_begin(s);
-    k_spmm<TV, TW, TA, KT, Epi><<<(unsigned)c.n_sblk, NT, 0, s>>>(c, epi, src, dst);
+    NVD_TRY_CUDA(launch_dependent(k_spmm<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, s, c, epi, src, dst));
     note_launch();
     if (prof) prof_end(s, bytes);
-    NVD_TRY_CUDA(cudaGetLastError());
     return NVD_OK;
 }
 
@@ -154,10 +186,9 @@ inline int launch_vec(const Ctx &c, const Op &op, cudaStream_t s) {
     if (c.n_vblk == 0) return NVD_OK;
     const bool prof = prof_vec_enabled();
     if (prof) prof_begin(s, 1);
-    k_vec<TV, KT, Op><<<(unsigned)c.n_vblk, NT, 0, s>>>(c, op);
+    NVD_TRY_CUDA(launch_dependent(k_vec<TV, KT, Op>, (unsigned)c.n_vblk, s, c, op));
     if (prof) prof_end(s, 0.0);
     note_launch();
-    NVD_TRY_CUDA(cudaGetLastError());
     return NVD_OK;
 }
 
