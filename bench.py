@@ -41,6 +41,8 @@ UNIT = "distances/s"
 PAIRS_PER_STEP = 8
 RTOL = 1e-10
 CHECK_EVERY = 2   # PCG iterations between the host's convergence polls (polled one batch behind)
+MIXED_RTOL_IN = 1e-4   # inner FP32 solve tolerance of the mixed-precision comparison
+MIXED_D2_RTOL = 1e-8   # its refinement stop (relative change of d^2)
 
 
 def workload_config(g, n0):
@@ -222,6 +224,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS comparison runs")
+    ap.add_argument("--no-tune", action="store_true", help="default work decomposition (no autotuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -251,6 +254,8 @@ def main():
     g = wl.graph
     X, Y = wl.pairs(rank * PAIRS_PER_STEP, PAIRS_PER_STEP)     # each rank its own pairs
     G = nvd.Graph.from_csr(g)
+    # work decomposition picked by the autotuner on this graph (set-up, not timed)
+    tuning = None if args.no_tune else G.tune(mode=nvd.MODE_FP64, k=PAIRS_PER_STEP, single_rhs=True)
     xt = torch.from_numpy(X).to(dev)
     yt = torch.from_numpy(Y).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -332,9 +337,13 @@ def main():
             b.record()
             torch.cuda.synchronize()
             return PAIRS_PER_STEP * reps / (a.elapsed_time(b) / 1e3), out
+        tune64 = None if args.no_tune else G.tune(mode=nvd.MODE_FP64, k=PAIRS_PER_STEP)
         r64, d64 = rate(rtol=RTOL)
-        rmx, dmx = rate(mode=nvd.MODE_MIXED, rtol=1e-4, d2_rtol=1e-10)
+        tunemx = None if args.no_tune else G.tune(mode=nvd.MODE_MIXED, k=PAIRS_PER_STEP)
+        rmx, dmx = rate(mode=nvd.MODE_MIXED, rtol=MIXED_RTOL_IN, d2_rtol=MIXED_D2_RTOL)
         extra = {"fp64_multi_rhs_distances_per_s": r64, "mixed_multi_rhs_distances_per_s": rmx,
+                 "mixed": f"FP32 block-PCG to rtol {MIXED_RTOL_IN} inside FP64 refinement to d2_rtol {MIXED_D2_RTOL}",
+                 "tuning_fp64_multi": tune64, "tuning_mixed": tunemx,
                  "d2_fp64_multi": d64.cpu().numpy().tolist(), "d2_mixed": dmx.cpu().numpy().tolist()}
 
     value = PAIRS_PER_STEP * world * args.steps / (total_ms / 1e3)
@@ -346,7 +355,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(g, wl.meta["n_generated"]),
+        "config": dict(workload_config(g, wl.meta["n_generated"]), tuning=tuning),
         "e2e": {"value": PAIRS_PER_STEP * world * args.steps / te, "unit": UNIT,
                 "h2d_bytes_per_step": int(xh.numel() * 8 * 2), "d2h_bytes_per_step": PAIRS_PER_STEP * 8},
         "gpu_launches": int(launches),

@@ -141,6 +141,53 @@ typedef struct {
  * max_refine 8, check_every 4, kt automatic, no flags. */
 void nvd_solve_opts_default(nvd_solve_opts *o);
 
+/* ------------------------------------------------------------------ tuning */
+
+#define NVD_TUNE_SINGLE_RHS 1u   /* tune for one right-hand side at a time (tile width 1) */
+
+typedef struct {
+    int32_t kt;            /* chosen right-hand sides per tile */
+    int32_t row_max_pct;   /* light-row limit in percent of the default (50, 100 or 200) */
+    int32_t blocks_pct;    /* light CTA blocks per SpMV in percent of the default */
+    int32_t persistent;    /* 1: one persistent launch per tile was faster */
+    int32_t candidates;    /* configurations timed */
+    int32_t reserved;
+    double ms_per_iter;    /* device time of one PCG iteration of one tile, chosen setting */
+    double ms_per_pair_iter; /* ms_per_iter / kt */
+} nvd_tune_result;
+
+/*
+ * nvd_graph_tune -- choose the work decomposition of the solve (Section 3.2) for
+ * this graph by timing it: tile width (k-blocking) for k pairs, the row-split
+ * limit (longer rows become split sub-items), the number of SpMV blocks, and
+ * host-driven versus persistent iterations.  Candidates run real solves with
+ * seeded synthetic right-hand sides for a fixed number of iterations on
+ * `stream`; the winner is stored in the handle and used by later calls of
+ * mode `mode` (MIXED is timed as its FP32 inner solve): plans built afterwards
+ * use the row split and block count, and nvd_ge_distance uses the tile width
+ * and launch mode when opts.kt = 0 and NVD_SOLVE_PERSISTENT is not set.
+ * Results do not depend on the choice beyond rounding (each choice is a valid
+ * order of the same sums).  Synchronous.
+ *   k      number of pairs the later calls will solve (sets the tile-width cost
+ *          ceil(k / kt) * per-tile time); flags: NVD_TUNE_* bits.
+ *   out    optional; the chosen setting.
+ * Memory: 32 n doubles of synthetic input plus the plans of the timed
+ * candidates (plans of losing candidates are freed on return).
+ * Errors: NVD_ERR_INVALID_ARG (NULL handle, bad mode, k < 1, unknown flag),
+ * NVD_ERR_OOM, NVD_ERR_CUDA; on error the handle's previous setting is kept.
+ */
+int nvd_graph_tune(nvd_graph_t g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_result *out,
+                   nvd_stream_t stream);
+
+/*
+ * nvd_graph_set_tuning -- apply a setting (for example one nvd_graph_tune chose
+ * earlier for the same graph) without timing anything.  Reads kt (0 = no
+ * preference), row_max_pct and blocks_pct (10..1000) and persistent (0/1); the
+ * other fields are ignored.  Host only; plans built afterwards use it.
+ * Errors: NVD_ERR_INVALID_ARG (NULL pointer, bad mode or field).
+ */
+int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_result *t);
+
 /*
  * nvd_ge_distance -- d^2 = (x_j - y_j)^T L^+ (x_j - y_j) for j < k (Section 3.1,
  * GE equation), by PCG on L z = P(x_j - y_j) (Section 3.2), P the per-component

@@ -39,6 +39,7 @@ SOLVE_PERSISTENT = 8
 SOLVE_NO_SYNC = 16
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_SYM_CHECK = 2
+TUNE_SINGLE_RHS = 1
 
 STATUS = {0: "NVD_OK", 1: "NVD_ERR_INVALID_ARG", 2: "NVD_ERR_NOT_SYMMETRIC", 3: "NVD_ERR_BAD_WEIGHT",
           4: "NVD_ERR_OOM", 5: "NVD_ERR_CUDA", 6: "NVD_ERR_NOT_CONVERGED", 7: "NVD_ERR_NUMERIC",
@@ -65,6 +66,13 @@ class SolveStats(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class TuneResult(ctypes.Structure):
+    """Mirror of ``nvd_tune_result``."""
+    _fields_ = [("kt", ctypes.c_int32), ("row_max_pct", ctypes.c_int32), ("blocks_pct", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms_per_iter", ctypes.c_double), ("ms_per_pair_iter", ctypes.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -77,6 +85,9 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int64)]),
     "nvd_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+    "nvd_graph_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                      ctypes.POINTER(TuneResult), ctypes.c_void_p]),
+    "nvd_graph_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(TuneResult)]),
     "nvd_ge_distance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -224,6 +235,24 @@ class Graph:
         _check(self._lib.nvd_graph_info(self.handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc),
                                         ctypes.byref(nb)), "nvd_graph_info")
         return {"n": n.value, "nnz": nnz.value, "ncomp": nc.value, "device_bytes": nb.value}
+
+    def tune(self, *, mode: int = 0, k: int = 1, single_rhs: bool = False) -> dict:
+        """Time the solve's work decompositions on this graph (``nvd_graph_tune``) and keep
+        the fastest for later calls of ``mode``; returns the chosen setting."""
+        torch = _torch()
+        r = TuneResult()
+        with torch.cuda.device(self.device):
+            rc = self._lib.nvd_graph_tune(self.handle, int(mode), int(k), TUNE_SINGLE_RHS if single_rhs else 0,
+                                          ctypes.byref(r), _stream_ptr(self.device))
+        _check(rc, "nvd_graph_tune")
+        return {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "reserved"}
+
+    def set_tuning(self, *, mode: int = 0, kt: int = 0, row_max_pct: int = 100, blocks_pct: int = 100,
+                   persistent: bool = False):
+        """Apply a work-decomposition setting without timing (``nvd_graph_set_tuning``)."""
+        r = TuneResult(kt=int(kt), row_max_pct=int(row_max_pct), blocks_pct=int(blocks_pct),
+                       persistent=int(bool(persistent)))
+        _check(self._lib.nvd_graph_set_tuning(self.handle, int(mode), ctypes.byref(r)), "nvd_graph_set_tuning")
 
     @property
     def n(self) -> int:

@@ -387,7 +387,8 @@ __global__ void k_fill_slices(int64_t n_slices, int H, const int64_t *__restrict
 }
 
 int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
-    const int key = KT * 256 + szv * 16 + sza;
+    const int64_t key = ((int64_t)(KT * 256 + szv * 16 + sza) << 32) | ((int64_t)g->sp.row_max_pct << 16) |
+                        (int64_t)g->sp.blocks_pct;
     auto it = g->plans.find(key);
     if (it != g->plans.end()) {
         *out = it->second.get();
@@ -397,7 +398,8 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     pl->KT = KT;
     pl->szv = szv;
     pl->sza = sza;
-    const int64_t RMAX = sp_row_max(KT, szv);
+    pl->sp = g->sp;
+    const int64_t RMAX = std::max<int64_t>(1, (int64_t)sp_row_max(KT, szv) * g->sp.row_max_pct / 100);
     const int64_t LONG = sp_long_max(KT);
     const int64_t CH = sp_chunk(KT, szv);
     const int H = sp_slice_rows(KT, szv);
@@ -453,8 +455,8 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     // warp rounds (NWARP slices of H rows) of about `target` work (entries + rows);
     // inside a block the rows are sorted by length (longest first, ties by row) and
     // dealt into slices.  Heavy blocks follow their segment's light blocks.
-    const int T = target_blocks(g);
-    const double target = ltot / std::max(1, T);
+    const int T = std::max(1, target_blocks(g) * g->sp.blocks_pct / 100);
+    const double target = ltot / T;
     const int64_t QR = (int64_t)NWARP * H;
     std::vector<Block> sblk;
     std::vector<int32_t> seg_sblk_off(nseg + 1, 0);

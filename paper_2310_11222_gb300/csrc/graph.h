@@ -53,9 +53,18 @@ struct DevBuf {
     template <class T> T *as() const { return reinterpret_cast<T *>(p); }
 };
 
-// Work decomposition for one (KT, vector size, accumulator size) configuration.
+// Tunable parameters of the SpMV work decomposition, in percent of the built-in
+// defaults: the light-row limit (rows above it are split into heavy sub-items) and
+// the number of light CTA blocks per launch.
+struct SpParams {
+    int32_t row_max_pct = 100;
+    int32_t blocks_pct = 100;
+};
+
+// Work decomposition for one (KT, vector size, accumulator size, SpParams).
 struct Plan {
     int KT = 0, szv = 0, sza = 0;
+    SpParams sp;
     int64_t n_items = 0, n_sblk = 0, n_heavy = 0, n_chunks = 0, n_vblk = 0;
     int64_t n_slices = 0, n_sl_entries = 0;
     DevBuf items, sblk, vblk, seg_sblk_off, seg_heavy_off, seg_vblk_off, hcount;
@@ -84,7 +93,10 @@ struct nvd_graph_s {
     int64_t n_singleton = 0;
     std::vector<int64_t> h_rowptr, h_seg_begin, h_seg_end;
     nvd::DevBuf seg_begin, seg_end, seg_owner;
-    std::map<int, std::unique_ptr<nvd::Plan>> plans;
+    nvd::SpParams sp;            // parameters of plans built from now on (nvd_graph_tune)
+    int32_t tuned_kt[3] = {0, 0, 0};          // per solve mode: tile width chosen by the tuner (0 = none)
+    int32_t tuned_persistent[3] = {0, 0, 0};  // per solve mode: 1 = persistent launch was faster
+    std::map<int64_t, std::unique_ptr<nvd::Plan>> plans;
     std::map<std::string, std::unique_ptr<nvd::DevBuf>> ws;  // named lazily-grown workspace
 
     void *wsp(const std::string &name, size_t bytes, int *st);

@@ -51,10 +51,12 @@ struct DeviceGuard {
     }
 };
 
-int pick_kt(const nvd_solve_opts &o, int k) {
+// Tile width: explicit (opts.kt), else the tuner's choice for this mode (no wider
+// than the pairs need), else the widest tile up to the pairs (FP64: 16, FP32: 32).
+int pick_kt(const nvd_graph_s *g, const nvd_solve_opts &o, int k) {
     if (o.flags & NVD_SOLVE_SINGLE_RHS) return 1;
     if (o.kt) return o.kt;
-    const int cap = o.mode == NVD_MODE_FP64 ? 16 : 32;
+    const int cap = g->tuned_kt[o.mode] ? g->tuned_kt[o.mode] : o.mode == NVD_MODE_FP64 ? 16 : 32;
     int kt = 1;
     for (int c : {4, 8, 16, 32})
         if (kt < k && c <= cap) kt = c;
@@ -90,7 +92,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     if (opts) o = *opts; else nvd_solve_opts_default(&o);
     NVD_TRY(check_opts(o));
     DeviceGuard guard(g->device);
-    const int KT = pick_kt(o, k);
+    const int KT = pick_kt(g, o, k);
     const bool mixed = o.mode == NVD_MODE_MIXED;
     const size_t szv = o.mode == NVD_MODE_FP64 ? 8 : 4;
     const size_t xsz = xdt == NVD_F64 ? 8 : 4;
@@ -114,7 +116,8 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.hsum = w.hsum;
     }
     // persistent single-launch solve (FP64/FP32 modes; the launch timer needs the host loop)
-    const bool persistent = (o.flags & NVD_SOLVE_PERSISTENT) && !mixed && !prof_enabled();
+    const bool persistent = ((o.flags & NVD_SOLVE_PERSISTENT) || g->tuned_persistent[o.mode]) && !mixed &&
+                            !prof_enabled();
     const int64_t sk = (int64_t)std::max(g->nseg, 1) * KT;
     unsigned *bar = nullptr;
     if (persistent) {
@@ -259,6 +262,13 @@ int apply_impl(nvd_graph_t g, int32_t k, const void *x, void *y, int32_t dtype, 
 }
 
 }  // namespace
+
+namespace nvd {
+int ge_distance_internal(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdt,
+                         const nvd_solve_opts *opts, double *d2_out, cudaStream_t s) {
+    return distance_impl(g, k, x, y, xdt, opts, d2_out, nullptr, nullptr, s);
+}
+}  // namespace nvd
 
 extern "C" int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdtype,
                                const nvd_solve_opts *opts, double *d2_out, void *z_out,

@@ -338,6 +338,12 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
     *conv_out = 0;
     const int max_steps = std::max(1, o.max_refine);
     while (step < max_steps) {
+        // The first inner solve goes to opts.rtol.  A later one solves for the
+        // correction L c = r of the current z; its d^2 change r^T c is what decides
+        // convergence and the variational d^2 error after it is quadratic in its
+        // residual, so a relative residual of 1e-2 (or opts.rtol if looser) suffices.
+        const double rtol_step = step == 0 ? o.rtol : std::max(o.rtol, 1e-2);
+        ci.rtol2 = rtol_step * rtol_step;
         NVD_TRY_CUDA(cudaMemsetAsync(c.n_active, 0, 4, s));
         dev::OpInit<float, KT> oi;
         oi.src = step == 0 ? delta : w.r64;
