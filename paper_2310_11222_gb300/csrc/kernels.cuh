@@ -142,6 +142,53 @@ template <> __device__ __forceinline__ const double *deg_of<double>(const Ctx &c
 
 // ------------------------------------------------------------------ reductions
 
+// Per-thread partial sums of inner products.  FP64 vectors: an FP64 accumulator.
+// FP32 vectors: a double-float accumulator (hi + lo, about 48 significant bits)
+// fed with the exact product of two floats (p = a*b and e = fma(a, b, -p) give
+// a*b = p + e) and Knuth's two-sum, all on the FP32 pipe -- on this part FP64
+// runs at 1/64 of the FP32 rate, and one FP64 multiply-add plus two conversions
+// per element made the FP64 unit the limit of every FP32 pass.  The thread's
+// partial is converted to FP64 (hi + lo) before the block and grid reductions,
+// which run in FP64.  The _rn intrinsics keep the compiler from fusing the
+// error-free steps.
+struct DFloat {
+    float hi, lo;
+};
+template <class TV> struct DotOf { typedef double type; };
+template <> struct DotOf<float> { typedef DFloat type; };
+
+__device__ __forceinline__ void dot_zero(double &d) { d = 0.0; }
+__device__ __forceinline__ void dot_zero(DFloat &d) { d.hi = 0.f; d.lo = 0.f; }
+__device__ __forceinline__ double dot_get(double d) { return d; }
+__device__ __forceinline__ double dot_get(const DFloat &d) { return (double)d.hi + (double)d.lo; }
+__device__ __forceinline__ void dot_add(double &d, double a) { d += a; }
+__device__ __forceinline__ void dot_fma(double &d, double a, double b) { d = fma(a, b, d); }
+__device__ __forceinline__ void dot_add(DFloat &d, float a) {
+    const float s = __fadd_rn(d.hi, a);          // two-sum: s + t = d.hi + a exactly
+    const float bb = __fsub_rn(s, d.hi);
+    const float t = __fadd_rn(__fsub_rn(d.hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+    d.hi = s;
+    d.lo = __fadd_rn(d.lo, t);
+}
+__device__ __forceinline__ void dot_fma(DFloat &d, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);         // a*b - p, exact
+    const float s = __fadd_rn(d.hi, p);
+    const float bb = __fsub_rn(s, d.hi);
+    const float t = __fadd_rn(__fsub_rn(d.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    d.hi = s;
+    d.lo = __fadd_rn(d.lo, __fadd_rn(t, e));
+}
+
+// FP64 copy of a thread's partial sums.
+template <int ND, int VEC, class D>
+__device__ __forceinline__ void dot_to_double(const D (&a)[ND][VEC], double (&o)[ND][VEC]) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[d][v] = dot_get(a[d][v]);
+}
+
 // Block-wide per-column sums.  Thread t holds acc[d][v] for column
 // (t % CG) * VEC + v.  On return tot[d * KT + j] (shared) holds the block total,
 // summed in a fixed order (KT = 1: per lane over the warps, then a butterfly;
@@ -399,15 +446,15 @@ struct FinResid {
 struct EpiLap {
     static constexpr int ND = 1;
     static constexpr bool NEEDS_LIVE = true;   // CG step: converged segments skip the work
-    template <class TV, class TA, int VEC>
+    template <class TV> using D = typename DotOf<TV>::type;
+    template <class TV, class TA, int VEC, class DT>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
-                                         const TA (&acc)[VEC], TA degi, TV *dst,
-                                         double (&dot)[1][VEC]) const {
+                                         const TA (&acc)[VEC], TA degi, TV *dst, DT (&dot)[1][VEC]) const {
         TV y[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             y[v] = (TV)(degi * (TA)own[v] - acc[v]);
-            dot[0][v] += (double)own[v] * (double)y[v];
+            dot_fma(dot[0][v], own[v], y[v]);
         }
         stv(dst + i * KT + col0, y);
     }
@@ -418,10 +465,10 @@ struct EpiLap {
 struct EpiApply {
     static constexpr int ND = 0;
     static constexpr bool NEEDS_LIVE = false;
-    template <class TV, class TA, int VEC>
+    template <class TV> using D = double;
+    template <class TV, class TA, int VEC, class DT>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
-                                         const TA (&acc)[VEC], TA degi, TV *dst,
-                                         double (&)[1][VEC]) const {
+                                         const TA (&acc)[VEC], TA degi, TV *dst, DT (&)[1][VEC]) const {
         TV y[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) y[v] = (TV)(degi * (TA)own[v] - acc[v]);
@@ -435,6 +482,7 @@ struct EpiResid {
     static constexpr int ND = 4;
     static constexpr bool NEEDS_LIVE = false;  // runs after the inner solve, always on every segment
     const double *delta;
+    template <class TV> using D = double;
     template <class TV, class TA, int VEC>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
                                          const TA (&acc)[VEC], TA degi, TV *dst,
@@ -477,10 +525,10 @@ struct SpCfg {
 };
 
 // Phase B of a sub-item: rows [r0, r1) with accumulated neighbour sums in s_acc.
-template <class LD, class TV, class TA, int KT, class Epi>
+template <class LD, class TV, class TA, int KT, class Epi, class DT>
 __device__ __forceinline__ void spmm_epilogue(const Ctx &c, const Epi &epi, const TV *src, TV *dst,
                                               int64_t r0, int64_t r1, const TA *s_acc,
-                                              double (&dot)[Epi::ND > 0 ? Epi::ND : 1][SpCfg<TV, TA, KT>::VEC]) {
+                                              DT (&dot)[Epi::ND > 0 ? Epi::ND : 1][SpCfg<TV, TA, KT>::VEC]) {
     constexpr int VEC = SpCfg<TV, TA, KT>::VEC, CG = KT / VEC;
     const TA *deg = deg_of<TA>(c);
     const int64_t ne = (r1 - r0) * CG;
@@ -576,11 +624,11 @@ __device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, const T
         }
         if (threadIdx.x == 0) atomicExch(c.hcount + it.hrow, 0);
         __syncthreads();
-        double hdot[ND > 0 ? ND : 1][VEC];
+        typename Epi::template D<TV> hdot[ND > 0 ? ND : 1][VEC];
 #pragma unroll
         for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) hdot[d][v] = 0.0;
+            for (int v = 0; v < VEC; ++v) dot_zero(hdot[d][v]);
         spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, src, dst, i, i + 1, s_acc, hdot);
         if constexpr (ND > 0) {
             constexpr int CG = KT / VEC;
@@ -590,7 +638,7 @@ __device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, const T
                 for (int d = 0; d < ND; ++d)
 #pragma unroll
                     for (int v = 0; v < VEC; ++v)
-                        c.part[((int64_t)d * c.part_stride + hs) * KT + threadIdx.x * VEC + v] = hdot[d][v];
+                        c.part[((int64_t)d * c.part_stride + hs) * KT + threadIdx.x * VEC + v] = dot_get(hdot[d][v]);
             }
         }
     }
@@ -603,7 +651,7 @@ __device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, const T
 template <class LD, class TV, class TW, class TA, class Epi>
 __device__ __noinline__ void spmv1_long(const Ctx &c, const Epi &epi, const TV *__restrict__ src,
                                         TV *__restrict__ dst, const SpItem &it,
-                                        double (&dot)[Epi::ND > 0 ? Epi::ND : 1][1]) {
+                                        typename Epi::template D<TV> (&dot)[Epi::ND > 0 ? Epi::ND : 1][1]) {
     constexpr int ND = Epi::ND;
     const int lane = threadIdx.x & 31;
     const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
@@ -645,14 +693,14 @@ __device__ __noinline__ void spmv1_long(const Ctx &c, const Epi &epi, const TV *
                 atomicExch(c.hcount + it.hrow, 0);
                 TV own[1] = {LD::ld(src + i)};
                 const TA acc[1] = {(TA)t};
-                double hdot[ND > 0 ? ND : 1][1];
+                typename Epi::template D<TV> hdot[ND > 0 ? ND : 1][1];
 #pragma unroll
-                for (int d = 0; d < (ND > 0 ? ND : 1); ++d) hdot[d][0] = 0.0;
+                for (int d = 0; d < (ND > 0 ? ND : 1); ++d) dot_zero(hdot[d][0]);
                 epi.template elem<TV, TA, 1>(c, i, 0, 1, own, acc, __ldg(deg + i), dst, hdot);
                 if constexpr (ND > 0) {
 #pragma unroll
                     for (int d = 0; d < ND; ++d)
-                        c.part[(int64_t)d * c.part_stride + c.n_sblk + it.hrow] = hdot[d][0];
+                        c.part[(int64_t)d * c.part_stride + c.n_sblk + it.hrow] = dot_get(hdot[d][0]);
                 }
             }
         }
@@ -660,9 +708,9 @@ __device__ __noinline__ void spmv1_long(const Ctx &c, const Epi &epi, const TV *
 }
 
 // Single right-hand side (KT = 1) SpMV block.  Warps never wait for each other
-// (only __syncwarp), so many independent load chains are in flight per SM.
-//   light block (pad 0): a run of consecutive light rows of one segment; a group
-//           of G lanes per row (G from the degree profile);
+// until the block's final reduction, so many independent load chains are in
+// flight per SM.
+//   light block (pad 0): slices of the sliced light-row layout, one row per lane;
 //   heavy block (pad 1): up to 8 sub-items, one per warp: a long row (kind 2) or a
 //           chunk of a split row (kind 1, see spmv1_long).
 template <class LD, class TV, class TW, class TA, class Epi>
@@ -675,9 +723,9 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
     const TA *__restrict__ deg = deg_of<TA>(c);
     const Block blk = c.sblk[b];
     const int seg = blk.seg;
-    double dot[ND > 0 ? ND : 1][1];
+    typename Epi::template D<TV> dot[ND > 0 ? ND : 1][1];
 #pragma unroll
-    for (int d = 0; d < (ND > 0 ? ND : 1); ++d) dot[d][0] = 0.0;
+    for (int d = 0; d < (ND > 0 ? ND : 1); ++d) dot_zero(dot[d][0]);
     const bool live = !Epi::NEEDS_LIVE || seg_live<1>(c, seg);
     if (live) {
         if (blk.pad == 0) {
@@ -756,7 +804,9 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
         }
     }
     if constexpr (ND > 0) {
-        block_reduce_cols<ND, 1, 1>(dot, red, tot);
+        double dd[ND][1];
+        dot_to_double(dot, dd);
+        block_reduce_cols<ND, 1, 1>(dd, red, tot);
         const int64_t s0 = c.seg_sblk_off[seg];
         const int32_t cnt = c.seg_sblk_off[seg + 1] - (int32_t)s0;
         const int64_t h0 = c.n_sblk + c.seg_heavy_off[seg];
@@ -782,11 +832,11 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
     const Block blk = c.sblk[b];
     const int seg = blk.seg;
 
-    double dot[ND > 0 ? ND : 1][VEC];
+    typename Epi::template D<TV> dot[ND > 0 ? ND : 1][VEC];
 #pragma unroll
     for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) dot[d][v] = 0.0;
+        for (int v = 0; v < VEC; ++v) dot_zero(dot[d][v]);
 
     const bool live = !Epi::NEEDS_LIVE || seg_live<KT>(c, seg);
     if (live) {
@@ -849,7 +899,9 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
         }
     }
     if constexpr (ND > 0) {
-        block_reduce_cols<ND, KT, VEC>(dot, red, tot);
+        double dd[ND][VEC];
+        dot_to_double(dot, dd);
+        block_reduce_cols<ND, KT, VEC>(dd, red, tot);
         const int64_t s0 = c.seg_sblk_off[seg];
         const int32_t cnt = c.seg_sblk_off[seg + 1] - (int32_t)s0;
         const int64_t h0 = c.n_sblk + c.seg_heavy_off[seg];

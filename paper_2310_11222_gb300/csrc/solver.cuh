@@ -32,7 +32,7 @@ namespace nvd {
 #define NVD_SPMM_MINB 4
 #endif
 #ifndef NVD_VEC_MINB
-#define NVD_VEC_MINB 4
+#define NVD_VEC_MINB 2
 #endif
 
 // The iteration's kernels are launched with programmatic dependent launch: each

@@ -15,8 +15,9 @@ namespace dev {
 
 // Generic streaming pass over rows [i0, i1) of one segment.  Op provides ND,
 // NEEDS_LIVE, a register type R, setup(c, seg, col0), load(c, i, col0, R&) and
-// apply(c, i, col0, R&, dot).  Each thread handles U lane-vectors per trip with all
-// U loads issued before the first use.
+// apply(c, i, col0, R&, dot) with per-thread partial sums of type Op::D (see DotOf).
+// Each thread handles U lane-vectors per trip with all U loads issued before the
+// first use.
 template <class TV, int KT, class Op>
 __device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
     constexpr int VEC = VecCfg<TV, KT>::VEC, CG = KT / VEC, ND = Op::ND, U = 4;
@@ -25,11 +26,11 @@ __device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
     const Block blk = c.vblk[b];
     const int seg = blk.seg;
     const int col0 = (int)(threadIdx.x % CG) * VEC;
-    double dot[ND > 0 ? ND : 1][VEC];
+    typename Op::D dot[ND > 0 ? ND : 1][VEC];
 #pragma unroll
     for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) dot[d][v] = 0.0;
+        for (int v = 0; v < VEC; ++v) dot_zero(dot[d][v]);
     if (!Op::NEEDS_LIVE || seg_live<KT>(c, seg)) {
         op.setup(c, seg, col0);
         const int64_t t1 = blk.i1 * CG;
@@ -48,7 +49,9 @@ __device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
         }
     }
     if constexpr (ND > 0) {
-        block_reduce_cols<ND, KT, VEC>(dot, red, tot);
+        double dd[ND][VEC];
+        dot_to_double(dot, dd);
+        block_reduce_cols<ND, KT, VEC>(dd, red, tot);
         const int64_t s0 = c.seg_vblk_off[seg];
         const int32_t cnt = c.seg_vblk_off[seg + 1] - (int32_t)s0;
         seg_arrive<ND, KT>(c, op.fin, seg, b, tot, s0, cnt, 0, 0, red);
@@ -62,6 +65,7 @@ struct OpFormDelta {
     static constexpr int ND = 1, VEC = VecCfg<double, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
     struct R { double d[VEC]; };
+    typedef double D;
     double *delta;
     FinMean fin;
     const TX *X, *Y;
@@ -97,6 +101,7 @@ struct OpInit {
     static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
     struct R { double s[VEC]; TV di; };
+    typedef typename DotOf<TV>::type D;
     const double *src;
     double *writeback;
     TV *x, *r, *p;
@@ -110,7 +115,7 @@ struct OpInit {
         ldv<LD, double, VEC>(src + i * KT + col0, q.s);
         q.di = __ldg(dinv_of<TV>(c) + i);
     }
-    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &q, double (&dot)[2][VEC]) const {
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &q, D (&dot)[2][VEC]) const {
         const int64_t o = i * KT + col0;
         TV rv[VEC], uv[VEC], zv[VEC];
 #pragma unroll
@@ -119,8 +124,8 @@ struct OpInit {
             rv[v] = (TV)q.s[v];
             uv[v] = q.di * rv[v];
             zv[v] = (TV)0;
-            dot[0][v] += (double)rv[v] * (double)uv[v];
-            dot[1][v] += (double)rv[v] * (double)rv[v];
+            dot_fma(dot[0][v], rv[v], uv[v]);
+            dot_fma(dot[1][v], rv[v], rv[v]);
         }
         if (writeback) stv(writeback + o, q.s);
         stv(r + o, rv);
@@ -135,6 +140,7 @@ struct OpUpdate {
     static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = true;
     struct R { TV x[VEC], r[VEC], p[VEC], q[VEC]; TV di; };
+    typedef typename DotOf<TV>::type D;
     TV *x, *r;
     const TV *p, *q;
     FinBeta fin;
@@ -151,15 +157,15 @@ struct OpUpdate {
         ldv<LD, TV, VEC>(q + o, g.q);
         g.di = __ldg(dinv_of<TV>(c) + i);
     }
-    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&dot)[2][VEC]) const {
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, D (&dot)[2][VEC]) const {
         const int64_t o = i * KT + col0;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             g.x[v] += al[v] * g.p[v];
             g.r[v] -= al[v] * g.q[v];
             const TV u = g.di * g.r[v];
-            dot[0][v] += (double)g.r[v] * (double)u;
-            dot[1][v] += (double)g.r[v] * (double)g.r[v];
+            dot_fma(dot[0][v], g.r[v], u);
+            dot_fma(dot[1][v], g.r[v], g.r[v]);
         }
         stv(x + o, g.x);
         stv(r + o, g.r);
@@ -172,6 +178,7 @@ struct OpDir {
     static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = true;
     struct R { TV r[VEC], p[VEC]; TV di; };
+    typedef double D;
     const TV *r;
     TV *p;
     FinNone fin;
@@ -203,6 +210,7 @@ struct OpFinal {
     static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
     struct R { TV x[VEC]; double d[VEC]; };
+    typedef double D;
     const TV *x;
     const double *delta;
     FinFinal fin;
@@ -227,6 +235,7 @@ struct OpZout {
     static constexpr int ND = 0, VEC = VecCfg<TS, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
     struct R { TS s[VEC]; };
+    typedef double D;
     const TS *src;
     const double *meanv;
     FinNone fin;
@@ -263,6 +272,7 @@ struct OpAccum {
     static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = false;
     struct R { TV x[VEC]; double z[VEC]; };
+    typedef double D;
     const TV *x;
     double *z;
     FinNone fin;
