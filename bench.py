@@ -179,6 +179,181 @@ def cpu_baseline(g, X, Y, budget_s=12.0, max_pairs=8):
     return len(d2s) / dt, threads, len(d2s), dt, d2s
 
 
+def run_other_workload(args, nvd, synth, torch, np, local):
+    """Measurement of the other workloads of the method (not the default bench line):
+    the power-law precision workload (MIXED), the 64-graph batched workload (one
+    persistent graph-captured launch) and the differentiation workload (forward +
+    adjoint backward).  Same JSON fields as the default line."""
+    from oracle import cg as ocg
+    dev = torch.device("cuda", local)
+    name = args.workload
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prof = True
+    tuning = None
+    if name == "powerlaw":
+        wl = synth.workload_powerlaw()
+        g = wl.graph
+        k = 128
+        X, Y = wl.pairs(0, k)
+        G = nvd.Graph.from_csr(g)
+        if not args.no_tune:
+            tuning = G.tune(mode=nvd.MODE_MIXED, k=k)
+        xt, yt = torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)
+        xh, yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()
+        kw = dict(mode=nvd.MODE_MIXED, rtol=1e-4, d2_rtol=1e-8)
+
+        def step():
+            return nvd.ge_distance(G, xt, yt, **kw)
+
+        def step_e2e():
+            xt.copy_(xh, non_blocking=True)
+            yt.copy_(yh, non_blocking=True)
+            return nvd.ge_distance(G, xt, yt, **kw).cpu()
+        h2d, d2h = 2 * X.nbytes, 8 * k
+        cfg = {"workload": "powerlaw: erased configuration model n=1e7, gamma 2.3 on [2, 1e4], largest "
+                           "component, lognormal(0,1) FP32 weights, 128 pairs U[0,1) on 0.1% of nodes; "
+                           "FP32 block-PCG (rtol 1e-4) inside FP64 refinement to d2_rtol 1e-8",
+               "n": g.n, "nnz": int(g.rowptr[-1]), "pairs_per_step": k, "tuning": tuning}
+        unit = UNIT
+        dtype = "f32+f64"
+
+        def oracle_sample():
+            t0 = time.perf_counter()
+            ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), X[:1], Y[:1], rtol=RTOL)
+            return 1.0 / (time.perf_counter() - t0), "1 pair, FP64 oracle CG at rtol 1e-10"
+    elif name == "batched":
+        wl = synth.workload_batched()
+        graphs = wl.graphs
+        X, Y = wl.pairs(0, 32)
+        Gs = [nvd.Graph.from_csr(gi) for gi in graphs]
+        xs = [torch.from_numpy(x).to(dev) for x in X]
+        ys = [torch.from_numpy(y).to(dev) for y in Y]
+        xhs = [torch.from_numpy(x).pin_memory() for x in X]
+        yhs = [torch.from_numpy(y).pin_memory() for y in Y]
+        k = 32 * len(graphs)
+        kw = dict(mode=nvd.MODE_FP32, rtol=1e-6)
+        prof = False   # one persistent launch: no separate SpMV launches to time
+
+        def step():
+            return nvd.ge_distance_batched(Gs, xs, ys, **kw)
+
+        def step_e2e():
+            for a, b in zip(xs, xhs):
+                a.copy_(b, non_blocking=True)
+            for a, b in zip(ys, yhs):
+                a.copy_(b, non_blocking=True)
+            return nvd.ge_distance_batched(Gs, xs, ys, **kw)
+        h2d, d2h = sum(2 * x.nbytes for x in X), 8 * k
+        cfg = {"workload": "batched: 64 graphs, n log-uniform in [1e3, 2e5], 32 BA (m in 2..6) + 32 WS "
+                           "(k=10, p=0.1), unit weights, 32 pairs each (16 e_i - e_j, 16 diffuse); FP32 "
+                           "block-PCG with FP64 reductions to rtol 1e-6 in one persistent graph-captured launch",
+               "graphs": len(graphs), "n_total": int(sum(gi.n for gi in graphs)),
+               "nnz_total": int(sum(int(gi.rowptr[-1]) for gi in graphs)), "pairs_per_step": k}
+        unit = UNIT
+        dtype = "f32+f64"
+
+        def oracle_sample():
+            t0 = time.perf_counter()
+            done = 0
+            for gi, x, y in zip(graphs, X, Y):
+                ocg.ge_d2_cg(gi.n, gi.rowptr, gi.colidx, gi.w.astype(np.float64), x, y, rtol=1e-6)
+                done += x.shape[0]
+                if time.perf_counter() - t0 > 10:
+                    break
+            return done / (time.perf_counter() - t0), f"{done} pairs of the first graphs, FP64 oracle CG at rtol 1e-6"
+    elif name == "grad":
+        wl = synth.workload_grad()
+        g = wl.graph
+        k = 64
+        X, Y = wl.pairs(0, k)
+        G = nvd.Graph.from_csr(g)
+        if not args.no_tune:
+            tuning = G.tune(mode=nvd.MODE_FP64, k=k)
+        w = torch.from_numpy(g.w).to(dev).requires_grad_(True)
+        xt = torch.from_numpy(X).to(dev).requires_grad_(True)
+        yt = torch.from_numpy(Y).to(dev)
+        xh, yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()
+
+        def step():
+            w.grad = None
+            xt.grad = None
+            d2 = nvd.ge_distance_autograd(G, xt, yt, w, rtol=RTOL)
+            d2.sum().backward()
+            return d2
+
+        def step_e2e():
+            with torch.no_grad():
+                xt.copy_(xh, non_blocking=True)
+                yt.copy_(yh, non_blocking=True)
+            d2 = step()
+            return d2.detach().cpu()
+        h2d, d2h = 2 * X.nbytes, 8 * k
+        cfg = {"workload": "grad: BA n=1e6 m=5, lognormal(0,0.5) FP32 weights with requires_grad, 64 pairs "
+                           "U[0,1) on 10% of nodes; forward FP64 PCG to rtol 1e-10 plus the adjoint backward "
+                           "(grad_w, grad_x)", "n": g.n, "nnz": int(g.rowptr[-1]), "pairs_per_step": k,
+               "tuning": tuning}
+        unit = "pairs/s (forward + backward)"
+        dtype = "f64"
+
+        def oracle_sample():
+            t0 = time.perf_counter()
+            ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), X[:1], Y[:1], rtol=RTOL, return_z=True)
+            return 1.0 / (time.perf_counter() - t0), "1 pair forward (z), FP64 oracle CG at rtol 1e-10"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if prof:
+        nvd.profile_enable(True)
+        nvd.profile_read(0)
+    launches0 = nvd.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s_ in range(args.steps):
+        flush.zero_()
+        ev[s_][0].record()
+        step()
+        ev[s_][1].record()
+    torch.cuda.synchronize()
+    launches = nvd.kernel_launches() - launches0
+    n_spmv, spmv_ms, spmv_bytes = nvd.profile_read(0) if prof else (0, 0.0, 0.0)
+    nvd.profile_enable(False)
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te0
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = (spmv_bytes / n_spmv) / (spmv_ms / n_spmv / 1e3) / 1e9 if n_spmv else None
+    value = k * args.steps / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg,
+        "e2e": {"value": k * args.steps / te, "unit": unit, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches), "clocks": clk,
+        "roofline": None if not n_spmv else {
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_spmm (every SpMV/SpMM launch of the step, algorithmic bytes)",
+            "launches": n_spmv, "avg_launch_us": 1e3 * spmv_ms / n_spmv,
+            "algorithmic_bytes_per_launch": spmv_bytes / n_spmv,
+            "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy) of MEASURED_PEAKS.json"},
+    }
+    if not args.no_cpu_baseline:
+        v, what = oracle_sample()
+        line["cpu_baseline"] = {"value": v, "unit": unit, "cores": ocg.default_threads(), "kind": "oracle",
+                                "sample": what}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     """Reference arm: the oracle timed as it stands on the host cores."""
     rank, world, _ = env_rank()
@@ -225,6 +400,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS comparison runs")
     ap.add_argument("--no-tune", action="store_true", help="default work decomposition (no autotuning)")
+    ap.add_argument("--workload", choices=["er_large", "powerlaw", "batched", "grad"], default="er_large",
+                    help="er_large (default) is the bench line; the others measure the method's other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -249,6 +426,10 @@ def main():
     import paper_2310_11222_gb300 as nvd
     import synth
     nvd.load_library()
+    if args.workload != "er_large":
+        if world > 1:
+            raise SystemExit("--workload other than er_large runs on one GPU")
+        return run_other_workload(args, nvd, synth, torch, np, local)
 
     wl = synth.workload_er_large()
     g = wl.graph

@@ -31,8 +31,10 @@ namespace nvd {
 #ifndef NVD_SPMM_MINB
 #define NVD_SPMM_MINB 4
 #endif
+// vector passes: one column 4 (64 registers), several columns 2 (128 registers:
+// four 16-byte lane vectors of four arrays in flight per thread without spills)
 #ifndef NVD_VEC_MINB
-#define NVD_VEC_MINB 2
+#define NVD_VEC_MINB(KT) ((KT) == 1 ? 4 : 2)
 #endif
 
 // The iteration's kernels are launched with programmatic dependent launch: each
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(NT, KT == 1 ? NVD_SPMV1_MINB : NVD_SPMM_MINB) 
 }
 
 template <class TV, int KT, class Op>
-__global__ void __launch_bounds__(NT, NVD_VEC_MINB) k_vec(Ctx c, Op op) {
+__global__ void __launch_bounds__(NT, NVD_VEC_MINB(KT)) k_vec(Ctx c, Op op) {
     __shared__ __align__(16) char smem[vec_smem_bytes(KT)];
     pdl_trigger_and_wait();
     dev::vec_block<TV, KT, Op>(c, op, blockIdx.x, smem);
