@@ -115,6 +115,9 @@ typedef enum {
 #define NVD_SOLVE_HOST_INPUTS 4u  /* x, y (and z_out) are host pointers; copies are done here */
 #define NVD_SOLVE_PERSISTENT 8u   /* run each PCG solve inside one persistent cooperative kernel */
 #define NVD_SOLVE_NO_SYNC 16u     /* with NVD_SOLVE_D2_DEVICE and no stats: return without a final sync */
+#define NVD_SOLVE_FOLD_DIRECTION 32u /* two kernels per CG iteration: the direction update folded into
+                                        an SpMV on D^-1 r (default: three, SpMV on p, x/r update,
+                                        direction pass) */
 
 typedef struct {
     int32_t mode;        /* nvd_mode */
@@ -151,7 +154,7 @@ typedef struct {
     int32_t blocks_pct;    /* light CTA blocks per SpMV in percent of the default */
     int32_t persistent;    /* 1: one persistent launch per tile was faster */
     int32_t candidates;    /* configurations timed */
-    int32_t reserved;
+    int32_t fold_direction; /* 1: two kernels per iteration (NVD_SOLVE_FOLD_DIRECTION) were faster */
     double ms_per_iter;    /* device time of one PCG iteration of one tile, chosen setting */
     double ms_per_pair_iter; /* ms_per_iter / kt */
 } nvd_tune_result;
@@ -160,12 +163,14 @@ typedef struct {
  * nvd_graph_tune -- choose the work decomposition of the solve (Section 3.2) for
  * this graph by timing it: tile width (k-blocking) for k pairs, the row-split
  * limit (longer rows become split sub-items), the number of SpMV blocks, and
- * host-driven versus persistent iterations.  Candidates run real solves with
+ * host-driven versus persistent iterations, and two versus three kernels per
+ * iteration (NVD_SOLVE_FOLD_DIRECTION).  Candidates run real solves with
  * seeded synthetic right-hand sides for a fixed number of iterations on
  * `stream`; the winner is stored in the handle and used by later calls of
  * mode `mode` (MIXED is timed as its FP32 inner solve): plans built afterwards
  * use the row split and block count, and nvd_ge_distance uses the tile width
- * and launch mode when opts.kt = 0 and NVD_SOLVE_PERSISTENT is not set.
+ * when opts.kt = 0 and the launch mode and iteration form when the flags leave
+ * them at their defaults.
  * Results do not depend on the choice beyond rounding (each choice is a valid
  * order of the same sums).  Synchronous.
  *   k      number of pairs the later calls will solve (sets the tile-width cost
@@ -182,8 +187,9 @@ int nvd_graph_tune(nvd_graph_t g, int32_t mode, int32_t k, uint32_t flags, nvd_t
 /*
  * nvd_graph_set_tuning -- apply a setting (for example one nvd_graph_tune chose
  * earlier for the same graph) without timing anything.  Reads kt (0 = no
- * preference), row_max_pct and blocks_pct (10..1000) and persistent (0/1); the
- * other fields are ignored.  Host only; plans built afterwards use it.
+ * preference), row_max_pct and blocks_pct (10..1000), persistent and
+ * fold_direction (0/1); the other fields are ignored.  Host only; plans built
+ * afterwards use it.
  * Errors: NVD_ERR_INVALID_ARG (NULL pointer, bad mode or field).
  */
 int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_result *t);

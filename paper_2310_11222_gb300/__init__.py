@@ -37,6 +37,7 @@ SOLVE_D2_DEVICE = 2
 SOLVE_HOST_INPUTS = 4
 SOLVE_PERSISTENT = 8
 SOLVE_NO_SYNC = 16
+SOLVE_FOLD_DIRECTION = 32
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_SYM_CHECK = 2
 TUNE_SINGLE_RHS = 1
@@ -69,7 +70,7 @@ class SolveStats(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     """Mirror of ``nvd_tune_result``."""
     _fields_ = [("kt", ctypes.c_int32), ("row_max_pct", ctypes.c_int32), ("blocks_pct", ctypes.c_int32),
-                ("persistent", ctypes.c_int32), ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("candidates", ctypes.c_int32), ("fold_direction", ctypes.c_int32),
                 ("ms_per_iter", ctypes.c_double), ("ms_per_pair_iter", ctypes.c_double)]
 
 
@@ -245,13 +246,13 @@ class Graph:
             rc = self._lib.nvd_graph_tune(self.handle, int(mode), int(k), TUNE_SINGLE_RHS if single_rhs else 0,
                                           ctypes.byref(r), _stream_ptr(self.device))
         _check(rc, "nvd_graph_tune")
-        return {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "reserved"}
+        return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
     def set_tuning(self, *, mode: int = 0, kt: int = 0, row_max_pct: int = 100, blocks_pct: int = 100,
-                   persistent: bool = False):
+                   persistent: bool = False, fold_direction: bool = False):
         """Apply a work-decomposition setting without timing (``nvd_graph_set_tuning``)."""
         r = TuneResult(kt=int(kt), row_max_pct=int(row_max_pct), blocks_pct=int(blocks_pct),
-                       persistent=int(bool(persistent)))
+                       persistent=int(bool(persistent)), fold_direction=int(bool(fold_direction)))
         _check(self._lib.nvd_graph_set_tuning(self.handle, int(mode), ctypes.byref(r)), "nvd_graph_set_tuning")
 
     @property
@@ -273,6 +274,7 @@ class Graph:
 def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
                 d2_rtol: float = 1e-8, max_iter: int = 10000, max_refine: int = 8, kt: int = 0,
                 check_every: int = 4, single_rhs: bool = False, persistent: bool = False,
+                fold_direction: bool = False,
                 return_z: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
     """Squared GE distances d^2 for the k pairs (rows) of x, y ([k, n] or [n]).
 
@@ -300,6 +302,8 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
         o.flags |= SOLVE_SINGLE_RHS
     if persistent:
         o.flags |= SOLVE_PERSISTENT
+    if fold_direction:
+        o.flags |= SOLVE_FOLD_DIRECTION
     xdt = _dtype_code(X)
     stats = (SolveStats * max(k, 1))()
     if X.is_cuda:
@@ -329,7 +333,8 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
 
 
 def ge_distance_batched(graphs: Sequence[Graph], xs, ys, *, mode: int = MODE_FP32,
-                        rtol: Optional[float] = None, max_iter: int = 10000, return_stats: bool = False):
+                        rtol: Optional[float] = None, max_iter: int = 10000, return_stats: bool = False,
+                        fold_direction: bool = False):
     """d^2 for many graphs in one persistent launch; xs[g], ys[g] are CUDA [k_g, n_g]."""
     torch = _torch()
     lib = load_library()
@@ -344,6 +349,8 @@ def ge_distance_batched(graphs: Sequence[Graph], xs, ys, *, mode: int = MODE_FP3
     o = default_opts(mode, max_iter=max_iter)
     if rtol is not None:
         o.rtol = rtol
+    if fold_direction:
+        o.flags |= SOLVE_FOLD_DIRECTION
     d2 = torch.empty(total, dtype=torch.float64)
     stats = (SolveStats * max(total, 1))()
     dev = xs[0].device

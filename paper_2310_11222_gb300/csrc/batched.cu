@@ -275,7 +275,7 @@ int batched_impl(const nvd_graph_t *gs, int32_t G, const int32_t *k_per, const v
         const float *w32 = nullptr;   // create the FP32 weights before any capture
         NVD_TRY(get_w32(U, &w32, s));
     }
-    PersistArgs a{w.delta, w.x, w.r, w.p, w.q, w.res, G, 0};
+    PersistArgs a{w.delta, w.x, w.r, w.p, w.q, w.u, (o.flags & NVD_SOLVE_FOLD_DIRECTION) ? 1 : 0, w.res, G, 0};
     const int64_t sk = (int64_t)std::max(U->nseg, 1) * KT;
     int overall = NVD_OK;
     std::vector<int64_t> out_off(G + 1, 0);
@@ -283,13 +283,14 @@ int batched_impl(const nvd_graph_t *gs, int32_t G, const int32_t *k_per, const v
     for (int c0 = 0; c0 < kmax; c0 += KT) {
         std::vector<Owner> own(G);
         std::vector<uint64_t> key = {(uint64_t)KT, (uint64_t)o.mode, (uint64_t)xdt, (uint64_t)c0,
-                                     (uint64_t)o.max_iter, (uint64_t)pl->n_sblk};
+                                     (uint64_t)o.max_iter, (uint64_t)pl->n_sblk, (uint64_t)a.fold};
         uint64_t rbits;
         memcpy(&rbits, &o.rtol, 8);
         key.push_back(rbits);
         // the captured launch holds workspace addresses: a regrown workspace is a new key
         for (const void *ptr : {(const void *)w.part, (const void *)w.x, (const void *)w.r, (const void *)w.p,
-                                (const void *)w.q, (const void *)w.delta, (const void *)w.res, (const void *)c.active,
+                                (const void *)w.q, (const void *)a.u, (const void *)w.delta, (const void *)w.res,
+                                (const void *)c.active,
                                 (const void *)w.hsum, (const void *)c.rho, (const void *)bar, (const void *)d_own})
             key.push_back((uint64_t)(uintptr_t)ptr);
         for (int i = 0; i < G; ++i) {

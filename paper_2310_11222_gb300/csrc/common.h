@@ -144,6 +144,8 @@ struct ColResult {
 struct PersistArgs {
     double *delta;
     void *x, *r, *p, *q;
+    void *u;             // D^-1 r (stored by the update phase)
+    int fold;            // 1: two phases per iteration (direction folded into the SpMV), 0: three
     ColResult *res;      // [n_owner][KT]
     int n_owner;
     int write_z;

@@ -96,6 +96,7 @@ struct nvd_graph_s {
     nvd::SpParams sp;            // parameters of plans built from now on (nvd_graph_tune)
     int32_t tuned_kt[3] = {0, 0, 0};          // per solve mode: tile width chosen by the tuner (0 = none)
     int32_t tuned_persistent[3] = {0, 0, 0};  // per solve mode: 1 = persistent launch was faster
+    int32_t tuned_fold[3] = {0, 0, 0};        // per solve mode: 1 = two kernels per iteration were faster
     std::map<int64_t, std::unique_ptr<nvd::Plan>> plans;
     std::map<std::string, std::unique_ptr<nvd::DevBuf>> ws;  // named lazily-grown workspace
 

@@ -447,6 +447,7 @@ struct EpiLap {
     static constexpr int ND = 1;
     static constexpr bool NEEDS_LIVE = true;   // CG step: converged segments skip the work
     template <class TV> using D = typename DotOf<TV>::type;
+    __device__ __forceinline__ void prep(const Ctx &, int, int) {}
     template <class TV, class TA, int VEC, class DT>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
                                          const TA (&acc)[VEC], TA degi, TV *dst, DT (&dot)[1][VEC]) const {
@@ -461,11 +462,69 @@ struct EpiLap {
     FinAlpha fin;
 };
 
+// The CG step with the direction update folded in.  The SpMV runs on the
+// preconditioned residual u = D^-1 r instead of the direction p; with
+// w = L u the new direction and its image follow row by row,
+//     p = u + beta p_old,   q = L p = w + beta q_old,
+// (q by the recurrence instead of a second product), and p^T q gives alpha.  This
+// is the same CG (same alpha, beta, x, r in exact arithmetic) with one pass over
+// the vectors fewer per iteration.  beta = 0 on the first iteration selects
+// p = u, q = w (p_old, q_old are not read then); columns that stopped keep p, q.
+template <class TVD, int KT>
+struct EpiLapDir {
+    static constexpr int ND = 1;
+    static constexpr bool NEEDS_LIVE = true;
+    static constexpr int VM = VecCfg<TVD, KT>::VEC;
+    template <class TV> using D = typename DotOf<TV>::type;
+    TVD *p, *q;
+    TVD be[VM];
+    unsigned act;   // bit v: column col0 + v still iterating
+    __device__ __forceinline__ void prep(const Ctx &c, int seg, int col0) {
+        act = 0;
+#pragma unroll
+        for (int v = 0; v < VM; ++v) {
+            be[v] = (TVD)__ldcg(c.beta + (int64_t)seg * KT + col0 + v);
+            if (__ldcg(c.active + (int64_t)seg * KT + col0 + v)) act |= 1u << v;
+        }
+    }
+    template <class TV, class TA, int VEC, class DT>
+    __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int, const TV (&own)[VEC],
+                                         const TA (&acc)[VEC], TA degi, TV *, DT (&dot)[1][VEC]) const {
+        static_assert(VEC == VM, "tile layout");
+        const int64_t o = i * KT + col0;
+        if (!act) return;
+        bool first = true;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) first = first && !(be[v] != (TVD)0);
+        TV pv[VEC], qv[VEC];
+        if (!first) {
+            ldv<LdPlain, TV, VEC>(p + o, pv);
+            ldv<LdPlain, TV, VEC>(q + o, qv);
+        }
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const TV w = (TV)(degi * (TA)own[v] - acc[v]);
+            const TV b = be[v];
+            const TV pn = first ? own[v] : own[v] + b * pv[v];
+            const TV qn = first ? w : w + b * qv[v];
+            if (act & (1u << v)) {
+                pv[v] = pn;
+                qv[v] = qn;
+                dot_fma(dot[0][v], pn, qn);
+            }
+        }
+        stv(p + o, pv);
+        stv(q + o, qv);
+    }
+    FinAlpha fin;
+};
+
 // y = L x only (operator application, no reduction).
 struct EpiApply {
     static constexpr int ND = 0;
     static constexpr bool NEEDS_LIVE = false;
     template <class TV> using D = double;
+    __device__ __forceinline__ void prep(const Ctx &, int, int) {}
     template <class TV, class TA, int VEC, class DT>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
                                          const TA (&acc)[VEC], TA degi, TV *dst, DT (&)[1][VEC]) const {
@@ -483,6 +542,7 @@ struct EpiResid {
     static constexpr bool NEEDS_LIVE = false;  // runs after the inner solve, always on every segment
     const double *delta;
     template <class TV> using D = double;
+    __device__ __forceinline__ void prep(const Ctx &, int, int) {}
     template <class TV, class TA, int VEC>
     __device__ __forceinline__ void elem(const Ctx &, int64_t i, int col0, int KT, const TV (&own)[VEC],
                                          const TA (&acc)[VEC], TA degi, TV *dst,
@@ -526,7 +586,7 @@ struct SpCfg {
 
 // Phase B of a sub-item: rows [r0, r1) with accumulated neighbour sums in s_acc.
 template <class LD, class TV, class TA, int KT, class Epi, class DT>
-__device__ __forceinline__ void spmm_epilogue(const Ctx &c, const Epi &epi, const TV *src, TV *dst,
+__device__ __forceinline__ void spmm_epilogue(const Ctx &c, const Epi &epi, int seg, const TV *src, TV *dst,
                                               int64_t r0, int64_t r1, const TA *s_acc,
                                               DT (&dot)[Epi::ND > 0 ? Epi::ND : 1][SpCfg<TV, TA, KT>::VEC]) {
     constexpr int VEC = SpCfg<TV, TA, KT>::VEC, CG = KT / VEC;
@@ -541,7 +601,9 @@ __device__ __forceinline__ void spmm_epilogue(const Ctx &c, const Epi &epi, cons
         TA acc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = s_acc[li * KT + col0 + v];
-        epi.template elem<TV, TA, VEC>(c, i, col0, KT, own, acc, __ldg(deg + i), dst, dot);
+        Epi e = epi;
+        e.prep(c, seg, col0);
+        e.template elem<TV, TA, VEC>(c, i, col0, KT, own, acc, __ldg(deg + i), dst, dot);
     }
 }
 
@@ -549,7 +611,7 @@ __device__ __forceinline__ void spmm_epilogue(const Ctx &c, const Epi &epi, cons
 // partial row sum into hsum; the chunk that arrives last adds the chunks in chunk
 // order, applies the row epilogue and writes the row's partial slot.
 template <class LD, class TV, class TW, class TA, int KT, class Epi>
-__device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, const TV *__restrict__ src,
+__device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, int seg, const TV *__restrict__ src,
                                            TV *__restrict__ dst, const SpItem &it, TA *s_acc, double *red) {
     typedef SpCfg<TV, TA, KT> C;
     constexpr int VEC = C::VEC, LPR = C::LPR, G = C::G, ND = Epi::ND;
@@ -629,7 +691,7 @@ __device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, const T
         for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
 #pragma unroll
             for (int v = 0; v < VEC; ++v) dot_zero(hdot[d][v]);
-        spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, src, dst, i, i + 1, s_acc, hdot);
+        spmm_epilogue<LD, TV, TA, KT, Epi>(c, epi, seg, src, dst, i, i + 1, s_acc, hdot);
         if constexpr (ND > 0) {
             constexpr int CG = KT / VEC;
             if (threadIdx.x < CG) {
@@ -649,10 +711,12 @@ __device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, const T
 // Whole-warp part of the single-RHS SpMV: one long row (kind 2) or one chunk of a
 // split row (kind 1).  Kept out of line so the short-row loop keeps few registers.
 template <class LD, class TV, class TW, class TA, class Epi>
-__device__ __noinline__ void spmv1_long(const Ctx &c, const Epi &epi, const TV *__restrict__ src,
+__device__ __noinline__ void spmv1_long(const Ctx &c, const Epi &epi_in, int seg, const TV *__restrict__ src,
                                         TV *__restrict__ dst, const SpItem &it,
                                         typename Epi::template D<TV> (&dot)[Epi::ND > 0 ? Epi::ND : 1][1]) {
     constexpr int ND = Epi::ND;
+    Epi epi = epi_in;
+    epi.prep(c, seg, 0);
     const int lane = threadIdx.x & 31;
     const TW *__restrict__ w = reinterpret_cast<const TW *>(c.w);
     const TA *__restrict__ deg = deg_of<TA>(c);
@@ -736,6 +800,8 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
             // order into one accumulator (no cross-lane sum)
             const TW *__restrict__ slw = reinterpret_cast<const TW *>(c.sl_w);
             const int64_t ns = blk.i1 - blk.i0;
+            Epi e = epi;
+            e.prep(c, seg, 0);
             for (int64_t round = 0; round * NWARP < ns; ++round) {
                 // longest slices first; alternate rounds reverse the warp order so
                 // the warps' totals even out
@@ -792,14 +858,14 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
                 }
                 if (i >= 0) {
                     const TA av[1] = {acc};
-                    epi.template elem<TV, TA, 1>(c, i, 0, 1, own, av, dg, dst, dot);
+                    e.template elem<TV, TA, 1>(c, i, 0, 1, own, av, dg, dst, dot);
                 }
             }
         } else {
             // heavy sub-items (long rows, chunks of split rows), one warp each
             for (int64_t si = blk.i0 + warp; si < blk.i1; si += NWARP) {
                 const SpItem it = c.items[si];
-                spmv1_long<LD, TV, TW, TA, Epi>(c, epi, src, dst, it, dot);
+                spmv1_long<LD, TV, TW, TA, Epi>(c, epi, seg, src, dst, it, dot);
             }
         }
     }
@@ -850,6 +916,8 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
             const TA *__restrict__ deg = deg_of<TA>(c);
             const TW *__restrict__ slw = reinterpret_cast<const TW *>(c.sl_w);
             const int64_t ns = blk.i1 - blk.i0;
+            Epi e = epi;
+            e.prep(c, seg, col0);
             for (int64_t round = 0; round * NWARP < ns; ++round) {
                 const int64_t q = round * NWARP + ((round & 1) ? NWARP - 1 - warp : warp);
                 if (q >= ns) continue;
@@ -888,13 +956,13 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
 #pragma unroll
                             for (int v = 0; v < VEC; ++v) acc[v] += wu[u] * (TA)pv[u][v];
                 }
-                if (i >= 0) epi.template elem<TV, TA, VEC>(c, i, col0, KT, own, acc, dg, dst, dot);
+                if (i >= 0) e.template elem<TV, TA, VEC>(c, i, col0, KT, own, acc, dg, dst, dot);
             }
         } else {
             // heavy block: chunks of split rows, each taken by the whole CTA
             for (int64_t si = blk.i0; si < blk.i1; ++si) {
                 const SpItem it = c.items[si];
-                spmm_chunk<LD, TV, TW, TA, KT, Epi>(c, epi, src, dst, it, s_acc, red);
+                spmm_chunk<LD, TV, TW, TA, KT, Epi>(c, epi, seg, src, dst, it, s_acc, red);
             }
         }
     }

@@ -54,7 +54,7 @@ __device__ __forceinline__ bool grid_sync(const Ctx &c) {
 // One tile: form delta, PCG to convergence, d^2, optional z_out, per-owner results.
 template <class TV, class TW, class TA, int KT, class TX>
 __device__ void persistent_solve(const Ctx &c, const PersistArgs &a, char *smem) {
-    TV *x = (TV *)a.x, *r = (TV *)a.r, *p = (TV *)a.p, *q = (TV *)a.q;
+    TV *x = (TV *)a.x, *r = (TV *)a.r, *p = (TV *)a.p, *q = (TV *)a.q, *u = (TV *)a.u;
     // delta = x - y, segment sums
     {
         OpFormDelta<TX, KT> fd;
@@ -69,30 +69,44 @@ __device__ void persistent_solve(const Ctx &c, const PersistArgs &a, char *smem)
         oi.writeback = a.delta;
         oi.x = x;
         oi.r = r;
-        oi.p = p;
+        oi.p = a.fold ? u : p;
         oi.fin.KT = KT;
         for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT>(c, oi, b, smem);
     }
     if (!grid_sync(c)) return;
     EpiLap epi;
     epi.fin.KT = KT;
+    EpiLapDir<TV, KT> epd;
+    epd.p = p;
+    epd.q = q;
+    epd.fin.KT = KT;
     OpUpdate<TV, KT, LdCoh> ou;
     ou.x = x;
     ou.r = r;
     ou.p = p;
     ou.q = q;
+    ou.u = u;
     ou.fin.KT = KT;
     OpDir<TV, KT, LdCoh> od;
     od.r = r;
     od.p = p;
-    // the device deactivates every column by max_iter, so this loop is bounded
+    od.u = u;
+    // the device deactivates every column by max_iter, so this loop is bounded;
+    // a.fold: two phases per iteration (SpMV on u with the direction update folded
+    // in, then the x/r/u update), else three (SpMV on p, update, direction)
     for (int it = 0; it <= c.max_iter; ++it) {
         if (__ldcg(c.n_active) == 0) break;
-        for (int64_t b = blockIdx.x; b < c.n_sblk; b += gridDim.x)
-            spmm_block<LdCoh, TV, TW, TA, KT>(c, epi, p, q, b, smem);
+        if (a.fold) {
+            for (int64_t b = blockIdx.x; b < c.n_sblk; b += gridDim.x)
+                spmm_block<LdCoh, TV, TW, TA, KT>(c, epd, u, q, b, smem);
+        } else {
+            for (int64_t b = blockIdx.x; b < c.n_sblk; b += gridDim.x)
+                spmm_block<LdCoh, TV, TW, TA, KT>(c, epi, p, q, b, smem);
+        }
         if (!grid_sync(c)) return;
         for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT>(c, ou, b, smem);
         if (!grid_sync(c)) return;
+        if (a.fold) continue;
         if (__ldcg(c.n_active) == 0) break;
         for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT>(c, od, b, smem);
         if (!grid_sync(c)) return;

@@ -65,7 +65,7 @@ int pick_kt(const nvd_graph_s *g, const nvd_solve_opts &o, int k) {
 
 int check_opts(const nvd_solve_opts &o) {
     const uint32_t known = NVD_SOLVE_SINGLE_RHS | NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS |
-                           NVD_SOLVE_PERSISTENT | NVD_SOLVE_NO_SYNC;
+                           NVD_SOLVE_PERSISTENT | NVD_SOLVE_NO_SYNC | NVD_SOLVE_FOLD_DIRECTION;
     if (o.mode < NVD_MODE_FP64 || o.mode > NVD_MODE_MIXED || !(o.rtol > 0.0) || o.max_iter < 1 ||
         o.check_every < 1 || !(o.kt == 0 || o.kt == 1 || o.kt == 4 || o.kt == 8 || o.kt == 16 || o.kt == 32) ||
         (o.flags & ~known) || (o.mode == NVD_MODE_MIXED && (!(o.d2_rtol > 0.0) || o.max_refine < 1))) {
@@ -91,6 +91,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     nvd_solve_opts o;
     if (opts) o = *opts; else nvd_solve_opts_default(&o);
     NVD_TRY(check_opts(o));
+    if (g->tuned_fold[o.mode]) o.flags |= NVD_SOLVE_FOLD_DIRECTION;
     DeviceGuard guard(g->device);
     const int KT = pick_kt(g, o, k);
     const bool mixed = o.mode == NVD_MODE_MIXED;
@@ -170,7 +171,8 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         if (persistent) {
             NVD_TRY_CUDA(cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 8) * 4, s));
             NVD_TRY_CUDA(cudaMemsetAsync(bar, 0, 16, s));
-            PersistArgs a{w.delta, w.x, w.r, w.p, w.q, w.res, 1, io.z ? 1 : 0};
+            PersistArgs a{w.delta, w.x, w.r, w.p, w.q, w.u, (o.flags & NVD_SOLVE_FOLD_DIRECTION) ? 1 : 0,
+                          w.res, 1, io.z ? 1 : 0};
             NVD_TRY(run_persistent(g, c, a, o.mode, KT, xdt, s));
         } else if (o.mode == NVD_MODE_FP64)
             NVD_TRY(run_tile_fp64(g, c, w, o, io, s, KT, xdt));

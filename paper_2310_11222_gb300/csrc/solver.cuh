@@ -125,6 +125,7 @@ struct SolveWs {
     double *hsum = nullptr;       // [n_chunks][KT] partial row sums of split rows
     double *delta = nullptr, *z64 = nullptr, *r64 = nullptr;
     void *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    void *u = nullptr;   // D^-1 r, the vector the SpMV runs on (direction folded into the SpMV)
 };
 
 // Allocate (or reuse) the workspace of a solve and point the Ctx state at it.
@@ -145,6 +146,7 @@ inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixe
     w->r = g->wsp("r", (size_t)nk * tv, &st);
     w->p = g->wsp("p", (size_t)nk * tv, &st);
     w->q = g->wsp("q", (size_t)nk * tv, &st);
+    w->u = g->wsp("u", (size_t)nk * tv, &st);
     if (mixed) {
         w->z64 = (double *)g->wsp("z64", (size_t)nk * 8, &st);
         w->r64 = (double *)g->wsp("r64", (size_t)nk * 8, &st);
@@ -196,12 +198,13 @@ inline int launch_vec(const Ctx &c, const Op &op, cudaStream_t s) {
 
 // Algorithmic bytes of one SpMV/SpMM launch: the CSR (column indices, weights,
 // row pointers), the degrees, one read of the gathered vector and one write of
-// the result, over the nodes that belong to a segment.
-inline double spmm_bytes(const nvd_graph_s *g, int KT, size_t szv, size_t szw, size_t sza) {
+// the result, over the nodes that belong to a segment; with the direction update
+// folded in (fused), also the read of p and q and the write of p.
+inline double spmm_bytes(const nvd_graph_s *g, int KT, size_t szv, size_t szw, size_t sza, bool fused = false) {
     int64_t rows = 0;
     for (int s2 = 0; s2 < g->nseg; ++s2) rows += g->h_seg_end[s2] - g->h_seg_begin[s2];
     return (double)g->nnz * (4.0 + (double)szw) + 8.0 * (double)(rows + 1) + (double)rows * (double)sza +
-           2.0 * (double)rows * KT * (double)szv;
+           (fused ? 5.0 : 2.0) * (double)rows * KT * (double)szv;
 }
 
 // Host-visible polling buffers (pinned) and events, one set per thread.
@@ -227,17 +230,23 @@ inline PollBufs &poll_bufs() {
 // polling never drains the GPU queue.  Iterations issued after convergence cost
 // one near-empty launch per pass (inactive segments skip their work).
 template <class TV, class TW, class TA, int KT>
-int pcg_loop(const Ctx &c, TV *x, TV *r, TV *p, TV *q, int max_iter, int check_every,
+int pcg_loop(const Ctx &c, TV *x, TV *r, TV *p, TV *q, TV *u, bool fold, int max_iter, int check_every,
              double bytes, cudaStream_t s) {
     PollBufs &pb = poll_bufs();
     NVD_TRY(pb.init());
+    // fold: two kernels per iteration, the SpMV on u = D^-1 r with the direction
+    // update folded into it (EpiLapDir), then the x/r/u update.  Otherwise three:
+    // the SpMV on p, the x/r/u update and the direction pass p = u + beta p.
     dev::EpiLap epi;
     epi.fin.KT = KT;
+    dev::EpiLapDir<TV, KT> epd;
+    epd.p = p; epd.q = q;
+    epd.fin.KT = KT;
     dev::OpUpdate<TV, KT> ou;
-    ou.x = x; ou.r = r; ou.p = p; ou.q = q;
+    ou.x = x; ou.r = r; ou.p = p; ou.q = q; ou.u = u;
     ou.fin.KT = KT;
     dev::OpDir<TV, KT> od;
-    od.r = r; od.p = p;
+    od.r = r; od.p = p; od.u = u;
     const int C = std::max(1, check_every);
     int64_t issued = 0;
     int batch = 0;
@@ -245,9 +254,14 @@ int pcg_loop(const Ctx &c, TV *x, TV *r, TV *p, TV *q, int max_iter, int check_e
     const int64_t cap = (int64_t)max_iter + 2 * C;
     while (!done && issued < cap) {
         for (int t = 0; t < C; ++t) {
-            NVD_TRY((launch_spmm<TV, TW, TA, KT>(c, epi, p, q, s, bytes)));
-            NVD_TRY((launch_vec<TV, KT>(c, ou, s)));
-            NVD_TRY((launch_vec<TV, KT>(c, od, s)));
+            if (fold) {
+                NVD_TRY((launch_spmm<TV, TW, TA, KT>(c, epd, u, q, s, bytes)));
+                NVD_TRY((launch_vec<TV, KT>(c, ou, s)));
+            } else {
+                NVD_TRY((launch_spmm<TV, TW, TA, KT>(c, epi, p, q, s, bytes)));
+                NVD_TRY((launch_vec<TV, KT>(c, ou, s)));
+                NVD_TRY((launch_vec<TV, KT>(c, od, s)));
+            }
         }
         issued += C;
         NVD_TRY_CUDA(cudaMemcpyAsync(pb.h + (batch & 1), c.n_active, 4, cudaMemcpyDeviceToHost, s));
@@ -285,12 +299,14 @@ int tile_pcg(nvd_graph_s *g, Ctx c, SolveWs &w, const nvd_solve_opts &o, const T
     fd.fin.KT = KT;
     NVD_TRY((launch_vec<double, KT>(c, fd, s)));
     NVD_TRY_CUDA(cudaMemsetAsync(c.n_active, 0, 4, s));
+    const bool fused = (o.flags & NVD_SOLVE_FOLD_DIRECTION) != 0;
+    TV *u = (TV *)w.u;
     dev::OpInit<TV, KT> oi;
-    oi.src = delta; oi.writeback = delta; oi.x = x; oi.r = r; oi.p = p;
+    oi.src = delta; oi.writeback = delta; oi.x = x; oi.r = r; oi.p = fused ? u : p;
     oi.fin.KT = KT;
     NVD_TRY((launch_vec<TV, KT>(c, oi, s)));
-    const double bytes = spmm_bytes(g, KT, sizeof(TV), sizeof(TW), sizeof(TA));
-    NVD_TRY((pcg_loop<TV, TW, TA, KT>(c, x, r, p, q, o.max_iter, o.check_every, bytes, s)));
+    const double bytes = spmm_bytes(g, KT, sizeof(TV), sizeof(TW), sizeof(TA), fused);
+    NVD_TRY((pcg_loop<TV, TW, TA, KT>(c, x, r, p, q, u, fused, o.max_iter, o.check_every, bytes, s)));
     dev::OpFinal<TV, KT> of;
     of.x = x; of.delta = delta;
     of.fin.KT = KT; of.fin.set_d2 = true;
@@ -325,7 +341,9 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
     fd.fin.KT = KT;
     NVD_TRY((launch_vec<double, KT>(c, fd, s)));
     NVD_TRY_CUDA(cudaMemsetAsync(w.z64, 0, (size_t)g->n * KT * 8, s));
-    const double bytes32 = spmm_bytes(g, KT, 4, 4, 4);
+    const bool fused = (o.flags & NVD_SOLVE_FOLD_DIRECTION) != 0;
+    float *u = (float *)w.u;
+    const double bytes32 = spmm_bytes(g, KT, 4, 4, 4, fused);
     const double bytes64 = spmm_bytes(g, KT, 8, sizeof(TWN), 8);
     std::vector<ColResult> res(KT);
     std::vector<double> prev(KT, 0.0), dd(KT, 0.0);
@@ -350,10 +368,11 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
         dev::OpInit<float, KT> oi;
         oi.src = step == 0 ? delta : w.r64;
         oi.writeback = step == 0 ? delta : nullptr;
-        oi.x = x; oi.r = r; oi.p = p;
+        oi.x = x; oi.r = r; oi.p = fused ? u : p;
         oi.fin.KT = KT;
         NVD_TRY((launch_vec<float, KT>(ci, oi, s)));
-        NVD_TRY((pcg_loop<float, float, float, KT>(ci, x, r, p, q, o.max_iter, o.check_every, bytes32, s)));
+        NVD_TRY((pcg_loop<float, float, float, KT>(ci, x, r, p, q, u, fused, o.max_iter, o.check_every, bytes32,
+                                                   s)));
         dev::OpAccum<float, KT> oa;
         oa.x = x; oa.z = w.z64;
         NVD_TRY((launch_vec<float, KT>(c, oa, s)));

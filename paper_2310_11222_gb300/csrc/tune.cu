@@ -8,13 +8,14 @@
 //     sub-items (whole-row warp items or fixed-size chunks) instead of being
 //     stored in the sliced layout, where it would make its whole slice as long;
 //   * the number of light CTA blocks per SpMV launch;
-//   * host-driven iterations versus one persistent cooperative launch per tile.
+//   * host-driven iterations versus one persistent cooperative launch per tile;
+//   * two kernels per iteration (direction update folded into the SpMV) or three.
 // Each candidate runs real solves on this graph with seeded synthetic
 // right-hand sides (the structure decides the cost, not the values) for a fixed
 // number of iterations; the cost of one iteration is the difference of two such
 // runs divided by the difference of their iteration counts, so set-up and
-// result collection cancel.  The search is coordinate-wise (tile width, then row
-// split, then block count, then launch mode) and the winner is stored in the
+// result collection cancel.  The search is coordinate-wise (tile width, row split,
+// block count, launch mode, iteration form) and the winner is stored in the
 // handle: later plans use it, and nvd_ge_distance uses the tile width and launch
 // mode for the tuned solve mode when the caller leaves them open.
 #include <algorithm>
@@ -64,6 +65,8 @@ struct Bench {
     Timer t;
     int lo, hi;            // iteration counts of the two runs
 
+    bool fold = false;     // time the two-kernel iteration
+
     // One solve of KT columns, max_iter = iters; returns its device time in ms.
     int run(int KT, bool persistent, int iters, float *ms) {
         nvd_solve_opts o;
@@ -74,7 +77,7 @@ struct Bench {
         o.kt = KT;
         o.check_every = 4;
         o.flags = NVD_SOLVE_D2_DEVICE | (KT == 1 ? NVD_SOLVE_SINGLE_RHS : 0u) |
-                  (persistent ? NVD_SOLVE_PERSISTENT : 0u);
+                  (persistent ? NVD_SOLVE_PERSISTENT : 0u) | (fold ? NVD_SOLVE_FOLD_DIRECTION : 0u);
         NVD_TRY_CUDA(cudaEventRecord(t.a, s));
         const int rc = ge_distance_internal(g, KT, x, y, NVD_F64, &o, d2, s);
         if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED) return rc;
@@ -130,12 +133,30 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
     NVD_TRY(b.t.init());
     const SpParams saved = g->sp;
     const int saved_kt = g->tuned_kt[mode], saved_pers = g->tuned_persistent[mode];
+    const int saved_fold = g->tuned_fold[mode];
     g->tuned_kt[mode] = 0;
     g->tuned_persistent[mode] = 0;
+    g->tuned_fold[mode] = 0;
+    // the timed mode's own settings must not leak into the candidates (MIXED is
+    // timed as FP32)
+    const int tm = b.mode;
+    const int keep_kt = g->tuned_kt[tm], keep_pers = g->tuned_persistent[tm], keep_fold = g->tuned_fold[tm];
+    g->tuned_kt[tm] = 0;
+    g->tuned_persistent[tm] = 0;
+    g->tuned_fold[tm] = 0;
+    auto restore_timed = [&]() {
+        if (tm != mode) {
+            g->tuned_kt[tm] = keep_kt;
+            g->tuned_persistent[tm] = keep_pers;
+            g->tuned_fold[tm] = keep_fold;
+        }
+    };
     auto fail = [&](int rc) {
         g->sp = saved;
         g->tuned_kt[mode] = saved_kt;
         g->tuned_persistent[mode] = saved_pers;
+        g->tuned_fold[mode] = saved_fold;
+        restore_timed();
         return rc;
     };
 
@@ -194,6 +215,21 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
             return fail(rc);
         }
     }
+    // 5. two kernels per iteration (direction folded into the SpMV) against three
+    int fold = 0;
+    {
+        b.fold = true;
+        double it = 0;
+        const int rc = b.per_iter(best_kt, pers != 0, &it);
+        b.fold = false;
+        if (rc) return fail(rc);
+        ++ntried;
+        if (it < best_iter * 0.98) {
+            fold = 1;
+            best_iter = it;
+        }
+    }
+    restore_timed();
     // drop the plans of the losing candidates
     for (auto it = g->plans.begin(); it != g->plans.end();) {
         const SpParams &p = it->second->sp;
@@ -202,13 +238,14 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
     }
     g->tuned_kt[mode] = single ? 0 : best_kt;
     g->tuned_persistent[mode] = pers;
+    g->tuned_fold[mode] = fold;
     if (out) {
         out->kt = best_kt;
         out->row_max_pct = g->sp.row_max_pct;
         out->blocks_pct = g->sp.blocks_pct;
         out->persistent = pers;
         out->candidates = ntried;
-        out->reserved = 0;
+        out->fold_direction = fold;
         out->ms_per_iter = best_iter;
         out->ms_per_pair_iter = best_iter / best_kt;
     }
@@ -222,7 +259,7 @@ extern "C" int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_
     if (!g || !t || mode < NVD_MODE_FP64 || mode > NVD_MODE_MIXED ||
         !(t->kt == 0 || t->kt == 1 || t->kt == 4 || t->kt == 8 || t->kt == 16 || t->kt == 32) ||
         t->row_max_pct < 10 || t->row_max_pct > 1000 || t->blocks_pct < 10 || t->blocks_pct > 1000 ||
-        (t->persistent != 0 && t->persistent != 1)) {
+        (t->persistent != 0 && t->persistent != 1) || (t->fold_direction != 0 && t->fold_direction != 1)) {
         set_error("nvd_graph_set_tuning: invalid argument");
         return NVD_ERR_INVALID_ARG;
     }
@@ -230,6 +267,7 @@ extern "C" int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_
     g->sp.blocks_pct = t->blocks_pct;
     g->tuned_kt[mode] = t->kt;
     g->tuned_persistent[mode] = t->persistent;
+    g->tuned_fold[mode] = t->fold_direction;
     return NVD_OK;
 }
 

@@ -134,7 +134,8 @@ struct OpInit {
     }
 };
 
-// x += alpha p, r -= alpha q, u = D^-1 r; r^T u and |r|^2.
+// x += alpha p, r -= alpha q, u = D^-1 r (stored when u is set: the next SpMV
+// runs on it); r^T u and |r|^2.
 template <class TV, int KT, class LD = LdPlain>
 struct OpUpdate {
     static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
@@ -143,6 +144,7 @@ struct OpUpdate {
     typedef typename DotOf<TV>::type D;
     TV *x, *r;
     const TV *p, *q;
+    TV *u = nullptr;
     FinBeta fin;
     TV al[VEC];
     __device__ void setup(const Ctx &c, int seg, int col0) {
@@ -159,20 +161,23 @@ struct OpUpdate {
     }
     __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, D (&dot)[2][VEC]) const {
         const int64_t o = i * KT + col0;
+        TV uv[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             g.x[v] += al[v] * g.p[v];
             g.r[v] -= al[v] * g.q[v];
-            const TV u = g.di * g.r[v];
-            dot_fma(dot[0][v], g.r[v], u);
+            uv[v] = g.di * g.r[v];
+            dot_fma(dot[0][v], g.r[v], uv[v]);
             dot_fma(dot[1][v], g.r[v], g.r[v]);
         }
         stv(x + o, g.x);
         stv(r + o, g.r);
+        if (u) stv(u + o, uv);
     }
 };
 
-// p = D^-1 r + beta p on the columns still iterating.
+// p = D^-1 r + beta p on the columns still iterating (D^-1 r read from u when the
+// update pass stored it: one read and one FP64 multiply fewer per element).
 template <class TV, int KT, class LD = LdPlain>
 struct OpDir {
     static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
@@ -181,6 +186,7 @@ struct OpDir {
     typedef double D;
     const TV *r;
     TV *p;
+    const TV *u = nullptr;
     FinNone fin;
     TV be[VEC];
     bool act[VEC];
@@ -193,13 +199,23 @@ struct OpDir {
     }
     __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &g) const {
         const int64_t o = i * KT + col0;
-        ldv<LD, TV, VEC>(r + o, g.r);
+        if (u) {
+            ldv<LD, TV, VEC>(u + o, g.r);
+            g.di = (TV)1;
+        } else {
+            ldv<LD, TV, VEC>(r + o, g.r);
+            g.di = __ldg(dinv_of<TV>(c) + i);
+        }
         ldv<LD, TV, VEC>(p + o, g.p);
-        g.di = __ldg(dinv_of<TV>(c) + i);
     }
     __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
+        if (u) {
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) g.p[v] = act[v] ? g.di * g.r[v] + be[v] * g.p[v] : g.p[v];
+            for (int v = 0; v < VEC; ++v) g.p[v] = act[v] ? g.r[v] + be[v] * g.p[v] : g.p[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) g.p[v] = act[v] ? g.di * g.r[v] + be[v] * g.p[v] : g.p[v];
+        }
         stv(p + i * KT + col0, g.p);
     }
 };

@@ -86,19 +86,33 @@ def test_batched_uneven_pair_counts_and_multiple_tiles(nvd, small_batch):
         off += k
 
 
+@pytest.mark.parametrize("fold", [False, True])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("kt", [1, 8, 32])
-def test_persistent_single_graph_bitwise_equals_host_loop(nvd, mode, kt):
+def test_persistent_single_graph_bitwise_equals_host_loop(nvd, mode, kt, fold):
     wl = synth.workload_ba_small()
     g = wl.graph
     X, Y = wl.pairs(0, 12)
     G = nvd.Graph.from_csr(g)
     if mode == 0 and kt == 32:
         kt = 16
-    a, za = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, return_z=True)
-    b, zb = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, persistent=True, return_z=True)
+    a, za = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, return_z=True, fold_direction=fold)
+    b, zb = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, persistent=True, return_z=True,
+                            fold_direction=fold)
     assert torch.equal(a, b)
     assert torch.equal(za, zb)
+
+
+@pytest.mark.parametrize("mode,tol", [(0, 1e-11), (1, 1e-5)])
+def test_batched_folded_direction_matches_three_kernel_iteration(nvd, small_batch, mode, tol):
+    graphs, pairs, want = small_batch
+    G = [nvd.Graph.from_csr(g) for g in graphs]
+    xs = [on(X) for X, _ in pairs]
+    ys = [on(Y) for _, Y in pairs]
+    rtol = 1e-10 if mode == 0 else 1e-6
+    a = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol).numpy()
+    b = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, fold_direction=True).numpy()
+    assert rel(a, b) < tol
 
 
 @pytest.mark.slow

@@ -49,13 +49,20 @@ def ba_small():
     return wl.graph, X, Y, want
 
 
+@pytest.mark.parametrize("fold", [False, True])
 @pytest.mark.parametrize("single", [False, True])
-def test_ba_small_fp64(nvd, ba_small, single):
+def test_ba_small_fp64(nvd, ba_small, single, fold):
     g, X, Y, want = ba_small
     G = nvd.Graph.from_csr(g)
-    d2, st = nvd.ge_distance(G, on(X), on(Y), rtol=1e-10, single_rhs=single, return_stats=True)
+    d2, st = nvd.ge_distance(G, on(X), on(Y), rtol=1e-10, single_rhs=single, return_stats=True,
+                             fold_direction=fold)
     assert rel(d2.cpu().numpy(), want) < 1e-8
     assert all(s["status"] == 0 and s["rel_resid"] <= 1e-10 for s in st)
+    # the same iteration count either way (the same CG in exact arithmetic)
+    it = [s["iters"] for s in st]
+    d2c, stc = nvd.ge_distance(G, on(X), on(Y), rtol=1e-10, single_rhs=single, return_stats=True,
+                               fold_direction=not fold)
+    assert all(abs(a - s["iters"]) <= 1 for a, s in zip(it, stc))
 
 
 @pytest.mark.parametrize("kt", [1, 4, 8, 16, 32])

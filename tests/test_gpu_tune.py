@@ -55,8 +55,9 @@ def test_every_setting_matches_oracle(nvd, hub_graph, row_max_pct, blocks_pct):
     G = nvd.Graph.from_csr(g)
     G.set_tuning(mode=nvd.MODE_FP64, row_max_pct=row_max_pct, blocks_pct=blocks_pct)
     for kt in (1, 8, 16):
-        d2 = nvd.ge_distance(G, on(X), on(Y), rtol=1e-12, kt=kt)
-        assert rel(d2.cpu().numpy(), want) < 1e-8, (kt, row_max_pct, blocks_pct)
+        for fold in (False, True):
+            d2 = nvd.ge_distance(G, on(X), on(Y), rtol=1e-12, kt=kt, fold_direction=fold)
+            assert rel(d2.cpu().numpy(), want) < 1e-8, (kt, fold, row_max_pct, blocks_pct)
     d2 = nvd.ge_distance(G, on(X), on(Y), mode=nvd.MODE_FP32, rtol=1e-7, kt=32)
     assert rel(d2.cpu().numpy(), want) < 1e-4
 
@@ -69,6 +70,7 @@ def test_tune_then_solve(nvd, hub_graph, mode):
     assert r["kt"] in (1, 4, 8, 16, 32) and (mode != 0 or r["kt"] <= 16)
     assert r["row_max_pct"] in (50, 100, 200) and r["blocks_pct"] in (50, 100, 200)
     assert r["persistent"] in (0, 1) and (mode != 2 or r["persistent"] == 0)
+    assert r["fold_direction"] in (0, 1)
     assert r["candidates"] >= 5 and r["ms_per_iter"] > 0
     tol = {0: 1e-8, 1: 1e-4, 2: 1e-8}[mode]
     kw = dict(mode=mode, rtol={0: 1e-12, 1: 1e-7, 2: 1e-6}[mode])
@@ -77,7 +79,8 @@ def test_tune_then_solve(nvd, hub_graph, mode):
     a = nvd.ge_distance(G, on(X), on(Y), **kw)
     assert rel(a.cpu().numpy(), want) < tol
     # the tuned tile width and launch mode are what an open call uses
-    b = nvd.ge_distance(G, on(X), on(Y), kt=r["kt"], persistent=bool(r["persistent"]), **kw)
+    b = nvd.ge_distance(G, on(X), on(Y), kt=r["kt"], persistent=bool(r["persistent"]),
+                        fold_direction=bool(r["fold_direction"]), **kw)
     assert torch.equal(a, b)
 
 
