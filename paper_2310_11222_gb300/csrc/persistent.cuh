@@ -51,16 +51,34 @@ __device__ __forceinline__ bool grid_sync(const Ctx &c) {
     return __ldcg(c.err) == 0;
 }
 
+// Lane vectors per trip of the vector phases: the whole solve is one kernel, so its
+// register budget is the largest phase's; 16-byte lane vectors take 2 per trip.
+template <class TV, int KT>
+constexpr int persist_unroll() { return VecCfg<TV, KT>::VEC * (int)sizeof(TV) >= 16 ? 2 : 4; }
+
+// One phase over all blocks of the grid-stride loop.  (Out-of-line phases spilled
+// less but ran slower: call overhead and saved registers on every block.)
+template <class TV, int KT, class Op, int U>
+__device__ __forceinline__ void vec_phase(const Ctx &c, const Op op, char *smem) {
+    for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT, Op, U>(c, op, b, smem);
+}
+template <class TV, class TW, class TA, int KT, class Epi>
+__device__ __forceinline__ void spmm_phase(const Ctx &c, const Epi epi, const TV *src, TV *dst, char *smem) {
+    for (int64_t b = blockIdx.x; b < c.n_sblk; b += gridDim.x)
+        spmm_block<LdCoh, TV, TW, TA, KT>(c, epi, src, dst, b, smem);
+}
+
 // One tile: form delta, PCG to convergence, d^2, optional z_out, per-owner results.
 template <class TV, class TW, class TA, int KT, class TX>
 __device__ void persistent_solve(const Ctx &c, const PersistArgs &a, char *smem) {
+    constexpr int PU = persist_unroll<TV, KT>();
     TV *x = (TV *)a.x, *r = (TV *)a.r, *p = (TV *)a.p, *q = (TV *)a.q, *u = (TV *)a.u;
     // delta = x - y, segment sums
     {
         OpFormDelta<TX, KT> fd;
         fd.delta = a.delta;
         fd.fin.KT = KT;
-        for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<double, KT>(c, fd, b, smem);
+        vec_phase<double, KT, decltype(fd), PU>(c, fd, smem);
     }
     if (!grid_sync(c)) return;
     {
@@ -71,7 +89,7 @@ __device__ void persistent_solve(const Ctx &c, const PersistArgs &a, char *smem)
         oi.r = r;
         oi.p = a.fold ? u : p;
         oi.fin.KT = KT;
-        for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT>(c, oi, b, smem);
+        vec_phase<TV, KT, decltype(oi), PU>(c, oi, smem);
     }
     if (!grid_sync(c)) return;
     EpiLap epi;
@@ -96,19 +114,16 @@ __device__ void persistent_solve(const Ctx &c, const PersistArgs &a, char *smem)
     // in, then the x/r/u update), else three (SpMV on p, update, direction)
     for (int it = 0; it <= c.max_iter; ++it) {
         if (__ldcg(c.n_active) == 0) break;
-        if (a.fold) {
-            for (int64_t b = blockIdx.x; b < c.n_sblk; b += gridDim.x)
-                spmm_block<LdCoh, TV, TW, TA, KT>(c, epd, u, q, b, smem);
-        } else {
-            for (int64_t b = blockIdx.x; b < c.n_sblk; b += gridDim.x)
-                spmm_block<LdCoh, TV, TW, TA, KT>(c, epi, p, q, b, smem);
-        }
+        if (a.fold)
+            spmm_phase<TV, TW, TA, KT>(c, epd, u, q, smem);
+        else
+            spmm_phase<TV, TW, TA, KT>(c, epi, p, q, smem);
         if (!grid_sync(c)) return;
-        for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT>(c, ou, b, smem);
+        vec_phase<TV, KT, decltype(ou), PU>(c, ou, smem);
         if (!grid_sync(c)) return;
         if (a.fold) continue;
         if (__ldcg(c.n_active) == 0) break;
-        for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT>(c, od, b, smem);
+        vec_phase<TV, KT, decltype(od), PU>(c, od, smem);
         if (!grid_sync(c)) return;
     }
     {
@@ -117,14 +132,14 @@ __device__ void persistent_solve(const Ctx &c, const PersistArgs &a, char *smem)
         of.delta = a.delta;
         of.fin.KT = KT;
         of.fin.set_d2 = true;
-        for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT>(c, of, b, smem);
+        vec_phase<TV, KT, decltype(of), PU>(c, of, smem);
     }
     if (!grid_sync(c)) return;
     if (a.write_z) {
         OpZout<TV, TX, KT, LdCoh> oz;
         oz.src = x;
         oz.meanv = c.meanx;
-        for (int64_t b = blockIdx.x; b < c.n_vblk; b += gridDim.x) vec_block<TV, KT>(c, oz, b, smem);
+        vec_phase<TV, KT, decltype(oz), PU>(c, oz, smem);
     }
     // per (owner, column) results
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -18,9 +18,9 @@ namespace dev {
 // apply(c, i, col0, R&, dot) with per-thread partial sums of type Op::D (see DotOf).
 // Each thread handles U lane-vectors per trip with all U loads issued before the
 // first use.
-template <class TV, int KT, class Op>
+template <class TV, int KT, class Op, int U = 4>
 __device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
-    constexpr int VEC = VecCfg<TV, KT>::VEC, CG = KT / VEC, ND = Op::ND, U = 4;
+    constexpr int VEC = VecCfg<TV, KT>::VEC, CG = KT / VEC, ND = Op::ND;
     double *red = reinterpret_cast<double *>(smem);
     double *tot = red + red_doubles(KT);
     const Block blk = c.vblk[b];
