@@ -345,9 +345,10 @@ int run_components(nvd_graph_s *g, std::vector<int32_t> &root, cudaStream_t s) {
 
 int target_blocks(const nvd_graph_s *g) { return 2 * g->num_sms * 8; }
 
-// CTAs per SM of one vector pass.
+// CTAs per SM of one vector pass: one column 4 (64 registers each), several
+// columns 2 (128 registers each), i.e. one full wave either way.
 #ifndef VEC_PER_SM
-#define VEC_PER_SM 2
+#define VEC_PER_SM(KT) ((KT) == 1 ? 4 : 2)
 #endif
 
 uint64_t next_graph_id() {
@@ -503,14 +504,14 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     }
     seg_sblk_off[nseg] = (int32_t)sblk.size();
 
-    // Vector blocks: one wave of equal blocks, VEC_PER_SM per SM (the FP64 units
+    // Vector blocks: one wave of equal blocks, VEC_PER_SM(KT) per SM (the FP64 units
     // are per SM, so every SM gets the same share), at least 1024 row-columns each,
     // split over the segments in proportion to their rows.
     std::vector<Block> vblk;
     std::vector<int32_t> seg_vblk_off(nseg + 1, 0);
     int64_t rows_tot = 0;
     for (int s = 0; s < nseg; ++s) rows_tot += g->h_seg_end[s] - g->h_seg_begin[s];
-    const int64_t TV = (int64_t)VEC_PER_SM * g->num_sms;
+    const int64_t TV = (int64_t)VEC_PER_SM(KT) * g->num_sms;
     for (int s = 0; s < nseg; ++s) {
         seg_vblk_off[s] = (int32_t)vblk.size();
         const int64_t a = g->h_seg_begin[s], b = g->h_seg_end[s], nr = b - a;

@@ -57,11 +57,19 @@ __global__ void __launch_bounds__(NT, KT == 1 ? NVD_SPMV1_MINB : NVD_SPMM_MINB) 
     dev::spmm_block<dev::LdRO, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, smem);
 }
 
+// lane vectors per thread per trip of the vector passes (one column / several)
+#ifndef NVD_VEC_U1
+#define NVD_VEC_U1 4
+#endif
+#ifndef NVD_VEC_UK
+#define NVD_VEC_UK 4
+#endif
+
 template <class TV, int KT, class Op>
 __global__ void __launch_bounds__(NT, NVD_VEC_MINB(KT)) k_vec(Ctx c, Op op) {
     __shared__ __align__(16) char smem[vec_smem_bytes(KT)];
     pdl_trigger_and_wait();
-    dev::vec_block<TV, KT, Op>(c, op, blockIdx.x, smem);
+    dev::vec_block<TV, KT, Op, KT == 1 ? NVD_VEC_U1 : NVD_VEC_UK>(c, op, blockIdx.x, smem);
 }
 
 // Launch one of the kernels above on NT threads, with the programmatic-dependent-
