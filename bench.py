@@ -61,6 +61,26 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def rank_pair_range(rank):
+    """First pair index and count of a rank's share (ranks take disjoint pairs: weak scaling)."""
+    return rank * PAIRS_PER_STEP, PAIRS_PER_STEP
+
+
+def job_time(local, dist=None, device=None):
+    """The job's time: the maximum of the ranks' times (one all-reduce; none on one rank)."""
+    if dist is None:
+        return float(local)
+    import torch
+    t = torch.tensor([float(local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, steps, total_ms):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world * steps / (total_ms / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -433,7 +453,7 @@ def main():
 
     wl = synth.workload_er_large()
     g = wl.graph
-    X, Y = wl.pairs(rank * PAIRS_PER_STEP, PAIRS_PER_STEP)     # each rank its own pairs
+    X, Y = wl.pairs(*rank_pair_range(rank))                    # each rank its own pairs
     G = nvd.Graph.from_csr(g)
     # work decomposition picked by the autotuner on this graph (set-up, not timed)
     tuning = None if args.no_tune else G.tune(mode=nvd.MODE_FP64, k=PAIRS_PER_STEP, single_rhs=True)
@@ -476,11 +496,7 @@ def main():
     nvd.profile_enable(False)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_time(sum(step_ms), dist, dev)
     d2_last, stats = last
     iters = [s["iters"] for s in stats]
     statuses = [s["status"] for s in stats]
@@ -497,11 +513,7 @@ def main():
     for _ in range(args.steps):
         d2_host = nvd.ge_distance(G, xh, yh, rtol=RTOL, single_rhs=True, check_every=CHECK_EVERY)
     torch.cuda.synchronize()
-    te = time.perf_counter() - te0
-    if dist is not None:
-        t = torch.tensor([te], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+    te = job_time(time.perf_counter() - te0, dist, dev)
 
     # ---- the batched comparison the method is built for (same graph, same 8 pairs)
     extra = None
@@ -527,7 +539,7 @@ def main():
                  "tuning_fp64_multi": tune64, "tuning_mixed": tunemx,
                  "d2_fp64_multi": d64.cpu().numpy().tolist(), "d2_mixed": dmx.cpu().numpy().tolist()}
 
-    value = PAIRS_PER_STEP * world * args.steps / (total_ms / 1e3)
+    value = job_rate(PAIRS_PER_STEP, world, args.steps, total_ms)
     peaks, peak_src = measured_peaks()
     peak = float(peaks["hbm_gbs"])
     achieved = (spmv_bytes / n_spmv) / (spmv_ms / n_spmv / 1e3) / 1e9 if n_spmv else None
@@ -537,7 +549,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(workload_config(g, wl.meta["n_generated"]), tuning=tuning),
-        "e2e": {"value": PAIRS_PER_STEP * world * args.steps / te, "unit": UNIT,
+        "e2e": {"value": job_rate(PAIRS_PER_STEP, world, args.steps, 1e3 * te), "unit": UNIT,
                 "h2d_bytes_per_step": int(xh.numel() * 8 * 2), "d2h_bytes_per_step": PAIRS_PER_STEP * 8},
         "gpu_launches": int(launches),
         "clocks": clk,
