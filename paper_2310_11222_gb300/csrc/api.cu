@@ -1,4 +1,5 @@
 // C ABI: status strings, defaults, version and the SpMV/SpMM launch timer.
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -49,17 +50,18 @@ size_t prof_mark() {
     return g_pending.size();
 }
 
-// Keep the first `keep` SpMV launches (class 0) recorded after `mark`; the later
-// ones ran after convergence and found no work.  Vector-pass launches (class 1)
-// are all kept: their time is spent either way.
-void prof_keep(size_t mark, int64_t keep) {
+// Of the SpMV launches (class 0) recorded in [mark, end), keep the first `keep`;
+// the later ones ran after convergence and found no work.  Vector-pass launches
+// (class 1) and launches outside the range are all kept.
+void prof_keep_range(size_t mark, size_t end, int64_t keep) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (mark > g_pending.size()) return;
+    end = std::min(end, g_pending.size());
     int64_t seen = 0;
     std::vector<Pending> kept(g_pending.begin(), g_pending.begin() + mark);
     for (size_t i = mark; i < g_pending.size(); ++i) {
         Pending &p = g_pending[i];
-        if (p.cls != 0 || seen++ < keep) {
+        if (i >= end || p.cls != 0 || seen++ < keep) {
             kept.push_back(p);
         } else {
             cudaEventSynchronize(p.b);
@@ -69,6 +71,9 @@ void prof_keep(size_t mark, int64_t keep) {
     }
     g_pending.swap(kept);
 }
+
+// prof_keep_range up to the newest launch.
+void prof_keep(size_t mark, int64_t keep) { prof_keep_range(mark, (size_t)-1, keep); }
 
 void prof_begin(cudaStream_t s, int cls) {
     std::lock_guard<std::mutex> lk(g_mu);

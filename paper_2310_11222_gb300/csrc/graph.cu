@@ -628,6 +628,14 @@ void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c) {
 
 }  // namespace nvd
 
+nvd_graph_s::~nvd_graph_s() {
+    for (int k = 0; k < 2; ++k) {
+        if (ev_copied[k]) cudaEventDestroy(ev_copied[k]);
+        if (ev_used[k]) cudaEventDestroy(ev_used[k]);
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+}
+
 void *nvd_graph_s::wsp(const std::string &name, size_t bytes, int *st) {
     auto &slot = ws[name];
     if (!slot) slot.reset(new nvd::DevBuf());

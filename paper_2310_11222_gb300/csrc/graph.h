@@ -99,6 +99,11 @@ struct nvd_graph_s {
     int32_t tuned_fold[3] = {0, 0, 0};        // per solve mode: 1 = two kernels per iteration were faster
     std::map<int64_t, std::unique_ptr<nvd::Plan>> plans;
     std::map<std::string, std::unique_ptr<nvd::DevBuf>> ws;  // named lazily-grown workspace
+    // host-input staging: a copy stream and per-slot events (two slots), created on
+    // first use, so the next tile's host-to-device copy overlaps the current solve
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+    ~nvd_graph_s();
 
     void *wsp(const std::string &name, size_t bytes, int *st);
     int64_t device_bytes() const;

@@ -128,30 +128,67 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.bar_count = bar;
         c.bar_gen = bar + 1;
     }
-    // staging for host inputs/outputs
-    void *sx = nullptr, *sy = nullptr, *sz = nullptr;
+    // staging for host inputs/outputs: two slots, the next tile's copy on the copy
+    // stream overlaps the current tile's solve
+    void *sx[2] = {nullptr, nullptr}, *sy[2] = {nullptr, nullptr}, *sz = nullptr;
+    const int32_t ntiles = (k + KT - 1) / KT;
     if (host_in) {
         int st = NVD_OK;
-        sx = g->wsp("stage_x", (size_t)KT * g->n * xsz, &st);
-        sy = g->wsp("stage_y", (size_t)KT * g->n * xsz, &st);
-        if (z_out) sz = g->wsp("stage_z", (size_t)KT * g->n * xsz, &st);
+        const size_t tb = (size_t)KT * g->n * xsz;
+        for (int q = 0; q < (ntiles > 1 ? 2 : 1); ++q) {
+            sx[q] = g->wsp(q ? "stage_x1" : "stage_x", tb, &st);
+            sy[q] = g->wsp(q ? "stage_y1" : "stage_y", tb, &st);
+        }
+        if (z_out) sz = g->wsp("stage_z", tb, &st);
         if (st) return st;
+        if (!g->copy_stream) {
+            NVD_TRY_CUDA(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+            for (int q = 0; q < 2; ++q) {
+                NVD_TRY_CUDA(cudaEventCreateWithFlags(&g->ev_copied[q], cudaEventDisableTiming));
+                NVD_TRY_CUDA(cudaEventCreateWithFlags(&g->ev_used[q], cudaEventDisableTiming));
+            }
+        }
+        // the copy stream must not run ahead of work the caller queued on s before
+        // this call (it may still write x, y)
+        NVD_TRY_CUDA(cudaEventRecord(g->ev_used[1], s));
+        NVD_TRY_CUDA(cudaStreamWaitEvent(g->copy_stream, g->ev_used[1], 0));
     }
-    std::vector<ColResult> res(KT);
-    std::vector<int> it_mixed;
-    std::vector<double> rr_mixed;
+    auto stage = [&](int32_t t) -> int {
+        const int q = t & 1;
+        const int32_t t0 = t * KT;
+        const int kc = std::min<int>(KT, k - t0);
+        const size_t off = (size_t)t0 * g->n * xsz;
+        cudaStream_t cs = g->copy_stream;
+        if (t >= 2) NVD_TRY_CUDA(cudaStreamWaitEvent(cs, g->ev_used[q], 0));
+        NVD_TRY_CUDA(cudaMemcpyAsync(sx[q], (const char *)x + off, (size_t)kc * g->n * xsz, cudaMemcpyHostToDevice, cs));
+        NVD_TRY_CUDA(cudaMemcpyAsync(sy[q], (const char *)y + off, (size_t)kc * g->n * xsz, cudaMemcpyHostToDevice, cs));
+        NVD_TRY_CUDA(cudaEventRecord(g->ev_copied[q], cs));
+        return NVD_OK;
+    };
+    // per-tile results stay on the device until the end of the call (no host sync
+    // between tiles)
+    int st_res = NVD_OK;
+    ColResult *res_dev = (ColResult *)g->wsp("res_all", (size_t)ntiles * KT * sizeof(ColResult), &st_res);
+    if (st_res) return st_res;
+    std::vector<ColResult> res((size_t)ntiles * KT);
+    std::vector<std::vector<int>> it_mixed(ntiles);
+    std::vector<std::vector<double>> rr_mixed(ntiles);
+    std::vector<int> steps_t(ntiles, 0), conv_t(ntiles, 1);
+    std::vector<size_t> marks(ntiles, 0);
     int overall = NVD_OK;
     const bool need_host = !d2_dev || stats || host_in;
+    if (host_in) NVD_TRY(stage(0));
     for (int32_t c0 = 0; c0 < k; c0 += KT) {
+        const int32_t t = c0 / KT;
         const int kc = std::min<int>(KT, k - c0);
         const size_t off = (size_t)c0 * g->n * xsz;
         TileIO io;
         io.kc = kc;
         if (host_in) {
-            NVD_TRY_CUDA(cudaMemcpyAsync(sx, (const char *)x + off, (size_t)kc * g->n * xsz, cudaMemcpyHostToDevice, s));
-            NVD_TRY_CUDA(cudaMemcpyAsync(sy, (const char *)y + off, (size_t)kc * g->n * xsz, cudaMemcpyHostToDevice, s));
-            io.x = sx;
-            io.y = sy;
+            if (t + 1 < ntiles) NVD_TRY(stage(t + 1));
+            NVD_TRY_CUDA(cudaStreamWaitEvent(s, g->ev_copied[t & 1], 0));
+            io.x = sx[t & 1];
+            io.y = sy[t & 1];
             io.z = sz;
         } else {
             io.x = (const char *)x + off;
@@ -167,7 +204,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.rtol2 = o.rtol * o.rtol;
         c.max_iter = o.max_iter;
         int steps = 0, conv = 1;
-        const size_t pmark = prof_enabled() ? prof_mark() : 0;
+        marks[t] = prof_enabled() ? prof_mark() : 0;
         if (persistent) {
             NVD_TRY_CUDA(cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 8) * 4, s));
             NVD_TRY_CUDA(cudaMemsetAsync(bar, 0, 16, s));
@@ -179,23 +216,37 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         else if (o.mode == NVD_MODE_FP32)
             NVD_TRY(run_tile_fp32(g, c, w, o, io, s, KT, xdt));
         else
-            NVD_TRY(run_tile_mixed(g, c, pl64, w, o, io, s, KT, xdt, it_mixed, rr_mixed, &steps, &conv));
+            NVD_TRY(run_tile_mixed(g, c, pl64, w, o, io, s, KT, xdt, it_mixed[t], rr_mixed[t], &steps, &conv));
+        steps_t[t] = steps;
+        conv_t[t] = conv;
         NVD_TRY(run_collect(c, KT, w.res, d2_dev ? d2_out + c0 : nullptr, 0, 1, s));
+        NVD_TRY_CUDA(cudaMemcpyAsync(res_dev + (size_t)t * KT, w.res, KT * sizeof(ColResult),
+                                     cudaMemcpyDeviceToDevice, s));
+        if (host_in) NVD_TRY_CUDA(cudaEventRecord(g->ev_used[t & 1], s));
         if (host_in && z_out)
             NVD_TRY_CUDA(cudaMemcpyAsync((char *)z_out + off, sz, (size_t)kc * g->n * xsz, cudaMemcpyDeviceToHost, s));
-        if (need_host || prof_enabled()) {
-            NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), w.res, KT * sizeof(ColResult), cudaMemcpyDeviceToHost, s));
-            NVD_TRY_CUDA(cudaStreamSynchronize(s));
-            if (prof_enabled() && !mixed) {
+    }
+    if (need_host || prof_enabled()) {
+        NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), res_dev, (size_t)ntiles * KT * sizeof(ColResult),
+                                     cudaMemcpyDeviceToHost, s));
+        NVD_TRY_CUDA(cudaStreamSynchronize(s));
+        if (prof_enabled() && !mixed) {
+            // drop the post-convergence SpMV launches of each tile (last tile first:
+            // the earlier marks stay valid)
+            for (int32_t t = ntiles - 1; t >= 0; --t) {
                 int real = 0;
-                for (int j = 0; j < kc; ++j) real = std::max(real, res[j].iters);
-                prof_keep(pmark, real);
+                for (int j = 0; j < std::min<int>(KT, k - t * KT); ++j) real = std::max(real, res[(size_t)t * KT + j].iters);
+                prof_keep_range(marks[t], t + 1 < ntiles ? marks[t + 1] : (size_t)-1, real);
             }
         }
-        if (need_host) {
+    }
+    if (need_host) {
+        for (int32_t t = 0; t < ntiles; ++t) {
+            const int32_t c0 = t * KT;
+            const int kc = std::min<int>(KT, k - c0);
             for (int j = 0; j < kc; ++j) {
-                ColResult &r = res[j];
-                if (mixed) r.status = conv ? NVD_OK : NVD_ERR_NOT_CONVERGED;
+                ColResult &r = res[(size_t)t * KT + j];
+                if (mixed) r.status = conv_t[t] ? NVD_OK : NVD_ERR_NOT_CONVERGED;
                 if (!d2_dev) d2_out[c0 + j] = r.d2;
                 if (r.status != NVD_OK && overall != NVD_ERR_NUMERIC) overall = r.status;
                 if (stats) {
@@ -203,9 +254,9 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
                     st.status = r.status;
                     st.reserved = 0;
                     if (mixed) {
-                        st.iters = it_mixed[j];
-                        st.refine_steps = steps;
-                        st.rel_resid = rr_mixed[j];
+                        st.iters = it_mixed[t][j];
+                        st.refine_steps = steps_t[t];
+                        st.rel_resid = rr_mixed[t][j];
                     } else {
                         st.iters = r.iters;
                         st.refine_steps = 0;

@@ -120,6 +120,7 @@ void prof_begin(cudaStream_t s, int cls = 0);
 void prof_end(cudaStream_t s, double bytes);
 size_t prof_mark();
 void prof_keep(size_t mark, int64_t keep);
+void prof_keep_range(size_t mark, size_t end, int64_t keep);
 void note_launch(int64_t n = 1);
 
 // ------------------------------------------------------------------ workspace
