@@ -304,9 +304,11 @@ const char *nvd_last_error(void);
  * algorithmic bytes of those launches since the last read (and resets them).
  * Class 0 = the SpMV/SpMM kernel, class 1 = the streaming vector passes (bytes
  * not tracked).  SpMV launches issued after every pair of a tile had converged
- * (they find nothing to do) are dropped from the count.  Enabling
- * forces the host-driven loop (no persistent kernel) so launches can be
- * bracketed.
+ * (they find nothing to do) are dropped from the count.  Bits 8..15 of `on`
+ * give a sampling period s (0 or 1 = every launch): only every s-th SpMV launch
+ * is bracketed, so the events disturb the launch sequence less (a bracketed
+ * launch cannot overlap its neighbours' start-up).  Enabling forces the
+ * host-driven loop (no persistent kernel) so launches can be bracketed.
  */
 int nvd_profile_enable(int32_t on);
 int nvd_profile_read(int32_t kernel_class, int64_t *launches, double *total_ms,

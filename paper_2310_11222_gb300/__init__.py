@@ -399,9 +399,13 @@ def kernel_launches() -> int:
     return int(load_library().nvd_kernel_launches())
 
 
-def profile_enable(on=True):
-    """on: False/0 off, True/1 time the SpMV launches, 2 also the vector passes."""
-    _check(load_library().nvd_profile_enable(int(on)), "nvd_profile_enable")
+def profile_enable(on=True, every: int = 1):
+    """on: False/0 off, True/1 time the SpMV launches, 2 also the vector passes;
+    every: time one SpMV launch in ``every`` (1..255)."""
+    code = int(on)
+    if code and every > 1:
+        code |= (min(int(every), 255) & 0xff) << 8
+    _check(load_library().nvd_profile_enable(code), "nvd_profile_enable")
 
 
 def profile_read(kernel_class: int = 0):

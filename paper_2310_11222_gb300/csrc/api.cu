@@ -17,9 +17,12 @@ struct Pending {
     cudaEvent_t a, b;
     double bytes;
     int cls;
+    int64_t seq;     // SpMV launch number (class 0)
 };
 std::mutex g_mu;
 int g_enabled = 0;   // 0 off, 1 SpMV launches, 2 SpMV and vector passes
+int g_every = 1;     // time one SpMV launch in g_every
+int64_t g_seq = 0;   // SpMV launches seen while enabled
 std::vector<cudaEvent_t> g_pool;
 std::vector<Pending> g_pending;
 constexpr int NCLS = 2;
@@ -50,18 +53,18 @@ size_t prof_mark() {
     return g_pending.size();
 }
 
-// Of the SpMV launches (class 0) recorded in [mark, end), keep the first `keep`;
-// the later ones ran after convergence and found no work.  Vector-pass launches
-// (class 1) and launches outside the range are all kept.
-void prof_keep_range(size_t mark, size_t end, int64_t keep) {
+// Of the SpMV launches (class 0) recorded in [mark, end), keep those among the
+// first `keep` launched since sequence number seq0; the later ones ran after
+// convergence and found no work.  Vector-pass launches (class 1) and launches
+// outside the range are all kept.
+void prof_keep_range(size_t mark, size_t end, int64_t keep, int64_t seq0) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (mark > g_pending.size()) return;
     end = std::min(end, g_pending.size());
-    int64_t seen = 0;
     std::vector<Pending> kept(g_pending.begin(), g_pending.begin() + mark);
     for (size_t i = mark; i < g_pending.size(); ++i) {
         Pending &p = g_pending[i];
-        if (i >= end || p.cls != 0 || seen++ < keep) {
+        if (i >= end || p.cls != 0 || p.seq - seq0 < keep) {
             kept.push_back(p);
         } else {
             cudaEventSynchronize(p.b);
@@ -72,14 +75,22 @@ void prof_keep_range(size_t mark, size_t end, int64_t keep) {
     g_pending.swap(kept);
 }
 
-// prof_keep_range up to the newest launch.
-void prof_keep(size_t mark, int64_t keep) { prof_keep_range(mark, (size_t)-1, keep); }
-
-void prof_begin(cudaStream_t s, int cls) {
+int64_t prof_seq() {
     std::lock_guard<std::mutex> lk(g_mu);
-    Pending p{take_event(), take_event(), 0.0, cls};
+    return g_seq;
+}
+
+bool prof_begin(cudaStream_t s, int cls) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int64_t seq = -1;
+    if (cls == 0) {
+        seq = g_seq++;
+        if (seq % g_every != 0) return false;   // not sampled: no events, no PDL break
+    }
+    Pending p{take_event(), take_event(), 0.0, cls, seq};
     cudaEventRecord(p.a, s);
     g_pending.push_back(p);
+    return true;
 }
 
 void prof_end(cudaStream_t s, double bytes) {
@@ -96,7 +107,10 @@ using namespace nvd;
 
 extern "C" int nvd_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_enabled = on <= 0 ? 0 : on == 1 ? 1 : 2;
+    const int mode = on <= 0 ? 0 : on & 0xff;
+    g_enabled = mode == 0 ? 0 : mode == 1 ? 1 : 2;
+    const int every = on > 0 ? (on >> 8) & 0xff : 0;
+    g_every = every < 1 ? 1 : every;
     return NVD_OK;
 }
 

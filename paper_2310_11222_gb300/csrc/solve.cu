@@ -175,6 +175,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     std::vector<std::vector<double>> rr_mixed(ntiles);
     std::vector<int> steps_t(ntiles, 0), conv_t(ntiles, 1);
     std::vector<size_t> marks(ntiles, 0);
+    std::vector<int64_t> seq0(ntiles, 0);
     int overall = NVD_OK;
     const bool need_host = !d2_dev || stats || host_in;
     if (host_in) NVD_TRY(stage(0));
@@ -205,6 +206,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.max_iter = o.max_iter;
         int steps = 0, conv = 1;
         marks[t] = prof_enabled() ? prof_mark() : 0;
+        seq0[t] = prof_enabled() ? prof_seq() : 0;
         if (persistent) {
             NVD_TRY_CUDA(cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 8) * 4, s));
             NVD_TRY_CUDA(cudaMemsetAsync(bar, 0, 16, s));
@@ -236,7 +238,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
             for (int32_t t = ntiles - 1; t >= 0; --t) {
                 int real = 0;
                 for (int j = 0; j < std::min<int>(KT, k - t * KT); ++j) real = std::max(real, res[(size_t)t * KT + j].iters);
-                prof_keep_range(marks[t], t + 1 < ntiles ? marks[t + 1] : (size_t)-1, real);
+                prof_keep_range(marks[t], t + 1 < ntiles ? marks[t + 1] : (size_t)-1, real, seq0[t]);
             }
         }
     }

@@ -116,11 +116,12 @@ __global__ void k_collect(Ctx c, ColResult *res, double *d2dev, int64_t d2_strid
 
 bool prof_enabled();
 bool prof_vec_enabled();
-void prof_begin(cudaStream_t s, int cls = 0);
+// false: this launch is not timed (sampling); do not call prof_end for it
+bool prof_begin(cudaStream_t s, int cls = 0);
 void prof_end(cudaStream_t s, double bytes);
 size_t prof_mark();
-void prof_keep(size_t mark, int64_t keep);
-void prof_keep_range(size_t mark, size_t end, int64_t keep);
+int64_t prof_seq();
+void prof_keep_range(size_t mark, size_t end, int64_t keep, int64_t seq0);
 void note_launch(int64_t n = 1);
 
 // ------------------------------------------------------------------ workspace
@@ -186,8 +187,7 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
         set_error("internal: SpMV plan built for another tile width or precision");
         return NVD_ERR_UNSUPPORTED;
     }
-    const bool prof = prof_enabled();
-    if (prof) prof_begin(s);
+    const bool prof = prof_enabled() && prof_begin(s);
     NVD_TRY_CUDA(launch_dependent(k_spmm<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, s, c, epi, src, dst));
     note_launch();
     if (prof) prof_end(s, bytes);
@@ -197,8 +197,7 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
 template <class TV, int KT, class Op>
 inline int launch_vec(const Ctx &c, const Op &op, cudaStream_t s) {
     if (c.n_vblk == 0) return NVD_OK;
-    const bool prof = prof_vec_enabled();
-    if (prof) prof_begin(s, 1);
+    const bool prof = prof_vec_enabled() && prof_begin(s, 1);
     NVD_TRY_CUDA(launch_dependent(k_vec<TV, KT, Op>, (unsigned)c.n_vblk, s, c, op));
     if (prof) prof_end(s, 0.0);
     note_launch();

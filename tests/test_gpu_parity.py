@@ -192,6 +192,35 @@ def test_host_inputs_path_matches_device_path(nvd, ba_small):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("mode,kw", [(0, dict(single_rhs=True)), (0, dict(kt=4)), (2, dict(kt=4))])
+def test_host_inputs_many_tiles_with_z(nvd, mode, kw):
+    """Host inputs over 5+ tiles (the two staging slots are each reused) with z_out on a
+    graph with interleaved components and an isolated node (node permutation): d^2 and
+    z equal the device-input path bitwise, stats per pair included."""
+    rng = np.random.default_rng(21)
+    parts = []
+    for seed, n in [(1, 400), (2, 1), (3, 250)]:
+        r = np.random.default_rng(seed)
+        if n == 1:
+            parts.append(synth.csr_from_edges(1, np.empty(0, np.int64), np.empty(0, np.int64), np.empty(0)))
+        else:
+            eu, ev = synth.barabasi_albert(n, 3, r)
+            parts.append(synth.csr_from_edges(n, eu, ev, r.uniform(0.5, 2, size=len(eu))))
+    gu, _ = synth.disjoint_union(parts)
+    perm = rng.permutation(gu.n)
+    g = synth.csr_from_edges(gu.n, perm[gu.eu], perm[gu.ev], gu.ew)
+    X, Y = rng.random((18, g.n)), rng.random((18, g.n))
+    G = nvd.Graph.from_csr(g)
+    a, za, sa = nvd.ge_distance(G, on(X), on(Y), mode=mode, rtol=1e-10, return_z=True, return_stats=True, **kw)
+    b, zb, sb = nvd.ge_distance(G, torch.from_numpy(X), torch.from_numpy(Y), mode=mode, rtol=1e-10,
+                                return_z=True, return_stats=True, **kw)
+    assert np.array_equal(a.cpu().numpy(), b.numpy())
+    assert np.array_equal(za.cpu().numpy(), zb.numpy())
+    assert [s["iters"] for s in sa] == [s["iters"] for s in sb]
+    want = dense.ge_d2_eig(g.n, g.rowptr, g.colidx, g.w, X, Y)
+    assert rel(b.numpy(), want) < 1e-8
+
+
 def test_repeatable_bitwise(nvd, ba_small):
     g, X, Y, _ = ba_small
     G = nvd.Graph.from_csr(g)
