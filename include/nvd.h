@@ -115,6 +115,9 @@ typedef enum {
 #define NVD_SOLVE_HOST_INPUTS 4u  /* x, y (and z_out) are host pointers; copies are done here */
 #define NVD_SOLVE_PERSISTENT 8u   /* run each PCG solve inside one persistent cooperative kernel */
 #define NVD_SOLVE_NO_SYNC 16u     /* with NVD_SOLVE_D2_DEVICE and no stats: return without a final sync */
+#define NVD_SOLVE_TEST_TIMEOUT 64u /* diagnostic, with NVD_SOLVE_PERSISTENT: the grid barrier waits for
+                                     one arrival more than the grid has, so its bounded wait runs out;
+                                     the call returns NVD_ERR_TIMEOUT (exercises the timeout path) */
 #define NVD_SOLVE_FOLD_DIRECTION 32u /* two kernels per CG iteration: the direction update folded into
                                         an SpMV on D^-1 r (default: three, SpMV on p, x/r update,
                                         direction pass) */

@@ -38,6 +38,7 @@ SOLVE_HOST_INPUTS = 4
 SOLVE_PERSISTENT = 8
 SOLVE_NO_SYNC = 16
 SOLVE_FOLD_DIRECTION = 32
+SOLVE_TEST_TIMEOUT = 64
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_SYM_CHECK = 2
 TUNE_SINGLE_RHS = 1
@@ -274,7 +275,7 @@ class Graph:
 def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
                 d2_rtol: float = 1e-8, max_iter: int = 10000, max_refine: int = 8, kt: int = 0,
                 check_every: int = 4, single_rhs: bool = False, persistent: bool = False,
-                fold_direction: bool = False,
+                fold_direction: bool = False, test_timeout: bool = False,
                 return_z: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
     """Squared GE distances d^2 for the k pairs (rows) of x, y ([k, n] or [n]).
 
@@ -304,6 +305,8 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
         o.flags |= SOLVE_PERSISTENT
     if fold_direction:
         o.flags |= SOLVE_FOLD_DIRECTION
+    if test_timeout:
+        o.flags |= SOLVE_TEST_TIMEOUT
     xdt = _dtype_code(X)
     stats = (SolveStats * max(k, 1))()
     if X.is_cuda:

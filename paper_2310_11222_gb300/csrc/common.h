@@ -128,6 +128,7 @@ struct Ctx {
     int32_t sl_h;                   // H of the plan the pointers above belong to
     // ---- persistent-kernel grid barrier
     unsigned *bar_count, *bar_gen;
+    int32_t bar_extra;              // arrivals awaited beyond the grid (0; 1 only to test the timeout)
     Owner own0;
 };
 

@@ -29,7 +29,7 @@ __device__ __forceinline__ bool grid_sync(const Ctx &c) {
         const unsigned gen = atomicAdd(c.bar_gen, 0u);
         __threadfence();
         const unsigned arrived = atomicAdd(c.bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == gridDim.x - 1 + (unsigned)c.bar_extra) {
             atomicExch(c.bar_count, 0u);
             __threadfence();
             atomicAdd(c.bar_gen, 1u);

@@ -65,7 +65,8 @@ int pick_kt(const nvd_graph_s *g, const nvd_solve_opts &o, int k) {
 
 int check_opts(const nvd_solve_opts &o) {
     const uint32_t known = NVD_SOLVE_SINGLE_RHS | NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS |
-                           NVD_SOLVE_PERSISTENT | NVD_SOLVE_NO_SYNC | NVD_SOLVE_FOLD_DIRECTION;
+                           NVD_SOLVE_PERSISTENT | NVD_SOLVE_NO_SYNC | NVD_SOLVE_FOLD_DIRECTION |
+                           NVD_SOLVE_TEST_TIMEOUT;
     if (o.mode < NVD_MODE_FP64 || o.mode > NVD_MODE_MIXED || !(o.rtol > 0.0) || o.max_iter < 1 ||
         o.check_every < 1 || !(o.kt == 0 || o.kt == 1 || o.kt == 4 || o.kt == 8 || o.kt == 16 || o.kt == 32) ||
         (o.flags & ~known) || (o.mode == NVD_MODE_MIXED && (!(o.d2_rtol > 0.0) || o.max_refine < 1))) {
@@ -127,6 +128,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         if (st) return st;
         c.bar_count = bar;
         c.bar_gen = bar + 1;
+        c.bar_extra = (o.flags & NVD_SOLVE_TEST_TIMEOUT) ? 1 : 0;
     }
     // staging for host inputs/outputs: two slots, the next tile's copy on the copy
     // stream overlaps the current tile's solve
@@ -208,7 +210,9 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         marks[t] = prof_enabled() ? prof_mark() : 0;
         seq0[t] = prof_enabled() ? prof_seq() : 0;
         if (persistent) {
-            NVD_TRY_CUDA(cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 8) * 4, s));
+            // active, iters, status and n_active; the barrier's error flag (c.err)
+            // stays sticky across the tiles of the call
+            NVD_TRY_CUDA(cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 1) * 4, s));
             NVD_TRY_CUDA(cudaMemsetAsync(bar, 0, 16, s));
             PersistArgs a{w.delta, w.x, w.r, w.p, w.q, w.u, (o.flags & NVD_SOLVE_FOLD_DIRECTION) ? 1 : 0,
                           w.res, 1, io.z ? 1 : 0};
@@ -266,6 +270,16 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
                     }
                 }
             }
+        }
+    }
+    if (persistent) {
+        // a grid barrier that gave up (bounded wait) leaves its status in c.err
+        int32_t err = 0;
+        NVD_TRY_CUDA(cudaMemcpyAsync(&err, c.err, 4, cudaMemcpyDeviceToHost, s));
+        NVD_TRY_CUDA(cudaStreamSynchronize(s));
+        if (err != 0) {
+            set_error("nvd_ge_distance: the persistent kernel's grid barrier gave up (status %d)", err);
+            return err;
         }
     }
     if (!(o.flags & NVD_SOLVE_NO_SYNC) || need_host) NVD_TRY_CUDA(cudaStreamSynchronize(s));
