@@ -19,12 +19,7 @@ constexpr int NWARP = NT / 32;
 //   KT = 1: a row with more entries, up to sp_long_max, is a sub-item of its own for
 //           a whole warp; longer rows are split into chunks of sp_chunk entries,
 //           one warp each.
-//   KT > 1: heavy rows are split into chunks of sp_chunk entries, one CTA each; the
-//           row accumulators (rows x KT x sza) fit 8 KB.
-constexpr int sp_rows_budget(int KT, int sza) {
-    return KT == 1 ? 256 : ((8192 / (KT * sza)) > NT ? NT : (8192 / (KT * sza)));
-}
-constexpr int sp_nnz_budget(int KT, int szv) { return KT == 1 ? 2048 : 32768 / (KT * szv); }
+//   KT > 1: heavy rows are split into chunks of sp_chunk entries, one CTA each.
 constexpr int sp_row_max(int KT, int szv) { return KT == 1 ? 128 : 32768 / (KT * szv); }
 constexpr int sp_long_max(int KT) { return KT == 1 ? 8192 : 0; }
 constexpr int sp_chunk(int KT, int szv) { return KT == 1 ? 4096 : 32768 / (KT * szv); }
@@ -40,9 +35,9 @@ constexpr int red_doubles(int KT) {
 }
 constexpr int vec_smem_bytes(int KT) { return (red_doubles(KT) + 4 * KT) * 8; }
 
-// Sub-item of the Laplacian SpMV/SpMM.
-//   kind 0: rows [r0, r1) of one segment whose entries fit one pass.
-//   kind 2: one long row r0, entries [e0, e1), processed whole (KT = 1 only).
+// Heavy sub-item of the Laplacian SpMV/SpMM (rows above the light-row limit; the
+// light rows are in the sliced layout).
+//   kind 2: one long row r0, entries [e0, e1), processed whole by a warp (KT = 1).
 //   kind 1: entries [e0, e1) of a very long row r0 split over several sub-items
 //           (merge-path style row splitting); this is chunk `hchunk` of `nchunk`;
 //           its partial row sum goes to hsum[hbase + hchunk] and the chunk that

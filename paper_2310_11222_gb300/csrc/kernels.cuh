@@ -8,8 +8,9 @@
 //
 // Work layout: block vectors are [n][KT] row-major (KT right-hand sides side by
 // side, one 16-byte-aligned row per node), the graph is CSR in internal node
-// order where every connected component ("segment") is a contiguous node
-// range.  Each CTA block covers a contiguous run of one segment and owns one
+// order where every connected component ("segment") is a contiguous node range,
+// plus a sliced copy of its light rows (see Ctx::sl_*).  Each CTA block covers
+// work of one segment (slices, heavy sub-items or a row range) and owns one
 // partial-sum slot per inner product; the last block of a segment to finish
 // (atomic arrival counter) sums the segment's slots in slot order and updates
 // the per-(segment, column) CG scalars -- so every reduction is deterministic
@@ -567,24 +568,20 @@ struct EpiResid {
 
 // ------------------------------------------------------------------ SpMV / SpMM block
 
-// Work budgets per sub-item (also used by the host planner, see plan_params()).
+// Lane layout of the multi-column SpMM and the shared memory of a CTA: the row
+// accumulators of one split row (KT x sza), the reduction scratch and the totals.
 template <class TV, class TA, int KT>
 struct SpCfg {
     static constexpr int VEC = VecCfg<TV, KT>::VEC;
     static constexpr int LPR = KT / VEC;          // lanes per gathered row vector
-    static constexpr int G = 32 / LPR;            // entries in flight per warp
-    // rows per sub-item: s_acc holds RB x KT accumulators (<= 8 KB)
-    static constexpr int RB = sp_rows_budget(KT, (int)sizeof(TA));
-    // entries per sub-item (KT = 1: staged products; KT > 1: ~32 KB of gathers)
-    static constexpr int NB = sp_nnz_budget(KT, (int)sizeof(TV));
+    static constexpr int G = 32 / LPR;            // rows per warp (rows per slice)
     static constexpr int ND_MAX = 4;
     static constexpr int RED = red_doubles(KT);
-    static constexpr int SMEM = (KT == 1 ? 0 : RB * KT * (int)sizeof(TA))  // row accumulators
-                                + RED * 8                                 // red
-                                + ND_MAX * KT * 8;                        // tot
+    static constexpr int ACC = KT == 1 ? 0 : ((KT * (int)sizeof(TA) + 15) / 16) * 16;
+    static constexpr int SMEM = ACC + RED * 8 + ND_MAX * KT * 8;
 };
 
-// Phase B of a sub-item: rows [r0, r1) with accumulated neighbour sums in s_acc.
+// Row epilogue of a split row: rows [r0, r1) with their neighbour sums in s_acc.
 template <class LD, class TV, class TA, int KT, class Epi, class DT>
 __device__ __forceinline__ void spmm_epilogue(const Ctx &c, const Epi &epi, int seg, const TV *src, TV *dst,
                                               int64_t r0, int64_t r1, const TA *s_acc,
@@ -881,7 +878,7 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
     }
 }
 
-// One SpMV/SpMM block b: its sub-items, then the segment arrival.
+// One SpMV/SpMM block b: its slices or heavy sub-items, then the segment arrival.
 template <class LD, class TV, class TW, class TA, int KT, class Epi>
 __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ src, TV *__restrict__ dst,
                            int64_t b, char *smem) {
@@ -892,7 +889,7 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
     typedef SpCfg<TV, TA, KT> C;
     constexpr int VEC = C::VEC, LPR = C::LPR, G = C::G, ND = Epi::ND;
     TA *s_acc = reinterpret_cast<TA *>(smem);
-    double *red = reinterpret_cast<double *>(smem + C::RB * KT * sizeof(TA));
+    double *red = reinterpret_cast<double *>(smem + C::ACC);
     double *tot = red + C::RED;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Block blk = c.sblk[b];
