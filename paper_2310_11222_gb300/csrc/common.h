@@ -23,6 +23,9 @@ constexpr int NWARP = NT / 32;
 constexpr int sp_row_max(int KT, int szv) { return KT == 1 ? 128 : 32768 / (KT * szv); }
 constexpr int sp_long_max(int KT) { return KT == 1 ? 8192 : 0; }
 constexpr int sp_chunk(int KT, int szv) { return KT == 1 ? 4096 : 32768 / (KT * szv); }
+// Rows (first to last) one single-column light SpMV block may span: its row sums
+// are staged in shared memory by row so the row epilogue runs in row order.
+constexpr int sp_span_max() { return 1024; }
 // Columns one lane owns (16-byte vectors where the row is that wide), lanes per
 // row, and rows per slice (one row per lane group of a warp).
 constexpr int sp_vec(int KT, int szv) { return KT * szv >= 16 ? 16 / szv : KT; }
@@ -51,12 +54,15 @@ struct SpItem {
 static_assert(sizeof(SpItem) == 48, "SpItem layout");
 
 // A CTA block: a contiguous run of work inside one segment.
-//   SpMV light blocks (pad = 0): slices [i0, i1).  SpMV heavy blocks (pad = 1):
-//   sub-items [i0, i1).  Vector blocks: rows [i0, i1).
+//   SpMV light blocks (pad = 0): slices [i0, i1) (rows r0 .. r0 + nr - 1 for one
+//   column).  SpMV heavy blocks (pad = 1): sub-items [i0, i1).  Vector blocks:
+//   rows [i0, i1).
 struct Block {
     int64_t i0, i1;
     int32_t seg, pad;
+    int32_t r0, nr;   // single-column light SpMV blocks: first row, rows spanned (<= sp_span_max)
 };
+static_assert(sizeof(Block) == 32, "Block layout");
 
 // Where one user graph's pairs live: x, y, z of shape [k][n_o] already offset to
 // the first column of the tile; the graph's nodes are internal nodes

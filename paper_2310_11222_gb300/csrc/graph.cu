@@ -478,16 +478,23 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
             }
             sl_base.push_back(sl_base.back() + L * H);
         }
-        sblk.push_back(Block{first, (int64_t)sl_base.size() - 1, s, 0});
+        sblk.push_back(Block{first, (int64_t)sl_base.size() - 1, s, 0, (int32_t)rows.front(),
+                             (int32_t)(rows.back() - rows.front() + 1)});
         rows.clear();
         lens.clear();
     };
+    // one column: a block's rows span at most sp_span_max() rows
+    const int64_t SPAN = KT == 1 ? sp_span_max() : INT64_MAX;
     for (int s = 0; s < nseg; ++s) {
         seg_sblk_off[s] = (int32_t)sblk.size();
         double acc = 0.0;
         for (int64_t r = g->h_seg_begin[s]; r < g->h_seg_end[s]; ++r) {
             const int64_t d = rp[r + 1] - rp[r];
             if (d > RMAX) continue;
+            if (!rows.empty() && r - rows.front() + 1 > SPAN) {
+                emit_block(s);
+                acc = 0.0;
+            }
             rows.push_back(r);
             lens.push_back(d);
             acc += (double)d + 1.0;
@@ -500,7 +507,7 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
         const size_t per = KT == 1 ? (size_t)NWARP : 4;
         const int64_t h0 = seg_item_off[s], h1 = seg_item_off[s + 1];
         for (int64_t q = h0; q < h1; q += (int64_t)per)
-            sblk.push_back(Block{q, std::min<int64_t>(h1, q + (int64_t)per), s, 1});
+            sblk.push_back(Block{q, std::min<int64_t>(h1, q + (int64_t)per), s, 1, 0, 0});
     }
     seg_sblk_off[nseg] = (int32_t)sblk.size();
 
@@ -519,7 +526,7 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
         const int64_t maxb = std::max<int64_t>(1, (nr * KT + 1023) / 1024);
         nb = std::max<int64_t>(1, std::min<int64_t>(nb, maxb));
         for (int64_t k = 0; k < nb; ++k)
-            vblk.push_back(Block{a + nr * k / nb, a + nr * (k + 1) / nb, s, 0});
+            vblk.push_back(Block{a + nr * k / nb, a + nr * (k + 1) / nb, s, 0, 0, 0});
     }
     seg_vblk_off[nseg] = (int32_t)vblk.size();
 

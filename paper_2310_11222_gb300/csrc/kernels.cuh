@@ -578,7 +578,11 @@ struct SpCfg {
     static constexpr int ND_MAX = 4;
     static constexpr int RED = red_doubles(KT);
     static constexpr int ACC = KT == 1 ? 0 : ((KT * (int)sizeof(TA) + 15) / 16) * 16;
-    static constexpr int SMEM = ACC + RED * 8 + ND_MAX * KT * 8;
+    // one column: the light rows' row sums (sp_span_max of them) live in the
+    // reduction scratch, their presence bits after the totals
+    static constexpr int HAS = KT == 1 ? sp_span_max() / 32 * 4 : 0;
+    static_assert(KT != 1 || RED * 8 >= sp_span_max() * (int)sizeof(TA), "row sums fit the scratch");
+    static constexpr int SMEM = ACC + RED * 8 + ND_MAX * KT * 8 + HAS;
 };
 
 // Row epilogue of a split row: rows [r0, r1) with their neighbour sums in s_acc.
@@ -794,11 +798,17 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
             // row per lane; entry j of the 32 rows is one coalesced load of columns
             // and of weights, the gathers of SPMV1_UNROLL entries are in flight
             // before their products, and each lane adds its row's products in entry
-            // order into one accumulator (no cross-lane sum)
+            // order into one accumulator (no cross-lane sum).  The row sums go to
+            // shared memory by row (rows r0 .. r0 + nr - 1; a bit marks each light
+            // row of the span) and the row epilogue then runs in row order, so its
+            // loads and stores of the own row are coalesced.
+            TA *s_acc = reinterpret_cast<TA *>(red);   // [nr]; the reduction scratch is free until the end
+            unsigned *s_has = reinterpret_cast<unsigned *>(tot + SpCfg<TV, TA, 1>::ND_MAX);
+            const int32_t r0 = blk.r0, nr = blk.nr;
+            for (int t = threadIdx.x; t < (nr + 31) / 32; t += NT) s_has[t] = 0u;
+            __syncthreads();
             const TW *__restrict__ slw = reinterpret_cast<const TW *>(c.sl_w);
             const int64_t ns = blk.i1 - blk.i0;
-            Epi e = epi;
-            e.prep(c, seg, 0);
             for (int64_t round = 0; round * NWARP < ns; ++round) {
                 // longest slices first; alternate rounds reverse the warp order so
                 // the warps' totals even out
@@ -808,12 +818,6 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
                 const int64_t base = __ldg(c.sl_base + sl);
                 const int L = (int)((__ldg(c.sl_base + sl + 1) - base) >> 5);
                 const int32_t i = __ldg(c.sl_row + sl * 32 + lane);
-                TV own[1] = {(TV)0};
-                TA dg = 0;
-                if (i >= 0) {
-                    own[0] = LD::ld(src + i);
-                    dg = __ldg(deg + i);
-                }
                 const int32_t *__restrict__ cp = c.sl_col + base + lane;
                 const TW *__restrict__ wp = slw + base + lane;
                 // L is the same for the whole warp, so the bounds tests below are
@@ -854,10 +858,22 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
                     }
                 }
                 if (i >= 0) {
-                    const TA av[1] = {acc};
-                    e.template elem<TV, TA, 1>(c, i, 0, 1, own, av, dg, dst, dot);
+                    const int t = i - r0;
+                    s_acc[t] = acc;
+                    atomicOr(s_has + (t >> 5), 1u << (t & 31));
                 }
             }
+            __syncthreads();
+            Epi e = epi;
+            e.prep(c, seg, 0);
+            for (int t = threadIdx.x; t < nr; t += NT) {
+                if (!((s_has[t >> 5] >> (t & 31)) & 1u)) continue;   // a heavy row inside the span
+                const int64_t i = (int64_t)r0 + t;
+                const TV own[1] = {LD::ld(src + i)};
+                const TA av[1] = {s_acc[t]};
+                e.template elem<TV, TA, 1>(c, i, 0, 1, own, av, __ldg(deg + i), dst, dot);
+            }
+            __syncthreads();   // s_acc aliases the reduction scratch
         } else {
             // heavy sub-items (long rows, chunks of split rows), one warp each
             for (int64_t si = blk.i0 + warp; si < blk.i1; si += NWARP) {
