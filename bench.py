@@ -544,7 +544,11 @@ def main():
     peaks, peak_src = measured_peaks()
     peak = float(peaks["hbm_gbs"])
     achieved = (spmv_bytes / n_spmv) / (spmv_ms / n_spmv / 1e3) / 1e9 if n_spmv else None
-    traffic = ncu_traffic()
+    folded = bool(tuning and tuning.get("fold_direction"))
+    # the committed ncu traffic was taken on the three-kernel form's SpMV
+    traffic = None if folded else ncu_traffic()
+    kernel_name = ("k_spmm<double,double,double,1,EpiLapDir> (SpMV on D^-1 r, direction update folded in, p^T q)"
+                   if folded else "k_spmm<double,double,double,1,EpiLap> (Laplacian SpMV + fused p^T q)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -556,7 +560,7 @@ def main():
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "k_spmm<double,double,double,1,EpiLap> (Laplacian SpMV + fused p^T q)",
+                     "kernel": kernel_name,
                      "launches": n_spmv, "sampled": f"1 in {SPMV_SAMPLE} SpMV launches of the timed steps",
                      "avg_launch_us": 1e3 * spmv_ms / n_spmv if n_spmv else None,
                      "algorithmic_bytes_per_launch": spmv_bytes / n_spmv if n_spmv else None,
