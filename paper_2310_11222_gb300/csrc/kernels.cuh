@@ -31,9 +31,13 @@ namespace dev {
 #ifndef SPMV1_UNROLL
 #define SPMV1_UNROLL 4
 #endif
-// Gathered neighbour rows each lane group keeps in flight in the multi-RHS SpMM.
-#ifndef SPMM_UNROLL
-#define SPMM_UNROLL 4
+// Gathered neighbour rows each lane group keeps in flight in the multi-RHS SpMM
+// (FP64 rows: 2, their products already keep the FP64 pipe busy; FP32 rows: 4).
+#ifndef SPMM_UNROLL_F64
+#define SPMM_UNROLL_F64 2
+#endif
+#ifndef SPMM_UNROLL_F32
+#define SPMM_UNROLL_F32 4
 #endif
 
 // ------------------------------------------------------------------ loads/stores
@@ -923,7 +927,7 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
             // light slices [i0, i1): a warp takes one slice of G rows at a time; the
             // LPR lanes of group `gid` own its row gid, lane `sub` of the group
             // columns col0..col0+VEC-1, so a row needs no cross-lane sum; entry j of
-            // the G rows is one load of columns and of weights, SPMM_UNROLL gathered
+            // the G rows is one load of columns and of weights, SPMM_UNROLL_* gathered
             // neighbour rows are in flight, products are added in entry order
             const int gid = lane / LPR, col0 = (lane % LPR) * VEC;
             const TA *__restrict__ deg = deg_of<TA>(c);
@@ -946,7 +950,7 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
                 }
                 const int32_t *__restrict__ cp = c.sl_col + base + gid;
                 const TW *__restrict__ wp = slw + base + gid;
-                constexpr int U = SPMM_UNROLL;
+                constexpr int U = sizeof(TV) == 8 ? SPMM_UNROLL_F64 : SPMM_UNROLL_F32;
                 TA acc[VEC];
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) acc[v] = 0;
