@@ -221,7 +221,7 @@ def run_other_workload(args, nvd, synth, torch, np, local):
             tuning = G.tune(mode=nvd.MODE_MIXED, k=k)
         xt, yt = torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)
         xh, yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()
-        kw = dict(mode=nvd.MODE_MIXED, rtol=1e-4, d2_rtol=1e-8)
+        kw = dict(mode=nvd.MODE_MIXED, rtol=1e-5, d2_rtol=1e-8)
 
         def step():
             return nvd.ge_distance(G, xt, yt, **kw)
@@ -233,7 +233,7 @@ def run_other_workload(args, nvd, synth, torch, np, local):
         h2d, d2h = 2 * X.nbytes, 8 * k
         cfg = {"workload": "powerlaw: erased configuration model n=1e7, gamma 2.3 on [2, 1e4], largest "
                            "component, lognormal(0,1) FP32 weights, 128 pairs U[0,1) on 0.1% of nodes; "
-                           "FP32 block-PCG (rtol 1e-4) inside FP64 refinement to d2_rtol 1e-8",
+                           "FP32 block-PCG (rtol 1e-5) inside FP64 refinement to d2_rtol 1e-8",
                "n": g.n, "nnz": int(g.rowptr[-1]), "pairs_per_step": k, "tuning": tuning}
         unit = UNIT
         dtype = "f32+f64"
