@@ -583,8 +583,8 @@ struct SpCfg {
     static constexpr int RED = red_doubles(KT);
     static constexpr int ACC = KT == 1 ? 0 : ((KT * (int)sizeof(TA) + 15) / 16) * 16;
     // one column: the light rows' row sums (sp_span_max of them) live in the
-    // reduction scratch, their presence bits after the totals
-    static constexpr int HAS = KT == 1 ? sp_span_max() / 32 * 4 : 0;
+    // reduction scratch; their presence bits and the slice counter follow the totals
+    static constexpr int HAS = KT == 1 ? sp_span_max() / 32 * 4 + 16 : 0;
     static_assert(KT != 1 || RED * 8 >= sp_span_max() * (int)sizeof(TA), "row sums fit the scratch");
     static constexpr int SMEM = ACC + RED * 8 + ND_MAX * KT * 8 + HAS;
 };
@@ -798,7 +798,7 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
     const bool live = !Epi::NEEDS_LIVE || seg_live<1>(c, seg);
     if (live) {
         if (blk.pad == 0) {
-            // light slices [i0, i1): a warp takes one slice of 32 rows at a time, one
+            // light slices [i0, i1): a warp takes the next slice of 32 rows, one
             // row per lane; entry j of the 32 rows is one coalesced load of columns
             // and of weights, the gathers of SPMV1_UNROLL entries are in flight
             // before their products, and each lane adds its row's products in entry
@@ -808,16 +808,20 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
             // loads and stores of the own row are coalesced.
             TA *s_acc = reinterpret_cast<TA *>(red);   // [nr]; the reduction scratch is free until the end
             unsigned *s_has = reinterpret_cast<unsigned *>(tot + SpCfg<TV, TA, 1>::ND_MAX);
+            int *s_next = reinterpret_cast<int *>(s_has + sp_span_max() / 32);
             const int32_t r0 = blk.r0, nr = blk.nr;
             for (int t = threadIdx.x; t < (nr + 31) / 32; t += NT) s_has[t] = 0u;
+            if (threadIdx.x == 0) *s_next = 0;
             __syncthreads();
             const TW *__restrict__ slw = reinterpret_cast<const TW *>(c.sl_w);
             const int64_t ns = blk.i1 - blk.i0;
-            for (int64_t round = 0; round * NWARP < ns; ++round) {
-                // longest slices first; alternate rounds reverse the warp order so
-                // the warps' totals even out
-                const int64_t q = round * NWARP + ((round & 1) ? NWARP - 1 - warp : warp);
-                if (q >= ns) continue;
+            for (;;) {
+                // the next slice of the block, longest first, to whichever warp is
+                // free (the warps finish together however the lengths fall)
+                int q = 0;
+                if (lane == 0) q = atomicAdd(s_next, 1);
+                q = __shfl_sync(NVD_FULLMASK, q, 0);
+                if (q >= ns) break;
                 const int64_t sl = blk.i0 + q;
                 const int64_t base = __ldg(c.sl_base + sl);
                 const int L = (int)((__ldg(c.sl_base + sl + 1) - base) >> 5);
