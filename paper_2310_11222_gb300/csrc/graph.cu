@@ -458,9 +458,8 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     // dealt into slices.  Heavy blocks follow their segment's light blocks.
     const int T = std::max(1, target_blocks(g) * g->sp.blocks_pct / 100);
     const double target = ltot / T;
-    // block sizes in whole slices (one column: warps take slices as they free up) or
-    // whole warp rounds of slices (several columns: slices dealt round-robin)
-    const int64_t QR = KT == 1 ? (int64_t)H : (int64_t)NWARP * H;
+    // block sizes in whole slices (warps take a block's slices as they free up)
+    const int64_t QR = (int64_t)H;
     std::vector<Block> sblk;
     std::vector<int32_t> seg_sblk_off(nseg + 1, 0);
     std::vector<int64_t> sl_base(1, 0);

@@ -583,8 +583,9 @@ struct SpCfg {
     static constexpr int RED = red_doubles(KT);
     static constexpr int ACC = KT == 1 ? 0 : ((KT * (int)sizeof(TA) + 15) / 16) * 16;
     // one column: the light rows' row sums (sp_span_max of them) live in the
-    // reduction scratch; their presence bits and the slice counter follow the totals
-    static constexpr int HAS = KT == 1 ? sp_span_max() / 32 * 4 + 16 : 0;
+    // reduction scratch; their presence bits and the slice counter follow the
+    // totals (several columns: the slice counter)
+    static constexpr int HAS = KT == 1 ? sp_span_max() / 32 * 4 + 16 : 16;
     static_assert(KT != 1 || RED * 8 >= sp_span_max() * (int)sizeof(TA), "row sums fit the scratch");
     static constexpr int SMEM = ACC + RED * 8 + ND_MAX * KT * 8 + HAS;
 };
@@ -915,7 +916,7 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
     TA *s_acc = reinterpret_cast<TA *>(smem);
     double *red = reinterpret_cast<double *>(smem + C::ACC);
     double *tot = red + C::RED;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const Block blk = c.sblk[b];
     const int seg = blk.seg;
 
@@ -928,7 +929,7 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
     const bool live = !Epi::NEEDS_LIVE || seg_live<KT>(c, seg);
     if (live) {
         if (blk.pad == 0) {
-            // light slices [i0, i1): a warp takes one slice of G rows at a time; the
+            // light slices [i0, i1): a warp takes the next slice of G rows; the
             // LPR lanes of group `gid` own its row gid, lane `sub` of the group
             // columns col0..col0+VEC-1, so a row needs no cross-lane sum; entry j of
             // the G rows is one load of columns and of weights, SPMM_UNROLL_* gathered
@@ -939,9 +940,15 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
             const int64_t ns = blk.i1 - blk.i0;
             Epi e = epi;
             e.prep(c, seg, col0);
-            for (int64_t round = 0; round * NWARP < ns; ++round) {
-                const int64_t q = round * NWARP + ((round & 1) ? NWARP - 1 - warp : warp);
-                if (q >= ns) continue;
+            int *s_next = reinterpret_cast<int *>(tot + C::ND_MAX * KT);
+            if (threadIdx.x == 0) *s_next = 0;
+            __syncthreads();
+            for (;;) {
+                // the next slice of the block (longest first) to whichever warp is free
+                int q = 0;
+                if (lane == 0) q = atomicAdd(s_next, 1);
+                q = __shfl_sync(NVD_FULLMASK, q, 0);
+                if (q >= ns) break;
                 const int64_t sl = blk.i0 + q;
                 const int64_t base = __ldg(c.sl_base + sl);
                 const int L = (int)((__ldg(c.sl_base + sl + 1) - base) / G);
