@@ -182,22 +182,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(g, X, Y, budget_s=12.0, max_pairs=8):
+def cpu_baseline(g, X, Y, budget_s=12.0, max_solves=200):
     """The oracle (plain FP64 CPU Jacobi-PCG, oracle/pcg.c) on this host's cores over a
-    bounded sample of the same pairs: returns (distances/s, threads, pairs, seconds, d2)."""
+    bounded sample of the same pairs (the step's pairs in turn, repeated until about
+    budget_s of CPU work): returns (distances/s, threads, solves, seconds, d2 of the
+    first pass over the pairs)."""
     from oracle import cg as ocg
     ocg.build()
     threads = ocg.default_threads()
+    k = X.shape[0]
     t0 = time.perf_counter()
     d2s = []
-    for j in range(max_pairs):
+    solves = 0
+    while solves < max_solves:
+        j = solves % k
         d2, it, rr = ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X[j:j + 1], Y[j:j + 1], rtol=RTOL,
                                   threads=threads)
-        d2s.append(float(d2[0]))
-        if time.perf_counter() - t0 >= budget_s:
+        if solves < k:
+            d2s.append(float(d2[0]))
+        solves += 1
+        if time.perf_counter() - t0 >= budget_s and solves >= min(k, max_solves):
             break
     dt = time.perf_counter() - t0
-    return len(d2s) / dt, threads, len(d2s), dt, d2s
+    return solves / dt, threads, solves, dt, d2s
 
 
 def run_other_workload(args, nvd, synth, torch, np, local):
@@ -569,10 +576,11 @@ def main():
                    "spmv_ms_per_step_est": spmv_ms * SPMV_SAMPLE / args.steps, "check_every": CHECK_EVERY},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, th, npairs, dt, d2_or = cpu_baseline(g, X, Y)
+        v, th, nsolves, dt, d2_or = cpu_baseline(g, X, Y)
+        npairs = len(d2_or)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
-                                "sample": f"first {npairs} of the step's 8 pairs ({dt:.1f} s), oracle "
-                                          f"FP64 Jacobi-PCG (oracle/pcg.c) at rtol 1e-10"}
+                                "sample": f"{nsolves} solves cycling over the step's {npairs} pairs ({dt:.1f} s), "
+                                          f"oracle FP64 Jacobi-PCG (oracle/pcg.c) at rtol 1e-10"}
         got = d2_last.cpu().numpy()[:npairs]
         line["max_rel_err_vs_oracle"] = float(np.max(np.abs(got - d2_or) / np.abs(d2_or)))
         line["max_rel_err_e2e_vs_oracle"] = float(np.max(np.abs(d2_host.numpy()[:npairs] - d2_or)

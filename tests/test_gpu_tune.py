@@ -60,6 +60,9 @@ def test_every_setting_matches_oracle(nvd, hub_graph, row_max_pct, blocks_pct):
             assert rel(d2.cpu().numpy(), want) < 1e-8, (kt, fold, row_max_pct, blocks_pct)
     d2 = nvd.ge_distance(G, on(X), on(Y), mode=nvd.MODE_FP32, rtol=1e-7, kt=32)
     assert rel(d2.cpu().numpy(), want) < 1e-4
+    d2 = nvd.ge_distance(G, on(X), on(Y), mode=nvd.MODE_MIXED, rtol=1e-5, d2_rtol=1e-10, kt=16,
+                         fold_direction=True)
+    assert rel(d2.cpu().numpy(), want) < 1e-8
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
