@@ -382,6 +382,61 @@ def run_other_workload(args, nvd, synth, torch, np, local):
     return 0
 
 
+def run_sweep(args, nvd, synth, torch, np, local):
+    """The paper's synthetic experiments (Section 4.2) on this GPU: time of one GE
+    evaluation (one pair, FP64 PCG to relative residual 1e-10, single right-hand side,
+    graph tuned beforehand) against |V| at mean degree 8 (size) or against the mean
+    degree at |V| = 10^4 (density), for ER, BA, WS and SBM graphs with the same number
+    of edges.  Ten runs per point; runs longer than twice the mean are dropped (the
+    paper's rule).  Prints one JSON line per point and one summary line with the
+    fitted exponent of time against |V| (size sweep, |V| >= 10^4)."""
+    dev = torch.device("cuda", local)
+    if args.sweep == "size":
+        points = [(n, 8.0) for n in (1000, 10000, 100000, 1000000)]
+    else:
+        points = [(10000, float(k)) for k in (1, 2, 4, 8, 16, 32, 64)]
+    rows = []
+    for model in ("er", "ba", "ws", "sbm"):
+        for n, kdeg in points:
+            if model in ("ba", "ws") and kdeg < 2:
+                continue
+            g = synth.sweep_graph(model, n, kdeg, seed=n + int(kdeg))
+            X, Y = synth.sparse_uniform_pairs(g.n, 1, 0.10, 5000 + n)
+            G = nvd.Graph.from_csr(g)
+            G.tune(mode=nvd.MODE_FP64, k=1, single_rhs=True)
+            xt, yt = torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)
+            for _ in range(3):
+                nvd.ge_distance(G, xt, yt, rtol=RTOL, single_rhs=True)
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(10):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                d2, st = nvd.ge_distance(G, xt, yt, rtol=RTOL, single_rhs=True, return_stats=True)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            mean = sum(times) / len(times)
+            kept = [t for t in times if t <= 2 * mean]
+            row = {"sweep": args.sweep, "model": model, "n": g.n, "mean_degree": kdeg,
+                   "nnz": int(g.rowptr[-1]), "ms_mean": sum(kept) / len(kept),
+                   "ms_median": statistics.median(times), "iters": st[0]["iters"],
+                   "d2": float(d2[0])}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            del G
+    if args.sweep == "size":
+        fits = {}
+        for model in ("er", "ba", "ws", "sbm"):
+            pts = [(r["n"], r["ms_mean"]) for r in rows if r["model"] == model and r["n"] >= 10000]
+            if len(pts) >= 2:
+                lx = np.log([p[0] for p in pts])
+                ly = np.log([p[1] for p in pts])
+                fits[model] = float(np.polyfit(lx, ly, 1)[0])
+        print(json.dumps({"sweep": "size", "exponent_time_vs_V": fits}), flush=True)
+    return 0
+
+
 def run_reference(args):
     """Reference arm: the oracle timed as it stands on the host cores."""
     rank, world, _ = env_rank()
@@ -430,6 +485,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="default work decomposition (no autotuning)")
     ap.add_argument("--workload", choices=["er_large", "powerlaw", "batched", "grad"], default="er_large",
                     help="er_large (default) is the bench line; the others measure the method's other workloads")
+    ap.add_argument("--sweep", choices=["size", "density"], default=None,
+                    help="the paper's synthetic runtime sweeps (one GE per point) instead of the bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -454,6 +511,8 @@ def main():
     import paper_2310_11222_gb300 as nvd
     import synth
     nvd.load_library()
+    if args.sweep:
+        return run_sweep(args, nvd, synth, torch, np, local)
     if args.workload != "er_large":
         if world > 1:
             raise SystemExit("--workload other than er_large runs on one GPU")

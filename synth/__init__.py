@@ -18,7 +18,7 @@ from .graphs import (CSRGraph, erdos_renyi_gnm, barabasi_albert, watts_strogatz,
                      random_tree, random_gnp_small)
 from .vectors import sparse_uniform_pairs, diffuse_uniform_pairs, indicator_pairs
 from .workloads import (workload_ba_small, workload_er_large, workload_batched,
-                        workload_powerlaw, workload_grad, WORKLOADS)
+                        workload_powerlaw, workload_grad, sweep_graph, WORKLOADS)
 
 __all__ = [
     "CSRGraph", "erdos_renyi_gnm", "barabasi_albert", "watts_strogatz",
@@ -26,5 +26,5 @@ __all__ = [
     "csr_from_edges", "disjoint_union", "path_graph", "cycle_graph", "complete_graph",
     "star_graph", "random_tree", "random_gnp_small", "sparse_uniform_pairs",
     "diffuse_uniform_pairs", "indicator_pairs", "workload_ba_small", "workload_er_large",
-    "workload_batched", "workload_powerlaw", "workload_grad", "WORKLOADS",
+    "workload_batched", "workload_powerlaw", "workload_grad", "sweep_graph", "WORKLOADS",
 ]

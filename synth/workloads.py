@@ -28,7 +28,7 @@ import numpy as np
 
 from .graphs import (CSRGraph, barabasi_albert, configuration_model_powerlaw,
                      csr_from_edges, disjoint_union, erdos_renyi_gnm, largest_component,
-                     watts_strogatz)
+                     stochastic_block_model, watts_strogatz)
 from .vectors import diffuse_uniform_pairs, indicator_pairs, sparse_uniform_pairs
 
 
@@ -158,3 +158,32 @@ WORKLOADS = {
     "powerlaw": workload_powerlaw,
     "grad": workload_grad,
 }
+
+
+def sweep_graph(model: str, n: int, mean_degree: float, seed: int) -> CSRGraph:
+    """Unit-weight graph of the size and density sweeps (the paper's synthetic models,
+    compared at the same number of edges n * mean_degree / 2):
+      er   G(n, m) with m = n * mean_degree / 2;
+      ba   Barabasi-Albert with mean_degree / 2 edges per new node (at least 1);
+      ws   Watts-Strogatz ring with mean_degree neighbours (even, at least 2), p = 0.1;
+      sbm  10 equal groups, 80% of a node's expected edges inside its group.
+    The whole graph is kept (components included)."""
+    rng = np.random.default_rng([4000, seed])
+    if model == "er":
+        m = max(1, int(round(n * mean_degree / 2)))
+        eu, ev = erdos_renyi_gnm(n, m, rng)
+    elif model == "ba":
+        eu, ev = barabasi_albert(n, max(1, int(round(mean_degree / 2))), rng)
+    elif model == "ws":
+        k = max(2, 2 * int(round(mean_degree / 2)))
+        eu, ev = watts_strogatz(n, k, 0.1, rng)
+    elif model == "sbm":
+        groups = 10
+        size = n // groups
+        sizes = [size] * (groups - 1) + [n - size * (groups - 1)]
+        p_in = min(1.0, 0.8 * mean_degree / max(size - 1, 1))
+        p_out = min(1.0, 0.2 * mean_degree / max(n - size, 1))
+        _, eu, ev = stochastic_block_model(sizes, p_in, p_out, rng)
+    else:
+        raise ValueError(model)
+    return csr_from_edges(n, eu, ev, np.ones(len(eu)), name=f"{model}_{n}_{mean_degree}")

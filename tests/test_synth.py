@@ -1,5 +1,6 @@
 """Host-side checks of the seeded input generators (shapes, counts, structure)."""
 import numpy as np
+import pytest
 import scipy.sparse as sp
 import scipy.sparse.csgraph as csg
 
@@ -79,3 +80,20 @@ def test_sbm():
     assert n == 150 and np.all(eu < ev)
     same = (eu // 50 == ev // 50) & (eu < 100) & (ev < 100)
     assert same.sum() > 0
+
+
+@pytest.mark.parametrize("model", ["er", "ba", "ws", "sbm"])
+def test_sweep_graphs_match_edge_counts(model):
+    """The sweep models are compared at the same number of edges, n * mean_degree / 2."""
+    for n, k in [(2000, 8.0), (3000, 4.0)]:
+        g = synth.sweep_graph(model, n, k, seed=1)
+        assert g.n == n
+        nnz = int(g.rowptr[-1])
+        assert abs(nnz / n - k) <= 0.1 * k, (model, n, k, nnz / n)
+        # symmetric, no self-loops, sorted rows
+        rows = np.repeat(np.arange(n), np.diff(g.rowptr))
+        assert np.all(rows != g.colidx)
+        fwd = set(zip(rows.tolist(), g.colidx.tolist()))
+        assert all((v, u) in fwd for u, v in list(fwd)[:2000])
+    assert synth.sweep_graph(model, 2000, 8.0, seed=3).structure_hash() == \
+        synth.sweep_graph(model, 2000, 8.0, seed=3).structure_hash()
