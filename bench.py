@@ -210,8 +210,9 @@ def cpu_baseline(g, X, Y, budget_s=12.0, max_solves=200):
 def run_other_workload(args, nvd, synth, torch, np, local):
     """Measurement of the other workloads of the method (not the default bench line):
     the power-law precision workload (MIXED), the 64-graph batched workload (one
-    persistent graph-captured launch) and the differentiation workload (forward +
-    adjoint backward).  Same JSON fields as the default line."""
+    persistent graph-captured launch), the differentiation workload (forward +
+    adjoint backward) and effective resistances on node-id pairs.  Same JSON fields
+    as the default line."""
     from oracle import cg as ocg
     dev = torch.device("cuda", local)
     name = args.workload
@@ -327,6 +328,37 @@ def run_other_workload(args, nvd, synth, torch, np, local):
             t0 = time.perf_counter()
             ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), X[:1], Y[:1], rtol=RTOL, return_z=True)
             return 1.0 / (time.perf_counter() - t0), "1 pair forward (z), FP64 oracle CG at rtol 1e-10"
+    elif name == "resistance":
+        wl = synth.workload_er_large()
+        g = wl.graph
+        k = 256
+        rng = np.random.default_rng(2024)
+        U = rng.integers(0, g.n, k).astype(np.int32)
+        V = ((U + 1 + rng.integers(0, g.n - 1, k)) % g.n).astype(np.int32)
+        G = nvd.Graph.from_csr(g)
+        if not args.no_tune:
+            tuning = G.tune(mode=nvd.MODE_FP64, k=k)
+
+        def step():
+            return nvd.effective_resistance(G, U, V, rtol=RTOL)
+        step_e2e = step                      # ids and results are host arrays in the call itself
+        h2d, d2h = 2 * 4 * k, 8 * k
+        cfg = {"workload": "resistance: effective resistance R(u,v) of 256 seeded node pairs on the ER graph "
+                           "(n=1e6 generated, largest component, mean degree 10, U[0.5,2] FP64 weights); "
+                           "right-hand sides e_u - e_v built on the device from the ids, FP64 block-PCG to "
+                           "rtol 1e-10; host ids in, host results out inside the timed call",
+               "n": g.n, "nnz": int(g.rowptr[-1]), "pairs_per_step": k, "tuning": tuning}
+        unit = "resistances/s"
+        dtype = "f64"
+
+        def oracle_sample():
+            x = np.zeros((1, g.n))
+            y = np.zeros((1, g.n))
+            x[0, U[0]] = 1.0
+            y[0, V[0]] = 1.0
+            t0 = time.perf_counter()
+            ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), x, y, rtol=RTOL)
+            return 1.0 / (time.perf_counter() - t0), "1 node pair (indicator vectors), FP64 oracle CG at rtol 1e-10"
     else:
         raise SystemExit(f"unknown workload {name}")
 
@@ -483,7 +515,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS comparison runs")
     ap.add_argument("--no-tune", action="store_true", help="default work decomposition (no autotuning)")
-    ap.add_argument("--workload", choices=["er_large", "powerlaw", "batched", "grad"], default="er_large",
+    ap.add_argument("--workload", choices=["er_large", "powerlaw", "batched", "grad", "resistance"],
+                    default="er_large",
                     help="er_large (default) is the bench line; the others measure the method's other workloads")
     ap.add_argument("--sweep", choices=["size", "density"], default=None,
                     help="the paper's synthetic runtime sweeps (one GE per point) instead of the bench line")

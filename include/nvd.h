@@ -218,6 +218,28 @@ int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int3
                     nvd_solve_stats *stats, nvd_stream_t stream);
 
 /*
+ * nvd_effective_resistance -- R(u_j, v_j) = (e_u - e_v)^T L^+ (e_u - e_v) for j < k:
+ * the GE distance (Section 3.1) of two indicator vectors, which on a graph with
+ * conductances w is the effective resistance between the two nodes (the
+ * L^+ quadratic forms of Section 2.1).  Solved like nvd_ge_distance, with the
+ * right-hand sides built on the device from the ids (no [k][n] input).
+ *
+ *   u, v    [k] host int32 node ids in [0, n).
+ *   r_out   [k] host doubles: R for u, v in one component; 0 for u = v; +inf
+ *           for u != v in different components (or an isolated node), which
+ *           are not solved.
+ *   stats   optional [k] host array (iters 0 for pairs that were not solved).
+ * opts as for nvd_ge_distance; NVD_SOLVE_D2_DEVICE and NVD_SOLVE_HOST_INPUTS are
+ * invalid here.  Synchronous.
+ * Errors: NVD_ERR_INVALID_ARG (NULL pointer, k < 0, an id outside [0, n), bad
+ * opts), NVD_ERR_NOT_CONVERGED / NVD_ERR_NUMERIC (every output still written),
+ * NVD_ERR_OOM, NVD_ERR_CUDA.
+ */
+int nvd_effective_resistance(nvd_graph_t g, int32_t k, const int32_t *u, const int32_t *v,
+                             const nvd_solve_opts *opts, double *r_out, nvd_solve_stats *stats,
+                             nvd_stream_t stream);
+
+/*
  * nvd_ge_distance_batched -- many graphs in one solve: the G graphs are treated as
  * the diagonal blocks of one block-diagonal Laplacian and every (graph, pair)
  * keeps its own CG scalars and convergence test, so the result equals G

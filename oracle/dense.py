@@ -10,6 +10,8 @@
 * ``ge_d2_grounded``       the same number by an independent route: per component,
                            ground one node, Cholesky-solve the reduced system.
 * ``ge_grad_dense``        gradients of d^2 from z = L^+ delta.
+* ``effective_resistance`` R(u, v) on node-id pairs (indicator vectors), +inf
+                           across components.
 
 Parity is pinned by closed forms (effective resistances of paths, cycles, trees,
 stars and complete graphs), Foster's theorem, invariants and the agreement of the
@@ -133,6 +135,25 @@ def ge_d2_grounded(n, rowptr, colidx, w, X, Y):
     Dr = D[:, keep]
     Z = sla.cho_solve(cf, Dr.T).T
     return np.einsum("ki,ki->k", Dr, Z)
+
+
+def effective_resistance(n, rowptr, colidx, w, U, V):
+    """R(u, v) = (e_u - e_v)^T L^+ (e_u - e_v) for node-id pairs (the GE equation of
+    Section 3.1 on indicator vectors), from the dense L^+ of each component.  With
+    no path between u != v the resistance is infinite (no current flows); u = v
+    gives 0."""
+    L = laplacian_dense(n, rowptr, colidx, w)
+    lab, c = components(n, rowptr, colidx)
+    Lp = pinv_laplacian(L, c)
+    out = np.empty(len(U))
+    for t, (u, v) in enumerate(zip(np.asarray(U, np.int64), np.asarray(V, np.int64))):
+        if u == v:
+            out[t] = 0.0
+        elif lab[u] != lab[v]:
+            out[t] = np.inf
+        else:
+            out[t] = Lp[u, u] + Lp[v, v] - 2.0 * Lp[u, v]
+    return out
 
 
 def ge_z_dense(n, rowptr, colidx, w, X, Y):

@@ -22,7 +22,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "Graph", "SolveOpts", "SolveStats", "ge_distance", "ge_distance_batched", "ge_grad",
+    "Graph", "SolveOpts", "SolveStats", "ge_distance", "effective_resistance", "ge_distance_batched", "ge_grad",
     "laplacian_apply", "GEDistance", "ge_distance_autograd", "profile_enable", "profile_read",
     "library_path", "load_library", "NvdError", "MODE_FP64", "MODE_FP32", "MODE_MIXED",
 ]
@@ -100,6 +100,9 @@ _SIGS = {
     "nvd_ge_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
+    "nvd_effective_resistance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.POINTER(SolveOpts), ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
     "nvd_laplacian_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.c_void_p]),
     "nvd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -333,6 +336,36 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
         out.append([{"iters": s.iters, "refine_steps": s.refine_steps, "rel_resid": s.rel_resid,
                      "status": s.status} for s in stats[:k]])
     return out[0] if len(out) == 1 else tuple(out)
+
+
+def effective_resistance(graph: Graph, u, v, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
+                         d2_rtol: float = 1e-8, max_iter: int = 10000, kt: int = 0, persistent: bool = False,
+                         return_stats: bool = False, allow_not_converged: bool = False):
+    """Effective resistances R(u_j, v_j) = (e_u - e_v)^T L^+ (e_u - e_v) for node-id
+    sequences u, v of equal length: 0 where u = v, inf across components.
+    Returns a float64 numpy array."""
+    lib = load_library()
+    U = np.ascontiguousarray(np.atleast_1d(np.asarray(u)), dtype=np.int32)
+    V = np.ascontiguousarray(np.atleast_1d(np.asarray(v)), dtype=np.int32)
+    if U.shape != V.shape or U.ndim != 1:
+        raise ValueError("u and v must be 1-D sequences of equal length")
+    k = U.shape[0]
+    o = default_opts(mode, d2_rtol=d2_rtol, max_iter=max_iter, kt=kt)
+    if rtol is not None:
+        o.rtol = rtol
+    if persistent:
+        o.flags |= SOLVE_PERSISTENT
+    r = np.empty(k, np.float64)
+    stats = (SolveStats * max(k, 1))()
+    torch = _torch()
+    with torch.cuda.device(graph.device):
+        rc = lib.nvd_effective_resistance(graph.handle, k, U.ctypes.data, V.ctypes.data, ctypes.byref(o),
+                                          r.ctypes.data, stats, _stream_ptr(graph.device))
+    _check(rc, "nvd_effective_resistance", allow=(0, 6) if allow_not_converged else (0,))
+    if return_stats:
+        return r, [{"iters": s.iters, "refine_steps": s.refine_steps, "rel_resid": s.rel_resid,
+                    "status": s.status} for s in stats[:k]]
+    return r
 
 
 def ge_distance_batched(graphs: Sequence[Graph], xs, ys, *, mode: int = MODE_FP32,

@@ -73,7 +73,7 @@ struct Owner {
     int64_t base, ld;
     int32_t kc;        // valid columns of this tile (pairs beyond k are padding)
     int32_t seg0, seg1;
-    int32_t pad;
+    int32_t idx;       // 1: x, y are int32 node ids, column j is e_x[j] - e_y[j]
 };
 
 // Everything a work kernel needs, passed by value.  Pointers whose element type

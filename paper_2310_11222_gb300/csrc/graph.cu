@@ -862,6 +862,10 @@ static int graph_create_impl(nvd_graph_t *out, int64_t n, int64_t nnz, const int
         }
     }
     g->nseg = (int32_t)g->h_seg_begin.size();
+    g->h_seg_of.assign(n, -1);
+    for (int32_t sg = 0; sg < g->nseg; ++sg)
+        for (int64_t i = g->h_seg_begin[sg]; i < g->h_seg_end[sg]; ++i)
+            g->h_seg_of[perm.empty() ? i : perm[i]] = sg;
     const size_t ns = std::max<size_t>(g->h_seg_begin.size(), 1);
     NVD_TRY(g->seg_begin.alloc(ns * 8));
     NVD_TRY(g->seg_end.alloc(ns * 8));

@@ -92,6 +92,7 @@ struct nvd_graph_s {
     int32_t ncomp = 0, nseg = 0;
     int64_t n_singleton = 0;
     std::vector<int64_t> h_rowptr, h_seg_begin, h_seg_end;
+    std::vector<int32_t> h_seg_of;  // user node -> its segment (-1: isolated node)
     nvd::DevBuf seg_begin, seg_end, seg_owner;
     nvd::SpParams sp;            // parameters of plans built from now on (nvd_graph_tune)
     int32_t tuned_kt[3] = {0, 0, 0};          // per solve mode: tile width chosen by the tuner (0 = none)

@@ -7,6 +7,7 @@
 // iteration, each (component, pair) keeping its own CG scalars.
 #include <algorithm>
 #include <cstring>
+#include <limits>
 #include <vector>
 
 #include "dispatch.h"
@@ -77,9 +78,12 @@ int check_opts(const nvd_solve_opts &o) {
     return NVD_OK;
 }
 
+// idx: x, y are [k] device int32 node ids (indicator pairs e_x - e_y); the caller
+// has checked them; host inputs and device d^2 are not used (z_out, if given, is
+// [k][n] of xdt).
 int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdt,
                   const nvd_solve_opts *opts, double *d2_out, void *z_out, nvd_solve_stats *stats,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool idx = false) {
     if (!g || k < 0 || (xdt != NVD_F32 && xdt != NVD_F64)) {
         set_error("nvd_ge_distance: invalid argument");
         return NVD_ERR_INVALID_ARG;
@@ -193,6 +197,11 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
             io.x = sx[t & 1];
             io.y = sy[t & 1];
             io.z = sz;
+        } else if (idx) {
+            io.x = (const int32_t *)x + c0;
+            io.y = (const int32_t *)y + c0;
+            io.z = z_out ? (char *)z_out + off : nullptr;
+            io.idx = 1;
         } else {
             io.x = (const char *)x + off;
             io.y = (const char *)y + off;
@@ -201,7 +210,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         if (io.z && g->n_singleton > 0)
             NVD_TRY_CUDA(cudaMemsetAsync(io.z, 0, (size_t)kc * g->n * xsz, s));
         // the tile's single owner: every segment of the graph, kc valid columns
-        c.own0 = Owner{io.x, io.y, io.z, 0, g->n, kc, 0, g->nseg, 0};
+        c.own0 = Owner{io.x, io.y, io.z, 0, g->n, kc, 0, g->nseg, io.idx};
         c.owners = nullptr;
         c.n_owner = 1;
         c.rtol2 = o.rtol * o.rtol;
@@ -288,6 +297,70 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     return overall;
 }
 
+// Effective resistance R(u, v) = (e_u - e_v)^T L^+ (e_u - e_v): pairs inside one
+// component go to the solve as indicator pairs (the delta kernel builds e_u - e_v
+// from the ids); u = v gives 0 and u, v in different components (or an isolated
+// node) give +inf without a solve.
+int resistance_impl(nvd_graph_t g, int32_t k, const int32_t *u, const int32_t *v, const nvd_solve_opts *opts,
+                    double *r_out, nvd_solve_stats *stats, cudaStream_t s) {
+    if (!g || k < 0) {
+        set_error("nvd_effective_resistance: invalid argument");
+        return NVD_ERR_INVALID_ARG;
+    }
+    if (k == 0) return NVD_OK;
+    if (!u || !v || !r_out) {
+        set_error("nvd_effective_resistance: u, v and r_out are required");
+        return NVD_ERR_INVALID_ARG;
+    }
+    nvd_solve_opts o;
+    if (opts) o = *opts; else nvd_solve_opts_default(&o);
+    NVD_TRY(check_opts(o));
+    if (o.flags & (NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS)) {
+        set_error("nvd_effective_resistance: NVD_SOLVE_D2_DEVICE and NVD_SOLVE_HOST_INPUTS do not apply "
+                  "(ids and results are host arrays)");
+        return NVD_ERR_INVALID_ARG;
+    }
+    std::vector<int32_t> su, sv;
+    std::vector<int32_t> where;  // solved pair -> its index in [0, k)
+    for (int32_t j = 0; j < k; ++j) {
+        if (u[j] < 0 || u[j] >= g->n || v[j] < 0 || v[j] >= g->n) {
+            set_error("nvd_effective_resistance: pair %d has a node id outside [0, %lld)", j, (long long)g->n);
+            return NVD_ERR_INVALID_ARG;
+        }
+    }
+    for (int32_t j = 0; j < k; ++j) {
+        const int32_t a = g->h_seg_of[u[j]], b = g->h_seg_of[v[j]];
+        const bool solve = u[j] != v[j] && a >= 0 && a == b;
+        r_out[j] = u[j] == v[j] ? 0.0 : std::numeric_limits<double>::infinity();
+        if (stats) stats[j] = nvd_solve_stats{0, 0, 0.0, NVD_OK, 0};
+        if (solve) {
+            su.push_back(u[j]);
+            sv.push_back(v[j]);
+            where.push_back(j);
+        }
+    }
+    const int32_t m = (int32_t)su.size();
+    if (m == 0) return NVD_OK;
+    DeviceGuard guard(g->device);
+    int st = NVD_OK;
+    int32_t *ids = (int32_t *)g->wsp("resist_ids", (size_t)2 * m * 4, &st);
+    if (st) return st;
+    NVD_TRY_CUDA(cudaMemcpyAsync(ids, su.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    NVD_TRY_CUDA(cudaMemcpyAsync(ids + m, sv.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    std::vector<double> r(m);
+    std::vector<nvd_solve_stats> sst(stats ? m : 0);
+    const int rc = distance_impl(g, m, ids, ids + m, NVD_F64, &o, r.data(), nullptr, stats ? sst.data() : nullptr,
+                                 s, true);
+    if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
+    for (int32_t i = 0; i < m; ++i) {
+        r_out[where[i]] = r[i];
+        if (stats) stats[where[i]] = sst[i];
+    }
+    if (rc != NVD_OK) set_error("nvd_effective_resistance: some pair ended with status %d (%s)", rc,
+                                nvd_status_string(rc));
+    return rc;
+}
+
 int apply_impl(nvd_graph_t g, int32_t k, const void *x, void *y, int32_t dtype, cudaStream_t s) {
     if (!g || k < 0 || (k > 0 && (!x || !y)) || (dtype != NVD_F32 && dtype != NVD_F64)) {
         set_error("nvd_laplacian_apply: invalid argument");
@@ -350,6 +423,21 @@ extern "C" int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const vo
         return NVD_ERR_OOM;
     } catch (...) {
         set_error("nvd_ge_distance: unexpected host exception");
+        return NVD_ERR_CUDA;
+    }
+}
+
+extern "C" int nvd_effective_resistance(nvd_graph_t g, int32_t k, const int32_t *u, const int32_t *v,
+                                        const nvd_solve_opts *opts, double *r_out, nvd_solve_stats *stats,
+                                        nvd_stream_t stream) {
+    clear_error();
+    try {
+        return resistance_impl(g, k, u, v, opts, r_out, stats, (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        set_error("nvd_effective_resistance: host allocation failed");
+        return NVD_ERR_OOM;
+    } catch (...) {
+        set_error("nvd_effective_resistance: unexpected host exception");
         return NVD_ERR_CUDA;
     }
 }

@@ -287,15 +287,16 @@ int pcg_loop(const Ctx &c, TV *x, TV *r, TV *p, TV *q, TV *u, bool fold, int max
 
 struct TileIO {
     int32_t kc;           // valid pairs in this tile
-    const void *x, *y;    // device, [kc][n], offset to the tile
+    const void *x, *y;    // device, [kc][n], offset to the tile (idx: [kc] int32 node ids)
     void *z;              // device or NULL
+    int32_t idx = 0;      // 1: x, y are node ids (indicator pairs)
 };
 
 // FP64 / FP32 PCG on one tile.  Results stay in the Ctx state (d2, rr, ...).
 template <class TV, class TW, class TA, int KT, class TX>
 int tile_pcg(nvd_graph_s *g, Ctx c, SolveWs &w, const nvd_solve_opts &o, const TileIO &io,
              cudaStream_t s) {
-    c.own0 = Owner{io.x, io.y, io.z, 0, g->n, io.kc, 0, g->nseg, 0};
+    c.own0 = Owner{io.x, io.y, io.z, 0, g->n, io.kc, 0, g->nseg, io.idx};
     c.owners = nullptr;
     c.n_owner = 1;
     c.rtol2 = o.rtol * o.rtol;
@@ -334,7 +335,7 @@ template <class TWN, int KT, class TX>
 int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_solve_opts &o,
                const TileIO &io, cudaStream_t s, std::vector<int> &iters_acc,
                std::vector<double> &relres, int *steps_out, int *conv_out) {
-    c.own0 = Owner{io.x, io.y, io.z, 0, g->n, io.kc, 0, g->nseg, 0};
+    c.own0 = Owner{io.x, io.y, io.z, 0, g->n, io.kc, 0, g->nseg, io.idx};
     c.owners = nullptr;
     c.n_owner = 1;
     c.rtol2 = o.rtol * o.rtol;

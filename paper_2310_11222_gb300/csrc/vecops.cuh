@@ -70,7 +70,7 @@ struct OpFormDelta {
     FinMean fin;
     const TX *X, *Y;
     int64_t base, ld;
-    int kc;
+    int kc, idx;
     __device__ void setup(const Ctx &c, int seg, int) {
         const Owner &o = owner_of(c, seg);
         X = reinterpret_cast<const TX *>(o.x);
@@ -78,9 +78,20 @@ struct OpFormDelta {
         base = o.base;
         ld = o.ld;
         kc = o.kc;
+        idx = o.idx & 1;
     }
     __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &r) const {
         const int64_t u = (c.perm ? (int64_t)__ldg(c.perm + i) : i) - base;
+        if (idx) {
+            // node-id pairs: column j is the indicator difference e_x[j] - e_y[j]
+            const int32_t *Xi = reinterpret_cast<const int32_t *>(X), *Yi = reinterpret_cast<const int32_t *>(Y);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int j = col0 + v;
+                r.d[v] = j < kc ? (double)(u == (int64_t)__ldg(Xi + j)) - (double)(u == (int64_t)__ldg(Yi + j)) : 0.0;
+            }
+            return;
+        }
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             const int j = col0 + v;

@@ -28,7 +28,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["nvd_graph_create", "nvd_graph_destroy", "nvd_graph_info", "nvd_ge_distance",
-                 "nvd_ge_distance_batched", "nvd_ge_grad", "nvd_status_string", "nvd_laplacian_apply"]:
+                 "nvd_ge_distance_batched", "nvd_ge_grad", "nvd_status_string", "nvd_laplacian_apply",
+                 "nvd_effective_resistance"]:
         assert must in names
 
 
@@ -63,6 +64,7 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert lib.nvd_ge_distance(None, 1, None, None, 1, None, None, None, None, None) == 1
     assert lib.nvd_ge_grad(None, 1, None, 1, None, None, None, None, None) == 1
     assert lib.nvd_graph_tune(None, 0, 1, 0, None, None) == 1
+    assert lib.nvd_effective_resistance(None, 1, None, None, None, None, None, None) == 1
     assert lib.nvd_graph_set_tuning(None, 0, None) == 1
     assert lib.nvd_graph_destroy(None) == 0
     assert lib.nvd_profile_read(3, None, None, None) == 1

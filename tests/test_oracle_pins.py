@@ -161,6 +161,56 @@ def test_foster_theorem(route):
         assert float(np.sum(wts * R)) == pytest.approx(n - c, rel=1e-10)
 
 
+def _mixed_union():
+    """Weighted tree (12 nodes) + unit cycle C_9 + unit path P_6 + two isolated nodes."""
+    rng = np.random.default_rng(41)
+    pu, cv = synth.random_tree(12, rng)
+    wts = rng.uniform(0.4, 2.5, size=len(pu))
+    parts = [graph(12, pu, cv, wts), graph(9, *synth.cycle_graph(9)), graph(6, *synth.path_graph(6))]
+    g, offs = synth.disjoint_union(parts)
+    g = graph(g.n + 2, g.eu, g.ev, g.ew)                   # nodes g.n, g.n+1 stay isolated
+    return g, offs, (pu, cv, wts)
+
+
+def test_effective_resistance_on_node_pairs():
+    """The node-id form: tree path sums, cycle h(n-h)/n and path hop counts inside
+    each component, 0 on the diagonal, +inf across components and to isolated nodes."""
+    g, offs, (pu, cv, wts) = _mixed_union()
+    t0, c0, p0, iso = offs[0], offs[1], offs[2], offs[3]
+    U, V, want = [], [], []
+    for i, j in [(0, 11), (3, 7), (5, 10)]:
+        U.append(t0 + i); V.append(t0 + j); want.append(_tree_path_resistance(pu, cv, wts, i, j))
+    for h in range(1, 9):
+        U.append(c0); V.append(c0 + h); want.append(h * (9 - h) / 9)
+    U.append(p0 + 5); V.append(p0); want.append(5.0)
+    U += [c0 + 4, t0 + 2, iso, iso]; V += [c0 + 4, c0 + 1, p0 + 3, iso + 1]; want += [0.0, np.inf, np.inf, np.inf]
+    R = dense.effective_resistance(g.n, g.rowptr, g.colidx, g.w, U, V)
+    fin = np.isfinite(want)
+    assert np.array_equal(np.isinf(R), ~fin)
+    assert np.allclose(R[fin], np.asarray(want)[fin], rtol=1e-11, atol=1e-13)
+    # the same numbers from the indicator-vector route where the pair is connected
+    X = np.zeros((int(fin.sum()), g.n)); Y = np.zeros_like(X)
+    X[np.arange(len(X)), np.asarray(U)[fin]] = 1.0
+    Y[np.arange(len(Y)), np.asarray(V)[fin]] = 1.0
+    assert np.allclose(dense.ge_d2_grounded(g.n, g.rowptr, g.colidx, g.w, X, Y), R[fin], rtol=1e-11, atol=1e-13)
+
+
+def test_effective_resistance_foster_disconnected():
+    """Foster: sum over edges of w_e R(u_e, v_e) = n - c with isolated nodes counted as components."""
+    g, _, _ = _mixed_union()
+    _, c = dense.components(g.n, g.rowptr, g.colidx)
+    R = dense.effective_resistance(g.n, g.rowptr, g.colidx, g.w, g.eu, g.ev)
+    assert float(np.sum(g.ew * R)) == pytest.approx(g.n - c, rel=1e-11)
+
+
+def test_effective_resistance_pin_catches_sign_mistake(monkeypatch):
+    """A copy with L^+_uu + L^+_vv + 2 L^+_uv (wrong sign) fails the path pin."""
+    orig = dense.pinv_laplacian
+    monkeypatch.setattr(dense, "pinv_laplacian", lambda L, c: orig(L, c) * np.where(np.eye(len(L)) > 0, 1.0, -1.0))
+    g = graph(6, *synth.path_graph(6))
+    assert dense.effective_resistance(g.n, g.rowptr, g.colidx, g.w, [0], [5])[0] != pytest.approx(5.0, rel=1e-6)
+
+
 # ---------------------------------------------------------------- invariants
 
 def _ba(n=60, seed=1, weighted=True):
