@@ -211,8 +211,8 @@ def run_other_workload(args, nvd, synth, torch, np, local):
     """Measurement of the other workloads of the method (not the default bench line):
     the power-law precision workload (MIXED), the 64-graph batched workload (one
     persistent graph-captured launch), the differentiation workload (forward +
-    adjoint backward) and effective resistances on node-id pairs.  Same JSON fields
-    as the default line."""
+    adjoint backward), effective resistances on node-id pairs and the resistance
+    matrix of a node subset.  Same JSON fields as the default line."""
     from oracle import cg as ocg
     dev = torch.device("cuda", local)
     name = args.workload
@@ -359,6 +359,38 @@ def run_other_workload(args, nvd, synth, torch, np, local):
             t0 = time.perf_counter()
             ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), x, y, rtol=RTOL)
             return 1.0 / (time.perf_counter() - t0), "1 node pair (indicator vectors), FP64 oracle CG at rtol 1e-10"
+    elif name == "resistance_matrix":
+        wl = synth.workload_er_large()
+        g = wl.graph
+        s_n = 256
+        nodes = np.random.default_rng(2025).choice(g.n, s_n, replace=False).astype(np.int32)
+        k = s_n * (s_n - 1) // 2                 # distinct node pairs of the matrix
+        G = nvd.Graph.from_csr(g)
+        if not args.no_tune:
+            tuning = G.tune(mode=nvd.MODE_FP64, k=s_n - 1)
+
+        def step():
+            return nvd.resistance_matrix(G, nodes, rtol=RTOL)
+        step_e2e = step                      # ids and the matrix are host arrays in the call itself
+        h2d, d2h = 4 * s_n, 8 * s_n * s_n
+        cfg = {"workload": "resistance_matrix: effective-resistance matrix of 256 seeded nodes of the ER graph "
+                           "(n=1e6 generated, largest component, mean degree 10, U[0.5,2] FP64 weights): 255 "
+                           "FP64 block-PCG solves L z_d = e_d - e_r to rtol 1e-10, then R(a,b) from the z "
+                           "entries at the subset; value counts the 32,640 distinct pairs per matrix",
+               "n": g.n, "nnz": int(g.rowptr[-1]), "subset": s_n, "solves_per_step": s_n - 1,
+               "pairs_per_step": k, "tuning": tuning}
+        unit = "resistances/s"
+        dtype = "f64"
+
+        def oracle_sample():
+            x = np.zeros((1, g.n))
+            y = np.zeros((1, g.n))
+            x[0, nodes[1]] = 1.0
+            y[0, nodes[0]] = 1.0
+            t0 = time.perf_counter()
+            ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), x, y, rtol=RTOL)
+            return 1.0 / (time.perf_counter() - t0), ("1 node pair per oracle CG solve at rtol 1e-10 (the oracle "
+                                                       "has no subset shortcut)")
     else:
         raise SystemExit(f"unknown workload {name}")
 
@@ -515,7 +547,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS comparison runs")
     ap.add_argument("--no-tune", action="store_true", help="default work decomposition (no autotuning)")
-    ap.add_argument("--workload", choices=["er_large", "powerlaw", "batched", "grad", "resistance"],
+    ap.add_argument("--workload", choices=["er_large", "powerlaw", "batched", "grad", "resistance",
+                                           "resistance_matrix"],
                     default="er_large",
                     help="er_large (default) is the bench line; the others measure the method's other workloads")
     ap.add_argument("--sweep", choices=["size", "density"], default=None,

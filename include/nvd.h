@@ -240,6 +240,47 @@ int nvd_effective_resistance(nvd_graph_t g, int32_t k, const int32_t *u, const i
                              nvd_stream_t stream);
 
 /*
+ * nvd_resistance_matrix -- the effective-resistance matrix of a node subset,
+ * R[i][j] = R(nodes[i], nodes[j]) (the L^+ quadratic forms of Section 2.1 on
+ * indicator vectors, GE equation of Section 3.1).  Per component, one node of
+ * the subset is the reference r and each other distinct node d gets one solve
+ * z_d = L^+ (e_d - e_r); then R(a, b) = z_a[a] - z_a[b] - z_b[a] + z_b[b]
+ * (z_r = 0), so s nodes in one component cost s - 1 solves, not s(s-1)/2.
+ *
+ *   nodes   [s] host int32 node ids in [0, n); repeats allowed.
+ *   R_out   [s][s] host doubles, row-major, symmetric up to rounding: 0 where
+ *           nodes[i] = nodes[j]; +inf across components or to an isolated node.
+ *   stats   optional [s] host array: entry i describes the solve of nodes[i]
+ *           (iters 0 for reference nodes and nodes without a solve).
+ * opts as for nvd_effective_resistance.  Device memory: up to 2 GiB of z per
+ * batch of solves (columns are processed in batches of at most 2^28 / n).
+ * Synchronous.
+ * Errors: NVD_ERR_INVALID_ARG (NULL pointer, s < 0, an id outside [0, n), bad
+ * opts), NVD_ERR_NOT_CONVERGED / NVD_ERR_NUMERIC (every output still written),
+ * NVD_ERR_OOM, NVD_ERR_CUDA.
+ */
+int nvd_resistance_matrix(nvd_graph_t g, int32_t s, const int32_t *nodes, const nvd_solve_opts *opts,
+                          double *R_out, nvd_solve_stats *stats, nvd_stream_t stream);
+
+/*
+ * nvd_network_variance -- the network variance of non-negative node weights p
+ * (a distribution on the graph; the variance of distributions on graphs cited in
+ * Section 2): var = (1/2) sum_ij p_i p_j R(nodes[i], nodes[j]), R the effective
+ * resistance, from nvd_resistance_matrix on the nodes with p_i > 0.  +inf when
+ * two nodes with positive weight lie in different components.  p is not
+ * normalised (for a distribution it sums to 1).
+ *
+ *   nodes   [s] host int32 node ids in [0, n); p [s] host doubles >= 0.
+ *   var_out host double.
+ * opts as for nvd_effective_resistance.  Synchronous.
+ * Errors: NVD_ERR_INVALID_ARG (NULL pointer, s < 0, an id outside [0, n), a
+ * negative or non-finite weight, bad opts), NVD_ERR_NOT_CONVERGED /
+ * NVD_ERR_NUMERIC (var_out still written), NVD_ERR_OOM, NVD_ERR_CUDA.
+ */
+int nvd_network_variance(nvd_graph_t g, int32_t s, const int32_t *nodes, const double *p,
+                         const nvd_solve_opts *opts, double *var_out, nvd_stream_t stream);
+
+/*
  * nvd_ge_distance_batched -- many graphs in one solve: the G graphs are treated as
  * the diagonal blocks of one block-diagonal Laplacian and every (graph, pair)
  * keeps its own CG scalars and convergence test, so the result equals G

@@ -12,6 +12,7 @@
 * ``ge_grad_dense``        gradients of d^2 from z = L^+ delta.
 * ``effective_resistance`` R(u, v) on node-id pairs (indicator vectors), +inf
                            across components.
+* ``network_variance``     (1/2) sum_ij p_i p_j R(i, j) of node weights p.
 
 Parity is pinned by closed forms (effective resistances of paths, cycles, trees,
 stars and complete graphs), Foster's theorem, invariants and the agreement of the
@@ -154,6 +155,22 @@ def effective_resistance(n, rowptr, colidx, w, U, V):
         else:
             out[t] = Lp[u, u] + Lp[v, v] - 2.0 * Lp[u, v]
     return out
+
+
+def network_variance(n, rowptr, colidx, w, nodes, p):
+    """Network variance of the node weights p on the nodes ``nodes`` (a distribution
+    on the graph, as in the variance of distributions on graphs the paper cites in
+    Section 2): (1/2) sum_ij p_i p_j R(i, j), R the effective resistance; +inf when
+    mass sits on two components."""
+    nodes = np.asarray(nodes, np.int64)
+    p = np.asarray(p, np.float64)
+    a, b = np.meshgrid(nodes, nodes, indexing="ij")
+    R = effective_resistance(n, rowptr, colidx, w, a.ravel(), b.ravel()).reshape(len(nodes), -1)
+    P = np.outer(p, p)
+    mass = P > 0
+    if np.isinf(R[mass]).any():
+        return np.inf
+    return 0.5 * float(np.sum(P[mass] * R[mass]))
 
 
 def ge_z_dense(n, rowptr, colidx, w, X, Y):

@@ -22,7 +22,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "Graph", "SolveOpts", "SolveStats", "ge_distance", "effective_resistance", "ge_distance_batched", "ge_grad",
+    "Graph", "SolveOpts", "SolveStats", "ge_distance", "effective_resistance", "resistance_matrix",
+    "network_variance", "ge_distance_batched", "ge_grad",
     "laplacian_apply", "GEDistance", "ge_distance_autograd", "profile_enable", "profile_read",
     "library_path", "load_library", "NvdError", "MODE_FP64", "MODE_FP32", "MODE_MIXED",
 ]
@@ -103,6 +104,11 @@ _SIGS = {
     "nvd_effective_resistance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.POINTER(SolveOpts), ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "nvd_resistance_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.POINTER(SolveOpts), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+    "nvd_network_variance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.POINTER(SolveOpts), ctypes.c_void_p, ctypes.c_void_p]),
     "nvd_laplacian_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.c_void_p]),
     "nvd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -366,6 +372,56 @@ def effective_resistance(graph: Graph, u, v, *, mode: int = MODE_FP64, rtol: Opt
         return r, [{"iters": s.iters, "refine_steps": s.refine_steps, "rel_resid": s.rel_resid,
                     "status": s.status} for s in stats[:k]]
     return r
+
+
+def resistance_matrix(graph: Graph, nodes, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
+                      d2_rtol: float = 1e-8, max_iter: int = 10000, kt: int = 0, persistent: bool = False,
+                      return_stats: bool = False, allow_not_converged: bool = False):
+    """Effective-resistance matrix [s, s] of the node subset ``nodes`` (one solve per
+    node and component beyond the first); inf across components.  float64 numpy."""
+    lib = load_library()
+    N = np.ascontiguousarray(np.atleast_1d(np.asarray(nodes)), dtype=np.int32)
+    if N.ndim != 1:
+        raise ValueError("nodes must be a 1-D sequence")
+    s_n = N.shape[0]
+    o = default_opts(mode, d2_rtol=d2_rtol, max_iter=max_iter, kt=kt)
+    if rtol is not None:
+        o.rtol = rtol
+    if persistent:
+        o.flags |= SOLVE_PERSISTENT
+    R = np.empty((s_n, s_n), np.float64)
+    stats = (SolveStats * max(s_n, 1))()
+    torch = _torch()
+    with torch.cuda.device(graph.device):
+        rc = lib.nvd_resistance_matrix(graph.handle, s_n, N.ctypes.data, ctypes.byref(o), R.ctypes.data, stats,
+                                       _stream_ptr(graph.device))
+    _check(rc, "nvd_resistance_matrix", allow=(0, 6) if allow_not_converged else (0,))
+    if return_stats:
+        return R, [{"iters": s.iters, "refine_steps": s.refine_steps, "rel_resid": s.rel_resid,
+                    "status": s.status} for s in stats[:s_n]]
+    return R
+
+
+def network_variance(graph: Graph, nodes, p, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
+                     d2_rtol: float = 1e-8, max_iter: int = 10000, kt: int = 0,
+                     allow_not_converged: bool = False) -> float:
+    """Network variance (1/2) sum_ij p_i p_j R(nodes[i], nodes[j]) of non-negative
+    node weights p (a distribution on the graph); inf across components."""
+    lib = load_library()
+    N = np.ascontiguousarray(np.atleast_1d(np.asarray(nodes)), dtype=np.int32)
+    P = np.ascontiguousarray(np.atleast_1d(np.asarray(p)), dtype=np.float64)
+    if N.ndim != 1 or N.shape != P.shape:
+        raise ValueError("nodes and p must be 1-D sequences of equal length")
+    o = default_opts(mode, d2_rtol=d2_rtol, max_iter=max_iter, kt=kt)
+    if rtol is not None:
+        o.rtol = rtol
+    out = ctypes.c_double(0.0)
+    torch = _torch()
+    with torch.cuda.device(graph.device):
+        rc = lib.nvd_network_variance(graph.handle, N.shape[0], N.ctypes.data, P.ctypes.data, ctypes.byref(o),
+                                      ctypes.byref(out), _stream_ptr(graph.device))
+    _check(rc, "nvd_network_variance", allow=(0, 6) if allow_not_converged else (0,))
+    return out.value
 
 
 def ge_distance_batched(graphs: Sequence[Graph], xs, ys, *, mode: int = MODE_FP32,

@@ -6,8 +6,10 @@
 // processed in tiles of KT right-hand sides that share one SpMM per CG
 // iteration, each (component, pair) keeping its own CG scalars.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <limits>
+#include <unordered_map>
 #include <vector>
 
 #include "dispatch.h"
@@ -361,6 +363,176 @@ int resistance_impl(nvd_graph_t g, int32_t k, const int32_t *u, const int32_t *v
     return rc;
 }
 
+__global__ void k_gather_f64(const double *__restrict__ z, const int64_t *__restrict__ off, double *__restrict__ out,
+                             int64_t m) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = z[off[t]];
+}
+
+// Effective-resistance matrix on a node subset.  Per component, one reference node
+// r and one solve per other distinct node d: z_d = L^+ (e_d - e_r) (z_r = 0).  By
+// linearity z_a - z_b = L^+ (e_a - e_b), so
+//   R(a, b) = (e_a - e_b)^T (z_a - z_b) = z_a[a] - z_a[b] - z_b[a] + z_b[b],
+// which needs only the entries of every z at the subset's nodes of its component.
+int resistance_matrix_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, const nvd_solve_opts *opts,
+                           double *R, nvd_solve_stats *stats, cudaStream_t s) {
+    if (!g || s_n < 0) {
+        set_error("nvd_resistance_matrix: invalid argument");
+        return NVD_ERR_INVALID_ARG;
+    }
+    if (s_n == 0) return NVD_OK;
+    if (!nodes || !R) {
+        set_error("nvd_resistance_matrix: nodes and R_out are required");
+        return NVD_ERR_INVALID_ARG;
+    }
+    nvd_solve_opts o;
+    if (opts) o = *opts; else nvd_solve_opts_default(&o);
+    NVD_TRY(check_opts(o));
+    if (o.flags & (NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS)) {
+        set_error("nvd_resistance_matrix: NVD_SOLVE_D2_DEVICE and NVD_SOLVE_HOST_INPUTS do not apply "
+                  "(ids and results are host arrays)");
+        return NVD_ERR_INVALID_ARG;
+    }
+    for (int32_t i = 0; i < s_n; ++i)
+        if (nodes[i] < 0 || nodes[i] >= g->n) {
+            set_error("nvd_resistance_matrix: nodes[%d] is outside [0, %lld)", i, (long long)g->n);
+            return NVD_ERR_INVALID_ARG;
+        }
+    const double inf = std::numeric_limits<double>::infinity();
+    for (int64_t i = 0; i < (int64_t)s_n * s_n; ++i) R[i] = inf;
+    for (int32_t i = 0; i < s_n; ++i)
+        for (int32_t j = 0; j < s_n; ++j)
+            if (nodes[i] == nodes[j]) R[(int64_t)i * s_n + j] = 0.0;
+    // distinct nodes per segment, in first-seen order; the first is the reference
+    std::vector<int32_t> seg_slot(g->nseg, -1);
+    std::vector<std::vector<int32_t>> grp;   // distinct node ids
+    std::vector<int32_t> mem(s_n, -1);       // position -> member index in its group
+    std::vector<int32_t> su, sv, col_grp;
+    {
+        std::unordered_map<int32_t, int32_t> member;
+        for (int32_t i = 0; i < s_n; ++i) {
+            const int32_t sg = g->h_seg_of[nodes[i]];
+            if (sg < 0) continue;
+            if (seg_slot[sg] < 0) {
+                seg_slot[sg] = (int32_t)grp.size();
+                grp.emplace_back();
+            }
+            auto &G = grp[seg_slot[sg]];
+            auto it = member.find(nodes[i]);
+            if (it == member.end()) {
+                it = member.emplace(nodes[i], (int32_t)G.size()).first;
+                G.push_back(nodes[i]);
+            }
+            mem[i] = it->second;
+        }
+    }
+    // columns: member m >= 1 of group q solves e_{G[m]} - e_{G[0]}
+    std::vector<std::vector<int32_t>> col(grp.size());
+    for (size_t q = 0; q < grp.size(); ++q) {
+        col[q].assign(grp[q].size(), -1);
+        for (size_t m = 1; m < grp[q].size(); ++m) {
+            col[q][m] = (int32_t)su.size();
+            su.push_back(grp[q][m]);
+            sv.push_back(grp[q][0]);
+            col_grp.push_back((int32_t)q);
+        }
+    }
+    const int32_t ncol = (int32_t)su.size();
+    if (stats) for (int32_t i = 0; i < s_n; ++i) stats[i] = nvd_solve_stats{0, 0, 0.0, NVD_OK, 0};
+    if (ncol == 0) return NVD_OK;
+    DeviceGuard guard(g->device);
+    int st = NVD_OK;
+    int32_t *ids = (int32_t *)g->wsp("rmat_ids", (size_t)2 * ncol * 4, &st);
+    if (st) return st;
+    NVD_TRY_CUDA(cudaMemcpyAsync(ids, su.data(), (size_t)ncol * 4, cudaMemcpyHostToDevice, s));
+    NVD_TRY_CUDA(cudaMemcpyAsync(ids + ncol, sv.data(), (size_t)ncol * 4, cudaMemcpyHostToDevice, s));
+    // columns per solve call: z of a chunk is at most 2^28 doubles (2 GiB)
+    const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ncol, ((int64_t)1 << 28) / g->n));
+    double *zb = (double *)g->wsp("rmat_z", (size_t)chunk * g->n * 8, &st);
+    if (st) return st;
+    // zval[c] = z_c at the members of its group, in member order
+    std::vector<std::vector<double>> zval(ncol);
+    std::vector<nvd_solve_stats> cst(ncol);
+    std::vector<double> d2(chunk);
+    int overall = NVD_OK;
+    for (int32_t c0 = 0; c0 < ncol; c0 += chunk) {
+        const int32_t kc = std::min(chunk, ncol - c0);
+        const int rc = distance_impl(g, kc, ids + c0, ids + ncol + c0, NVD_F64, &o, d2.data(), zb, cst.data() + c0,
+                                     s, true);
+        if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
+        if (rc != NVD_OK && overall != NVD_ERR_NUMERIC) overall = rc;
+        std::vector<int64_t> off;
+        for (int32_t c = c0; c < c0 + kc; ++c)
+            for (int32_t v : grp[col_grp[c]]) off.push_back((int64_t)(c - c0) * g->n + v);
+        const int64_t m = (int64_t)off.size();
+        int64_t *doff = (int64_t *)g->wsp("rmat_off", (size_t)m * 8, &st);
+        double *dval = (double *)g->wsp("rmat_val", (size_t)m * 8, &st);
+        if (st) return st;
+        std::vector<double> val(m);
+        NVD_TRY_CUDA(cudaMemcpyAsync(doff, off.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+        k_gather_f64<<<(int)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, s>>>(zb, doff, dval, m);
+        note_launch();
+        NVD_TRY_CUDA(cudaGetLastError());
+        NVD_TRY_CUDA(cudaMemcpyAsync(val.data(), dval, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+        NVD_TRY_CUDA(cudaStreamSynchronize(s));
+        int64_t t = 0;
+        for (int32_t c = c0; c < c0 + kc; ++c) {
+            zval[c].assign(val.begin() + t, val.begin() + t + grp[col_grp[c]].size());
+            t += (int64_t)grp[col_grp[c]].size();
+        }
+    }
+    // Z(q, a, b) = z of member a of group q at member b (0 for the reference)
+    auto Z = [&](size_t q, size_t a, size_t b) { return a == 0 ? 0.0 : zval[col[q][a]][b]; };
+    for (int32_t i = 0; i < s_n; ++i) {
+        const int32_t sg = g->h_seg_of[nodes[i]];
+        if (sg < 0) continue;
+        const size_t q = (size_t)seg_slot[sg];
+        const size_t a = (size_t)mem[i];
+        if (stats && a > 0) stats[i] = cst[col[q][a]];
+        for (int32_t j = 0; j < s_n; ++j) {
+            if (g->h_seg_of[nodes[j]] != sg || nodes[j] == nodes[i]) continue;
+            const size_t b = (size_t)mem[j];
+            R[(int64_t)i * s_n + j] = Z(q, a, a) - Z(q, a, b) - Z(q, b, a) + Z(q, b, b);
+        }
+    }
+    if (overall != NVD_OK) set_error("nvd_resistance_matrix: some solve ended with status %d (%s)", overall,
+                                     nvd_status_string(overall));
+    return overall;
+}
+
+// Network variance of node weights p: (1/2) sum_ij p_i p_j R(i, j) over the nodes
+// with p_i > 0, from the resistance matrix of that support.
+int network_variance_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, const double *p,
+                          const nvd_solve_opts *opts, double *var_out, cudaStream_t s) {
+    if (!g || s_n < 0 || !var_out || (s_n > 0 && (!nodes || !p))) {
+        set_error("nvd_network_variance: invalid argument");
+        return NVD_ERR_INVALID_ARG;
+    }
+    std::vector<int32_t> sup;
+    std::vector<double> ps;
+    for (int32_t i = 0; i < s_n; ++i) {
+        if (!(p[i] >= 0.0) || !std::isfinite(p[i])) {
+            set_error("nvd_network_variance: p[%d] = %g is not a finite non-negative weight", i, p[i]);
+            return NVD_ERR_INVALID_ARG;
+        }
+        if (p[i] > 0.0) {
+            sup.push_back(nodes[i]);
+            ps.push_back(p[i]);
+        }
+    }
+    *var_out = 0.0;
+    const int32_t m = (int32_t)sup.size();
+    if (m == 0) return NVD_OK;
+    std::vector<double> R((size_t)m * m);
+    const int rc = resistance_matrix_impl(g, m, sup.data(), opts, R.data(), nullptr, s);
+    if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
+    double v = 0.0;
+    for (int32_t i = 0; i < m; ++i)
+        for (int32_t j = 0; j < m; ++j) v += ps[i] * ps[j] * R[(size_t)i * m + j];
+    *var_out = 0.5 * v;
+    return rc;
+}
+
 int apply_impl(nvd_graph_t g, int32_t k, const void *x, void *y, int32_t dtype, cudaStream_t s) {
     if (!g || k < 0 || (k > 0 && (!x || !y)) || (dtype != NVD_F32 && dtype != NVD_F64)) {
         set_error("nvd_laplacian_apply: invalid argument");
@@ -438,6 +610,35 @@ extern "C" int nvd_effective_resistance(nvd_graph_t g, int32_t k, const int32_t 
         return NVD_ERR_OOM;
     } catch (...) {
         set_error("nvd_effective_resistance: unexpected host exception");
+        return NVD_ERR_CUDA;
+    }
+}
+
+extern "C" int nvd_resistance_matrix(nvd_graph_t g, int32_t s_n, const int32_t *nodes,
+                                     const nvd_solve_opts *opts, double *R_out, nvd_solve_stats *stats,
+                                     nvd_stream_t stream) {
+    clear_error();
+    try {
+        return resistance_matrix_impl(g, s_n, nodes, opts, R_out, stats, (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        set_error("nvd_resistance_matrix: host allocation failed");
+        return NVD_ERR_OOM;
+    } catch (...) {
+        set_error("nvd_resistance_matrix: unexpected host exception");
+        return NVD_ERR_CUDA;
+    }
+}
+
+extern "C" int nvd_network_variance(nvd_graph_t g, int32_t s_n, const int32_t *nodes, const double *p,
+                                    const nvd_solve_opts *opts, double *var_out, nvd_stream_t stream) {
+    clear_error();
+    try {
+        return network_variance_impl(g, s_n, nodes, p, opts, var_out, (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        set_error("nvd_network_variance: host allocation failed");
+        return NVD_ERR_OOM;
+    } catch (...) {
+        set_error("nvd_network_variance: unexpected host exception");
         return NVD_ERR_CUDA;
     }
 }

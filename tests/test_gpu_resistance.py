@@ -194,3 +194,112 @@ def test_er_large_full_size_sampled(nvd):
     R, st = nvd.effective_resistance(G, U, V, rtol=1e-10, return_stats=True)
     assert rel(R, want) < 1e-8
     assert all(s["status"] == 0 for s in st)
+
+
+# ------------------------------------------------- effective-resistance matrix
+
+def oracle_matrix(g, nodes):
+    a, b = np.meshgrid(nodes, nodes, indexing="ij")
+    return dense.effective_resistance(g.n, g.rowptr, g.colidx, g.w, a.ravel(), b.ravel()).reshape(len(nodes), -1)
+
+
+def check_matrix(R, want, tol):
+    assert R.shape == want.shape
+    assert np.array_equal(np.isposinf(R), np.isposinf(want))
+    assert np.all(R[want == 0.0] == 0.0)
+    nz = np.isfinite(want) & (want > 0)
+    assert rel(R[nz], want[nz]) < tol
+
+
+@pytest.mark.parametrize("kt", [1, 16])
+def test_matrix_on_union_subset(nvd, union_case, kt):
+    """30 subset nodes drawn from every component of the shuffled union, with
+    repeats and isolated nodes, against the dense oracle entry by entry."""
+    g = union_case[0]
+    rng = np.random.default_rng(5)
+    nodes = rng.choice(g.n, 26, replace=False)
+    nodes = np.concatenate([nodes, nodes[[0, 3]], nodes[[7, 7]]])
+    rng.shuffle(nodes)
+    want = oracle_matrix(g, nodes)
+    assert np.isinf(want).any() and np.isfinite(want[want > 0]).any()
+    G = nvd.Graph.from_csr(g)
+    R, st = nvd.resistance_matrix(G, nodes, rtol=1e-12, kt=kt, return_stats=True)
+    check_matrix(R, want, 1e-8)
+    assert all(s["status"] == 0 for s in st)
+    Rp = nvd.resistance_matrix(G, nodes, rtol=1e-12, kt=kt, persistent=True)
+    check_matrix(Rp, want, 1e-8)
+
+
+def test_matrix_edge_cases(nvd, union_case):
+    g = union_case[0]
+    G = nvd.Graph.from_csr(g)
+    assert nvd.resistance_matrix(G, []).shape == (0, 0)
+    assert np.array_equal(nvd.resistance_matrix(G, [4]), np.zeros((1, 1)))
+    assert np.array_equal(nvd.resistance_matrix(G, [4, 4]), np.zeros((2, 2)))
+    for bad in ([-1, 0], [0, g.n]):
+        with pytest.raises(nvd.NvdError) as e:
+            nvd.resistance_matrix(G, bad)
+        assert e.value.status == 1
+
+
+@pytest.mark.slow
+def test_matrix_er_large_full_size(nvd):
+    """300 seeded nodes of the n = 1e6 ER graph: 299 solves, run in two batches of
+    z (268 + 31 columns at 2^28 doubles per batch).  Zero diagonal, symmetry, the
+    triangle inequality on sampled triples, 40 sampled entries against the direct
+    per-pair path and 3 against the C FP64 CG oracle."""
+    g = synth.workload_er_large().graph
+    rng = np.random.default_rng(29)
+    nodes = rng.choice(g.n, 300, replace=False)
+    G = nvd.Graph.from_csr(g)
+    R = nvd.resistance_matrix(G, nodes, rtol=1e-11)
+    assert np.all(np.diag(R) == 0.0) and np.all(np.isfinite(R))
+    off = ~np.eye(300, dtype=bool)
+    assert np.all(R[off] > 0)
+    assert np.max(np.abs(R - R.T)[off] / R[off]) < 1e-8
+    i, j, k = rng.integers(0, 300, (3, 2000))
+    assert np.all(R[i, k] <= R[i, j] + R[j, k] + 1e-9)
+    a, b = rng.integers(0, 300, (2, 40))
+    a, b = a[a != b], b[a != b]
+    direct = nvd.effective_resistance(G, nodes[a], nodes[b], rtol=1e-11)
+    assert rel(R[a, b], direct) < 1e-8
+    X = np.zeros((3, g.n)); Y = np.zeros((3, g.n))
+    X[np.arange(3), nodes[a[:3]]] = 1.0
+    Y[np.arange(3), nodes[b[:3]]] = 1.0
+    want, it, _ = ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X, Y, rtol=1e-12)
+    assert np.all(it > 0)
+    assert rel(R[a[:3], b[:3]], want) < 1e-8
+
+
+# ------------------------------------------------------------ network variance
+
+def test_network_variance(nvd):
+    """Uniform distributions on a unit cycle C_301 and on K_50 (weight 1.7) inside
+    one graph with labels shuffled: tr(L^+)/n = (n^2 - 1)/(12 n) and (n - 1)/(n^2 w);
+    random distributions on a weighted BA graph against the dense oracle; a point
+    mass gives 0 and mass on two components gives inf."""
+    cyc = synth.csr_from_edges(301, *synth.cycle_graph(301), np.ones(301))
+    kn = synth.csr_from_edges(50, *synth.complete_graph(50), np.full(50 * 49 // 2, 1.7))
+    u0, offs = synth.disjoint_union([cyc, kn])
+    rng = np.random.default_rng(8)
+    lab = rng.permutation(u0.n)
+    g = synth.csr_from_edges(u0.n, lab[u0.eu], lab[u0.ev], u0.ew)
+    G = nvd.Graph.from_csr(g)
+    v = nvd.network_variance(G, lab[np.arange(301)], np.full(301, 1 / 301), rtol=1e-12)
+    assert v == pytest.approx((301 ** 2 - 1) / (12 * 301), rel=1e-8)
+    v = nvd.network_variance(G, lab[301 + np.arange(50)], np.full(50, 1 / 50), rtol=1e-12)
+    assert v == pytest.approx(49 / (2500 * 1.7), rel=1e-8)
+    assert nvd.network_variance(G, [lab[5]], [1.0]) == 0.0
+    assert nvd.network_variance(G, [lab[5], lab[310]], [0.5, 0.5]) == np.inf
+    assert nvd.network_variance(G, [lab[5], lab[310]], [1.0, 0.0]) == 0.0
+    with pytest.raises(nvd.NvdError) as e:
+        nvd.network_variance(G, [0, 1], [0.5, -0.5])
+    assert e.value.status == 1
+    b = synth.workload_ba_small().graph
+    bw = synth.csr_from_edges(b.n, b.eu, b.ev, rng.uniform(0.5, 2.0, b.m))
+    B = nvd.Graph.from_csr(bw)
+    for t in range(3):
+        nodes = rng.choice(bw.n, 40, replace=False)
+        p = rng.dirichlet(np.ones(40))
+        want = dense.network_variance(bw.n, bw.rowptr, bw.colidx, bw.w, nodes, p)
+        assert nvd.network_variance(B, nodes, p, rtol=1e-12) == pytest.approx(want, rel=1e-8)

@@ -211,6 +211,29 @@ def test_effective_resistance_pin_catches_sign_mistake(monkeypatch):
     assert dense.effective_resistance(g.n, g.rowptr, g.colidx, g.w, [0], [5])[0] != pytest.approx(5.0, rel=1e-6)
 
 
+def test_network_variance_closed_forms():
+    """Variance of the uniform distribution is tr(L^+)/n (the sum of all effective
+    resistances is 2n tr L^+), so with the textbook Laplacian spectra: K_n with
+    weight w gives (n-1)/(n^2 w), the unit cycle C_n gives (n^2-1)/(12n).  A point
+    mass has variance 0 and two equal masses have R/4."""
+    n, wgt = 9, 1.7
+    kn = graph(n, *synth.complete_graph(n), np.full(n * (n - 1) // 2, wgt))
+    u = np.full(n, 1.0 / n)
+    assert dense.network_variance(kn.n, kn.rowptr, kn.colidx, kn.w, np.arange(n), u) == \
+        pytest.approx((n - 1) / (n * n * wgt), rel=1e-12)
+    m = 11
+    cyc = graph(m, *synth.cycle_graph(m))
+    assert dense.network_variance(cyc.n, cyc.rowptr, cyc.colidx, cyc.w, np.arange(m), np.full(m, 1.0 / m)) == \
+        pytest.approx((m * m - 1) / (12 * m), rel=1e-12)
+    pth = graph(7, *synth.path_graph(7))
+    assert dense.network_variance(pth.n, pth.rowptr, pth.colidx, pth.w, [3], [1.0]) == 0.0
+    assert dense.network_variance(pth.n, pth.rowptr, pth.colidx, pth.w, [1, 6], [0.5, 0.5]) == \
+        pytest.approx(5 / 4, rel=1e-12)
+    two = synth.disjoint_union([pth, cyc])[0]
+    assert dense.network_variance(two.n, two.rowptr, two.colidx, two.w, [0, 9], [0.5, 0.5]) == np.inf
+    assert dense.network_variance(two.n, two.rowptr, two.colidx, two.w, [0, 9], [1.0, 0.0]) == 0.0
+
+
 # ---------------------------------------------------------------- invariants
 
 def _ba(n=60, seed=1, weighted=True):
