@@ -121,13 +121,20 @@ typedef enum {
 #define NVD_SOLVE_FOLD_DIRECTION 32u /* two kernels per CG iteration: the direction update folded into
                                         an SpMV on D^-1 r (default: three, SpMV on p, x/r update,
                                         direction pass) */
+#define NVD_SOLVE_D2_STOP 128u    /* FP64/FP32: a pair also stops once its d^2 is estimated to be
+                                     within d2_rtol: step k of CG from z = 0 adds exactly
+                                     alpha_k r_k^T D^-1 r_k to delta^T z and the remaining gap is
+                                     |z* - z_k|_L^2; the gap is extrapolated from the last terms'
+                                     geometric decay (an estimate, not a bound; see the finalizer).
+                                     Not with MIXED, nvd_resistance_matrix or nvd_network_variance */
 
 typedef struct {
     int32_t mode;        /* nvd_mode */
     int32_t max_iter;    /* CG iteration limit per solve (MIXED: per inner solve) */
     double rtol;         /* FP64/FP32: stop when ||delta - L z||_2 <= rtol ||delta||_2 per pair
                             (recursive residual); MIXED: tolerance of each inner FP32 solve */
-    double d2_rtol;      /* MIXED: stop refining when the relative change of d^2 <= d2_rtol */
+    double d2_rtol;      /* MIXED: stop refining when the relative change of d^2 <= d2_rtol;
+                            with NVD_SOLVE_D2_STOP: the d^2 accuracy asked of each pair (< 1) */
     int32_t max_refine;  /* MIXED: limit on outer refinement steps */
     int32_t check_every; /* iterations between host convergence polls (host-driven loop) */
     int32_t kt;          /* right-hand sides per tile: 0 = automatic, else 1, 4, 8, 16 or 32 */

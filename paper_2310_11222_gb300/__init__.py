@@ -40,6 +40,7 @@ SOLVE_PERSISTENT = 8
 SOLVE_NO_SYNC = 16
 SOLVE_FOLD_DIRECTION = 32
 SOLVE_TEST_TIMEOUT = 64
+SOLVE_D2_STOP = 128
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_SYM_CHECK = 2
 TUNE_SINGLE_RHS = 1
@@ -284,7 +285,7 @@ class Graph:
 def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
                 d2_rtol: float = 1e-8, max_iter: int = 10000, max_refine: int = 8, kt: int = 0,
                 check_every: int = 4, single_rhs: bool = False, persistent: bool = False,
-                fold_direction: bool = False, test_timeout: bool = False,
+                fold_direction: bool = False, test_timeout: bool = False, d2_stop: bool = False,
                 return_z: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
     """Squared GE distances d^2 for the k pairs (rows) of x, y ([k, n] or [n]).
 
@@ -316,6 +317,8 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
         o.flags |= SOLVE_FOLD_DIRECTION
     if test_timeout:
         o.flags |= SOLVE_TEST_TIMEOUT
+    if d2_stop:
+        o.flags |= SOLVE_D2_STOP
     xdt = _dtype_code(X)
     stats = (SolveStats * max(k, 1))()
     if X.is_cuda:
@@ -346,7 +349,7 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
 
 def effective_resistance(graph: Graph, u, v, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
                          d2_rtol: float = 1e-8, max_iter: int = 10000, kt: int = 0, persistent: bool = False,
-                         return_stats: bool = False, allow_not_converged: bool = False):
+                         d2_stop: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
     """Effective resistances R(u_j, v_j) = (e_u - e_v)^T L^+ (e_u - e_v) for node-id
     sequences u, v of equal length: 0 where u = v, inf across components.
     Returns a float64 numpy array."""
@@ -361,6 +364,8 @@ def effective_resistance(graph: Graph, u, v, *, mode: int = MODE_FP64, rtol: Opt
         o.rtol = rtol
     if persistent:
         o.flags |= SOLVE_PERSISTENT
+    if d2_stop:
+        o.flags |= SOLVE_D2_STOP
     r = np.empty(k, np.float64)
     stats = (SolveStats * max(k, 1))()
     torch = _torch()

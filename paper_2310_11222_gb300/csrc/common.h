@@ -26,6 +26,11 @@ constexpr int sp_chunk(int KT, int szv) { return KT == 1 ? 4096 : 32768 / (KT * 
 // Rows (first to last) one single-column light SpMV block may span: its row sums
 // are staged in shared memory by row so the row epilogue runs in row order.
 constexpr int sp_span_max() { return 1024; }
+// d^2 stop: the gap estimate takes the largest of the last d2_window ratios of
+// consecutive d^2 increments (window and safety factor chosen on recorded CG
+// traces of ER, BA, WS and SBM graphs of mean degree 2..32, paths and cycles).
+constexpr int d2_window() { return 6; }
+constexpr double d2_safety() { return 0.03; }
 // Columns one lane owns (16-byte vectors where the row is that wide), lanes per
 // row, and rows per slice (one row per lane group of a warp).
 constexpr int sp_vec(int KT, int szv) { return KT * szv >= 16 ? 16 / szv : KT; }
@@ -108,10 +113,12 @@ struct Ctx {
     unsigned *counter;              // [nseg] arrival counters (self-resetting)
     // ---- per (segment, column) scalar state, [nseg][KT]
     double *rho, *rr, *rr0, *alpha, *beta, *mean, *meanx, *d2, *dz, *zr;
+    double *hs_sum, *hs_hist;       // d^2 stop: sum of alpha_k rho_k; [nseg*KT][d2_window] last terms
     int32_t *active, *iters, *status;
     int32_t *n_active;              // number of (segment, column) pairs still iterating
     int32_t *err;                   // sticky device error code (grid-barrier timeout)
     double rtol2;
+    double d2stop;                  // > 0: also stop when the estimated d^2 error <= d2stop * d^2
     int32_t max_iter;
     // ---- sources and destinations: one "owner" per user graph (one for single-graph
     //      solves, passed inline in own0; G for batched solves, in the owners table)

@@ -357,6 +357,10 @@ struct FinInit {
         c.alpha[i] = 0.0;
         c.beta[i] = 0.0;
         c.iters[i] = 0;
+        if (c.d2stop > 0.0) {
+            c.hs_sum[i] = 0.0;
+            for (int w = 0; w < d2_window(); ++w) c.hs_hist[i * d2_window() + w] = 0.0;
+        }
         const bool finite = isfinite(rr) && isfinite(rho);
         c.status[i] = (valid && !finite) ? NVD_ERR_NUMERIC : NVD_OK;
         const bool act = valid && finite && rr > 0.0 && rho > 0.0;
@@ -387,6 +391,16 @@ struct FinAlpha {
 
 // After x += alpha p, r -= alpha q: convergence test on |r|^2 <= rtol^2 |r0|^2,
 // beta = rho_new / rho.
+//
+// With c.d2stop > 0 a column also stops when its d^2 is accurate enough.  From
+// x_0 = 0, step k raises delta^T x by exactly t_k = alpha_k rho_k (rho_k =
+// r_k^T D^-1 r_k), and the remaining gap d^2 - delta^T x_k = |x* - x_k|_L^2 is the
+// sum of the terms still to come (the Hestenes-Stiefel identity behind the CG
+// error estimates of Strakos and Tichy).  The terms shrink about geometrically
+// once CG settles, so the gap is extrapolated as t_k q / (1 - q) with q the largest
+// ratio of consecutive terms over the last d2_window() steps; the column stops when
+// that is at most d2_safety() * d2stop of the sum so far and q < 0.95 (no stop
+// while the terms are not clearly shrinking).  This is an estimate, not a bound.
 struct FinBeta {
     int KT;
     __device__ void operator()(const Ctx &c, int seg, int j, const double *s) const {
@@ -396,10 +410,27 @@ struct FinBeta {
         c.iters[i] = it;
         const double rho_new = s[0], rr = s[1];
         c.rr[i] = rr;
+        bool d2_done = false;
+        if (c.d2stop > 0.0) {
+            double *h = c.hs_hist + i * d2_window();   // t_{k-1}, t_{k-2}, ...
+            const double t = c.alpha[i] * c.rho[i];
+            const double sum = c.hs_sum[i] + t;
+            c.hs_sum[i] = sum;
+            bool ok = it > d2_window() && t > 0.0;
+            double q = 0.0, nxt = t;
+            for (int w = 0; w < d2_window(); ++w) {
+                const double prev = h[w];
+                ok = ok && prev > 0.0;
+                if (prev > 0.0) q = fmax(q, nxt / prev);
+                h[w] = nxt;
+                nxt = prev;
+            }
+            d2_done = ok && q < 0.95 && t * q <= d2_safety() * c.d2stop * sum * (1.0 - q);
+        }
         int st = -1;
         if (c.status[i] == NVD_ERR_NUMERIC || !isfinite(rr) || !isfinite(rho_new))
             st = NVD_ERR_NUMERIC;
-        else if (rr <= c.rtol2 * c.rr0[i])
+        else if (rr <= c.rtol2 * c.rr0[i] || d2_done)
             st = NVD_OK;
         else if (it >= c.max_iter)
             st = NVD_ERR_NOT_CONVERGED;

@@ -69,10 +69,12 @@ int pick_kt(const nvd_graph_s *g, const nvd_solve_opts &o, int k) {
 int check_opts(const nvd_solve_opts &o) {
     const uint32_t known = NVD_SOLVE_SINGLE_RHS | NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS |
                            NVD_SOLVE_PERSISTENT | NVD_SOLVE_NO_SYNC | NVD_SOLVE_FOLD_DIRECTION |
-                           NVD_SOLVE_TEST_TIMEOUT;
+                           NVD_SOLVE_TEST_TIMEOUT | NVD_SOLVE_D2_STOP;
+    const bool d2stop = (o.flags & NVD_SOLVE_D2_STOP) != 0;
     if (o.mode < NVD_MODE_FP64 || o.mode > NVD_MODE_MIXED || !(o.rtol > 0.0) || o.max_iter < 1 ||
         o.check_every < 1 || !(o.kt == 0 || o.kt == 1 || o.kt == 4 || o.kt == 8 || o.kt == 16 || o.kt == 32) ||
-        (o.flags & ~known) || (o.mode == NVD_MODE_MIXED && (!(o.d2_rtol > 0.0) || o.max_refine < 1))) {
+        (o.flags & ~known) || (o.mode == NVD_MODE_MIXED && (!(o.d2_rtol > 0.0) || o.max_refine < 1)) ||
+        (d2stop && (o.mode == NVD_MODE_MIXED || !(o.d2_rtol > 0.0) || !(o.d2_rtol < 1.0)))) {
         set_error("nvd_solve_opts: invalid field (mode=%d rtol=%g max_iter=%d check_every=%d kt=%d flags=%u)",
                   o.mode, o.rtol, o.max_iter, o.check_every, o.kt, o.flags);
         return NVD_ERR_INVALID_ARG;
@@ -216,6 +218,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.owners = nullptr;
         c.n_owner = 1;
         c.rtol2 = o.rtol * o.rtol;
+        c.d2stop = (o.flags & NVD_SOLVE_D2_STOP) ? o.d2_rtol : 0.0;
         c.max_iter = o.max_iter;
         int steps = 0, conv = 1;
         marks[t] = prof_enabled() ? prof_mark() : 0;
@@ -388,9 +391,9 @@ int resistance_matrix_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, con
     nvd_solve_opts o;
     if (opts) o = *opts; else nvd_solve_opts_default(&o);
     NVD_TRY(check_opts(o));
-    if (o.flags & (NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS)) {
-        set_error("nvd_resistance_matrix: NVD_SOLVE_D2_DEVICE and NVD_SOLVE_HOST_INPUTS do not apply "
-                  "(ids and results are host arrays)");
+    if (o.flags & (NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS | NVD_SOLVE_D2_STOP)) {
+        set_error("nvd_resistance_matrix: NVD_SOLVE_D2_DEVICE, NVD_SOLVE_HOST_INPUTS and NVD_SOLVE_D2_STOP do "
+                  "not apply (host arrays; entries are combinations of solutions, not d^2 values)");
         return NVD_ERR_INVALID_ARG;
     }
     for (int32_t i = 0; i < s_n; ++i)

@@ -129,7 +129,7 @@ void note_launch(int64_t n = 1);
 struct SolveWs {
     double *part = nullptr;
     unsigned *counter = nullptr;
-    double *st_d = nullptr;   // 10 x [nseg][KT]
+    double *st_d = nullptr;   // (11 + d2_window) x [nseg][KT]
     int32_t *st_i = nullptr;  // 3 x [nseg][KT] + n_active + err
     ColResult *res = nullptr;
     double *hsum = nullptr;       // [n_chunks][KT] partial row sums of split rows
@@ -147,7 +147,7 @@ inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixe
     const int64_t nk = g->n * KT;
     w->part = (double *)g->wsp("part", (size_t)4 * pl->part_slots() * KT * 8 + 64, &st);
     w->counter = (unsigned *)g->wsp("counter", (size_t)nseg * 4, &st);
-    w->st_d = (double *)g->wsp("st_d", (size_t)10 * sk * 8, &st);
+    w->st_d = (double *)g->wsp("st_d", (size_t)(11 + d2_window()) * sk * 8, &st);
     w->st_i = (int32_t *)g->wsp("st_i", (size_t)(3 * sk + 8) * 4, &st);
     w->res = (ColResult *)g->wsp("res", (size_t)std::max(n_owner, 1) * KT * sizeof(ColResult), &st);
     w->hsum = (double *)g->wsp("hsum", (size_t)std::max<int64_t>(pl->n_chunks, 1) * KT * 8, &st);
@@ -167,6 +167,7 @@ inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixe
     double *d = w->st_d;
     c->rho = d; c->rr = d + sk; c->rr0 = d + 2 * sk; c->alpha = d + 3 * sk; c->beta = d + 4 * sk;
     c->mean = d + 5 * sk; c->meanx = d + 6 * sk; c->d2 = d + 7 * sk; c->dz = d + 8 * sk; c->zr = d + 9 * sk;
+    c->hs_sum = d + 10 * sk; c->hs_hist = d + 11 * sk;
     c->active = w->st_i; c->iters = w->st_i + sk; c->status = w->st_i + 2 * sk;
     c->n_active = w->st_i + 3 * sk;
     c->err = w->st_i + 3 * sk + 1;
@@ -300,6 +301,7 @@ int tile_pcg(nvd_graph_s *g, Ctx c, SolveWs &w, const nvd_solve_opts &o, const T
     c.owners = nullptr;
     c.n_owner = 1;
     c.rtol2 = o.rtol * o.rtol;
+    c.d2stop = (o.flags & NVD_SOLVE_D2_STOP) ? o.d2_rtol : 0.0;
     c.max_iter = o.max_iter;
     double *delta = w.delta;
     TV *x = (TV *)w.x, *r = (TV *)w.r, *p = (TV *)w.p, *q = (TV *)w.q;
@@ -339,6 +341,7 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
     c.owners = nullptr;
     c.n_owner = 1;
     c.rtol2 = o.rtol * o.rtol;
+    c.d2stop = 0.0;
     c.max_iter = o.max_iter;
     const float *w32 = nullptr;
     NVD_TRY(get_w32(g, &w32, s));

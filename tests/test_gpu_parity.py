@@ -317,6 +317,63 @@ def test_autograd_function(nvd):
     assert np.max(np.abs(y.grad.cpu().numpy() + gx_ref)) <= 1e-5 * np.max(np.abs(gx_ref))
 
 
+@pytest.fixture(scope="module")
+def d2stop_cases():
+    """Graphs of the four synthetic families at n = 20,000 (ER mean degree 8, BA m = 4,
+    WS k = 4, SBM mean degree 8, U[0.5, 2) weights) and the BA workload graph, each
+    with 6 pairs of 10% support and 2 indicator pairs, and the oracle's d^2 (C FP64
+    CG at relative residual 1e-13)."""
+    out = []
+    for model, kdeg in [("er", 8), ("ba", 8), ("ws", 4), ("sbm", 8)]:
+        g0 = synth.sweep_graph(model, 20000, kdeg, seed=40 + kdeg)
+        out.append(weighted(g0, 41))
+    out.append(synth.workload_ba_small().graph)
+    cases = []
+    for g in out:
+        X, Y = synth.sparse_uniform_pairs(g.n, 6, 0.10, 77)
+        lab, _ = ocg.components(g.n, g.rowptr, g.colidx)
+        big = np.nonzero(lab == np.argmax(np.bincount(lab)))[0]
+        rng = np.random.default_rng(g.n)
+        Xi, Yi = np.zeros((2, g.n)), np.zeros((2, g.n))
+        for j in range(2):
+            a, b = rng.choice(big, 2, replace=False)
+            Xi[j, a] = 1.0
+            Yi[j, b] = 1.0
+        X, Y = np.vstack([X, Xi]), np.vstack([Y, Yi])
+        want, it, _ = ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), X, Y, rtol=1e-13)
+        assert np.all(it > 0)
+        cases.append((g, X, Y, want))
+    return cases
+
+
+@pytest.mark.parametrize("kw", [dict(single_rhs=True), dict(single_rhs=True, persistent=True),
+                                dict(single_rhs=True, fold_direction=True), dict(kt=8),
+                                dict(kt=8, persistent=True, fold_direction=True)])
+def test_d2_stop_meets_its_tolerance(nvd, d2stop_cases, kw):
+    """NVD_SOLVE_D2_STOP: every pair's d^2 within d2_rtol of the oracle (1e-6 and 1e-8),
+    with fewer iterations than the residual test at rtol 1e-10 needs."""
+    for g, X, Y, want in d2stop_cases:
+        G = nvd.Graph.from_csr(g)
+        _, st_ref = nvd.ge_distance(G, on(X), on(Y), rtol=1e-10, return_stats=True, **kw)
+        for tol in (1e-6, 1e-8):
+            d2, st = nvd.ge_distance(G, on(X), on(Y), rtol=1e-14, d2_stop=True, d2_rtol=tol,
+                                     return_stats=True, **kw)
+            assert all(s["status"] == 0 for s in st)
+            assert rel(d2.cpu().numpy(), want) <= tol, (g.n, tol)
+            assert sum(s["iters"] for s in st) < sum(s["iters"] for s in st_ref)
+
+
+def test_d2_stop_fp32_and_invalid_uses(nvd, d2stop_cases):
+    g, X, Y, want = d2stop_cases[0]
+    G = nvd.Graph.from_csr(g)
+    d2 = nvd.ge_distance(G, on(X), on(Y), mode=nvd.MODE_FP32, rtol=1e-6, d2_stop=True, d2_rtol=1e-4, kt=8)
+    assert rel(d2.cpu().numpy(), want) <= 1e-4
+    for bad in (dict(mode=nvd.MODE_MIXED, d2_stop=True), dict(d2_stop=True, d2_rtol=1.0)):
+        with pytest.raises(nvd.NvdError) as e:
+            nvd.ge_distance(G, on(X), on(Y), **bad)
+        assert e.value.status == 1
+
+
 @pytest.mark.slow
 def test_er_large_full_size_single_rhs(nvd):
     """ER n = 1e6 (largest component), mean degree 10, FP64 weights, 8 pairs solved one
@@ -333,3 +390,8 @@ def test_er_large_full_size_single_rhs(nvd):
     assert all(s["status"] == 0 for s in st)
     d2b = nvd.ge_distance(G, on(X), on(Y), rtol=1e-10)          # batched RHS, same answer
     assert rel(d2b.cpu().numpy(), want) < 1e-8
+    # the accuracy the metric asks (d^2 within 1e-6) by the d^2 stop, in far fewer iterations
+    d2s, sts = nvd.ge_distance(G, on(X), on(Y), rtol=1e-14, single_rhs=True, d2_stop=True, d2_rtol=1e-6,
+                               return_stats=True)
+    assert rel(d2s.cpu().numpy(), want) <= 1e-6
+    assert max(s["iters"] for s in sts) < min(s["iters"] for s in st)
