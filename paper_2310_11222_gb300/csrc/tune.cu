@@ -182,32 +182,56 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
         }
     }
     // 2. row split, 3. light blocks per launch (each keeps the better of default and
-    //    the candidates)
+    //    the candidates; the kept setting and the candidate are re-timed back to
+    //    back, twice each, and the candidate must win by 2%: single timings differ
+    //    by a few percent from run to run)
     for (int pass = 0; pass < 2; ++pass) {
         for (int pct : {50, 200}) {
             SpParams cand = g->sp;
             (pass == 0 ? cand.row_max_pct : cand.blocks_pct) = pct;
             const SpParams keep = g->sp;
-            g->sp = cand;
-            double it = 0;
-            int rc = b.per_iter(best_kt, false, &it);
-            if (rc) return fail(rc);
+            double base = INFINITY, alt = INFINITY;
+            for (int rep = 0; rep < 2; ++rep) {
+                double it = 0;
+                g->sp = keep;
+                int rc = b.per_iter(best_kt, false, &it);
+                if (rc) return fail(rc);
+                base = std::min(base, it);
+                g->sp = cand;
+                rc = b.per_iter(best_kt, false, &it);
+                if (rc) return fail(rc);
+                alt = std::min(alt, it);
+            }
             ++ntried;
-            if (it < best_iter * 0.99) best_iter = it;
-            else g->sp = keep;
+            if (alt < base * 0.98) {
+                best_iter = alt;
+            } else {
+                g->sp = keep;
+                best_iter = std::min(best_iter, base);
+            }
         }
     }
     // 4. one persistent launch per tile (not for the mixed mode, whose outer loop
     //    runs on the host)
     int pers = 0;
     if (mode != NVD_MODE_MIXED) {
-        double it = 0;
-        const int rc = b.per_iter(best_kt, true, &it);
+        double it = 0, base = best_iter, alt = INFINITY;
+        int rc = b.per_iter(best_kt, true, &it);
         if (rc == NVD_OK) {
+            alt = it;
+            // re-time both back to back before switching (as for the steps above)
+            rc = b.per_iter(best_kt, false, &it);
+            if (rc) return fail(rc);
+            base = std::min(base, it);
+            rc = b.per_iter(best_kt, true, &it);
+            if (rc) return fail(rc);
+            alt = std::min(alt, it);
             ++ntried;
-            if (it < best_iter * 0.97) {
+            if (alt < base * 0.97) {
                 pers = 1;
-                best_iter = it;
+                best_iter = alt;
+            } else {
+                best_iter = base;
             }
         } else if (rc == NVD_ERR_UNSUPPORTED) {
             clear_error();   // does not fit one wave: host-driven only
