@@ -86,7 +86,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+           "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-ldl"]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)

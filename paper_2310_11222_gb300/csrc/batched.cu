@@ -383,6 +383,7 @@ extern "C" int nvd_ge_distance_batched(const nvd_graph_t *graphs, int32_t G, con
                                        const nvd_solve_opts *opts, double *d2_out, nvd_solve_stats *stats,
                                        nvd_stream_t stream) {
     clear_error();
+    TraceRange trace("nvd_ge_distance_batched");
     try {
         return batched_impl(graphs, G, k_per, x, y, xdtype, opts, d2_out, stats, (cudaStream_t)stream);
     } catch (const std::bad_alloc &) {

@@ -215,6 +215,7 @@ int grad_impl(nvd_graph_t g, int32_t k, const void *z, int32_t zdt, const double
 extern "C" int nvd_ge_grad(nvd_graph_t g, int32_t k, const void *z, int32_t zdtype, const double *gbar,
                            void *grad_w, void *grad_x, void *grad_y, nvd_stream_t stream) {
     clear_error();
+    TraceRange trace("nvd_ge_grad");
     try {
         return grad_impl(g, k, z, zdtype, gbar, grad_w, grad_x, grad_y, (cudaStream_t)stream);
     } catch (...) {

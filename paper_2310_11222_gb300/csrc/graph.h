@@ -8,10 +8,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.h"
 #include "nvd.h"
 
 namespace nvd {
+
+// NVTX range around a phase of a call (graph creation, plan build, one tile, one
+// refinement step, ...), for profilers that attach; without one it costs a call.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Thread-local error detail for nvd_last_error().
 void set_error(const char *fmt, ...);

@@ -93,6 +93,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         return NVD_ERR_INVALID_ARG;
     }
     if (k == 0) return NVD_OK;
+    TraceRange trace(idx ? "nvd solve (node-id pairs)" : "nvd_ge_distance");
     if (!x || !y || !d2_out) {
         set_error("nvd_ge_distance: x, y and d2_out are required");
         return NVD_ERR_INVALID_ARG;
@@ -193,6 +194,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         const int32_t t = c0 / KT;
         const int kc = std::min<int>(KT, k - c0);
         const size_t off = (size_t)c0 * g->n * xsz;
+        TraceRange trace_tile("nvd tile");
         TileIO io;
         io.kc = kc;
         if (host_in) {
@@ -441,6 +443,7 @@ int resistance_matrix_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, con
         }
     }
     const int32_t ncol = (int32_t)su.size();
+    TraceRange trace("nvd_resistance_matrix");
     if (stats) for (int32_t i = 0; i < s_n; ++i) stats[i] = nvd_solve_stats{0, 0, 0.0, NVD_OK, 0};
     if (ncol == 0) return NVD_OK;
     DeviceGuard guard(g->device);

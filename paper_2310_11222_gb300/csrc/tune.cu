@@ -310,6 +310,7 @@ extern "C" int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_
 extern "C" int nvd_graph_tune(nvd_graph_t g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_result *out,
                               nvd_stream_t stream) {
     clear_error();
+    TraceRange trace("nvd_graph_tune");
     try {
         return tune_impl(g, mode, k, flags, out, (cudaStream_t)stream);
     } catch (...) {
