@@ -374,45 +374,102 @@ __global__ void k_gather_f64(const double *__restrict__ z, const int64_t *__rest
         out[t] = z[off[t]];
 }
 
-// Effective-resistance matrix on a node subset.  Per component, one reference node
-// r and one solve per other distinct node d: z_d = L^+ (e_d - e_r) (z_r = 0).  By
-// linearity z_a - z_b = L^+ (e_a - e_b), so
+__device__ __forceinline__ double pos_inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+// R[i][j] of the subset from the gathered solution entries.  Position i has node
+// node[i], group q[i] (-1: isolated) and member a[i] of its group; member a >= 1 of
+// group q is solve column col1[q] + a - 1, whose entries at the group's members
+// start at zval[off[column]] (member order).  Z(a, b) = z_a at member b, 0 for the
+// reference member 0; R = Z(a,a) - Z(a,b) - Z(b,a) + Z(b,b).
+__global__ void k_rmat_assemble(int32_t s_n, const int32_t *__restrict__ node, const int32_t *__restrict__ q,
+                                const int32_t *__restrict__ a, const int32_t *__restrict__ col1,
+                                const int64_t *__restrict__ off, const double *__restrict__ zval,
+                                double *__restrict__ R) {
+    const int64_t tot = (int64_t)s_n * s_n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)(t / s_n), j = (int32_t)(t % s_n);
+        double r;
+        if (node[i] == node[j]) {
+            r = 0.0;
+        } else if (q[i] < 0 || q[i] != q[j]) {
+            r = pos_inf();
+        } else {
+            const int32_t ai = a[i], bj = a[j], c1 = col1[q[i]];
+            const double *za = ai ? zval + off[c1 + ai - 1] : nullptr;
+            const double *zb = bj ? zval + off[c1 + bj - 1] : nullptr;
+            const double zaa = za ? za[ai] : 0.0, zab = za ? za[bj] : 0.0;
+            const double zba = zb ? zb[ai] : 0.0, zbb = zb ? zb[bj] : 0.0;
+            r = zaa - zab - zba + zbb;
+        }
+        R[t] = r;
+    }
+}
+
+// (1/2) sum_ij p_i p_j R_ij over the pairs with p_i p_j > 0 (+inf if one of them has
+// R = inf): per-block partials in a fixed order, then one block adds them in block
+// order, so the result does not depend on scheduling.
+constexpr int QF_NT = 256;
+__device__ __forceinline__ void qf_block_sum(double v, bool inf, double *sh, double *out, int *out_inf) {
+    sh[threadIdx.x] = v;
+    const int any = __syncthreads_or(inf ? 1 : 0);
+    for (int w = QF_NT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *out = sh[0];
+        *out_inf = any;
+    }
+}
+__global__ void k_quadform_part(int32_t m, const double *__restrict__ p, const double *__restrict__ R,
+                                double *__restrict__ part, int *__restrict__ part_inf) {
+    __shared__ double sh[QF_NT];
+    const int64_t tot = (int64_t)m * m;
+    double acc = 0.0;
+    bool inf = false;
+    for (int64_t t = (int64_t)blockIdx.x * QF_NT + threadIdx.x; t < tot; t += (int64_t)gridDim.x * QF_NT) {
+        const double w = p[t / m] * p[t % m];
+        if (w > 0.0) {
+            const double r = R[t];
+            if (isinf(r)) inf = true;
+            else acc += w * r;
+        }
+    }
+    qf_block_sum(acc, inf, sh, part + blockIdx.x, part_inf + blockIdx.x);
+}
+__global__ void k_quadform_final(int32_t nb, const double *__restrict__ part, const int *__restrict__ part_inf,
+                                 double *__restrict__ out) {
+    __shared__ double sh[QF_NT];
+    __shared__ int fl;
+    double acc = 0.0;
+    bool inf = false;
+    for (int b = threadIdx.x; b < nb; b += QF_NT) {
+        acc += part[b];
+        inf = inf || part_inf[b] != 0;
+    }
+    qf_block_sum(acc, inf, sh, out, &fl);
+    if (threadIdx.x == 0) out[0] = fl ? pos_inf() : 0.5 * out[0];
+}
+
+// Effective-resistance matrix on a node subset, left on the device in R_dev
+// ([s][s]).  Per component, one reference node r and one solve per other distinct
+// node d: z_d = L^+ (e_d - e_r) (z_r = 0).  By linearity z_a - z_b = L^+ (e_a - e_b),
+// so
 //   R(a, b) = (e_a - e_b)^T (z_a - z_b) = z_a[a] - z_a[b] - z_b[a] + z_b[b],
-// which needs only the entries of every z at the subset's nodes of its component.
-int resistance_matrix_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, const nvd_solve_opts *opts,
-                           double *R, nvd_solve_stats *stats, cudaStream_t s) {
-    if (!g || s_n < 0) {
-        set_error("nvd_resistance_matrix: invalid argument");
-        return NVD_ERR_INVALID_ARG;
-    }
-    if (s_n == 0) return NVD_OK;
-    if (!nodes || !R) {
-        set_error("nvd_resistance_matrix: nodes and R_out are required");
-        return NVD_ERR_INVALID_ARG;
-    }
-    nvd_solve_opts o;
-    if (opts) o = *opts; else nvd_solve_opts_default(&o);
-    NVD_TRY(check_opts(o));
-    if (o.flags & (NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS | NVD_SOLVE_D2_STOP)) {
-        set_error("nvd_resistance_matrix: NVD_SOLVE_D2_DEVICE, NVD_SOLVE_HOST_INPUTS and NVD_SOLVE_D2_STOP do "
-                  "not apply (host arrays; entries are combinations of solutions, not d^2 values)");
-        return NVD_ERR_INVALID_ARG;
-    }
+// which needs only the entries of every z at the subset's nodes of its component:
+// they are gathered on the device after each batch of solves, and k_rmat_assemble
+// forms R (0 on repeated nodes, +inf across components).
+int resistance_matrix_core(nvd_graph_t g, int32_t s_n, const int32_t *nodes, const nvd_solve_opts &o,
+                           double *R_dev, nvd_solve_stats *stats, cudaStream_t s) {
     for (int32_t i = 0; i < s_n; ++i)
         if (nodes[i] < 0 || nodes[i] >= g->n) {
             set_error("nvd_resistance_matrix: nodes[%d] is outside [0, %lld)", i, (long long)g->n);
             return NVD_ERR_INVALID_ARG;
         }
-    const double inf = std::numeric_limits<double>::infinity();
-    for (int64_t i = 0; i < (int64_t)s_n * s_n; ++i) R[i] = inf;
-    for (int32_t i = 0; i < s_n; ++i)
-        for (int32_t j = 0; j < s_n; ++j)
-            if (nodes[i] == nodes[j]) R[(int64_t)i * s_n + j] = 0.0;
     // distinct nodes per segment, in first-seen order; the first is the reference
     std::vector<int32_t> seg_slot(g->nseg, -1);
     std::vector<std::vector<int32_t>> grp;   // distinct node ids
-    std::vector<int32_t> mem(s_n, -1);       // position -> member index in its group
-    std::vector<int32_t> su, sv, col_grp;
+    std::vector<int32_t> pos_q(s_n, -1), pos_a(s_n, 0);
     {
         std::unordered_map<int32_t, int32_t> member;
         for (int32_t i = 0; i < s_n; ++i) {
@@ -428,95 +485,145 @@ int resistance_matrix_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, con
                 it = member.emplace(nodes[i], (int32_t)G.size()).first;
                 G.push_back(nodes[i]);
             }
-            mem[i] = it->second;
+            pos_q[i] = seg_slot[sg];
+            pos_a[i] = it->second;
         }
     }
-    // columns: member m >= 1 of group q solves e_{G[m]} - e_{G[0]}
-    std::vector<std::vector<int32_t>> col(grp.size());
-    for (size_t q = 0; q < grp.size(); ++q) {
-        col[q].assign(grp[q].size(), -1);
+    // columns: member m >= 1 of group q is column col1[q] + m - 1 and solves
+    // e_{G[m]} - e_{G[0]}; its gathered entries start at col_off[column]
+    const int32_t ngrp = (int32_t)grp.size();
+    std::vector<int32_t> su, sv, col_grp, col1(std::max(ngrp, 1), 0);
+    std::vector<int64_t> col_off;
+    int64_t nval = 0;
+    for (int32_t q = 0; q < ngrp; ++q) {
+        col1[q] = (int32_t)su.size();
         for (size_t m = 1; m < grp[q].size(); ++m) {
-            col[q][m] = (int32_t)su.size();
             su.push_back(grp[q][m]);
             sv.push_back(grp[q][0]);
-            col_grp.push_back((int32_t)q);
+            col_grp.push_back(q);
+            col_off.push_back(nval);
+            nval += (int64_t)grp[q].size();
         }
     }
     const int32_t ncol = (int32_t)su.size();
     TraceRange trace("nvd_resistance_matrix");
     if (stats) for (int32_t i = 0; i < s_n; ++i) stats[i] = nvd_solve_stats{0, 0, 0.0, NVD_OK, 0};
-    if (ncol == 0) return NVD_OK;
     DeviceGuard guard(g->device);
     int st = NVD_OK;
-    int32_t *ids = (int32_t *)g->wsp("rmat_ids", (size_t)2 * ncol * 4, &st);
+    // index tables: node, q, a [s_n] | col1 [ngrp] | ids u, v [ncol]  (int32), col_off [ncol] (int64)
+    const size_t nint = (size_t)3 * s_n + col1.size() + 2 * (size_t)ncol;
+    std::vector<int32_t> hint;
+    hint.reserve(nint);
+    hint.insert(hint.end(), nodes, nodes + s_n);
+    hint.insert(hint.end(), pos_q.begin(), pos_q.end());
+    hint.insert(hint.end(), pos_a.begin(), pos_a.end());
+    hint.insert(hint.end(), col1.begin(), col1.end());
+    hint.insert(hint.end(), su.begin(), su.end());
+    hint.insert(hint.end(), sv.begin(), sv.end());
+    int32_t *dint = (int32_t *)g->wsp("rmat_int", nint * 4, &st);
+    int64_t *doff_col = (int64_t *)g->wsp("rmat_coloff", std::max<size_t>(col_off.size(), 1) * 8, &st);
+    double *zval = (double *)g->wsp("rmat_zval", (size_t)std::max<int64_t>(nval, 1) * 8, &st);
     if (st) return st;
-    NVD_TRY_CUDA(cudaMemcpyAsync(ids, su.data(), (size_t)ncol * 4, cudaMemcpyHostToDevice, s));
-    NVD_TRY_CUDA(cudaMemcpyAsync(ids + ncol, sv.data(), (size_t)ncol * 4, cudaMemcpyHostToDevice, s));
-    // columns per solve call: z of a chunk is at most 2^28 doubles (2 GiB)
-    const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ncol, ((int64_t)1 << 28) / g->n));
-    double *zb = (double *)g->wsp("rmat_z", (size_t)chunk * g->n * 8, &st);
-    if (st) return st;
-    // zval[c] = z_c at the members of its group, in member order
-    std::vector<std::vector<double>> zval(ncol);
-    std::vector<nvd_solve_stats> cst(ncol);
-    std::vector<double> d2(chunk);
+    NVD_TRY_CUDA(cudaMemcpyAsync(dint, hint.data(), nint * 4, cudaMemcpyHostToDevice, s));
+    if (ncol) NVD_TRY_CUDA(cudaMemcpyAsync(doff_col, col_off.data(), col_off.size() * 8, cudaMemcpyHostToDevice, s));
+    const int32_t *d_node = dint, *d_q = dint + s_n, *d_a = dint + 2 * s_n, *d_col1 = dint + 3 * s_n;
+    const int32_t *ids_u = d_col1 + col1.size(), *ids_v = ids_u + ncol;
     int overall = NVD_OK;
-    for (int32_t c0 = 0; c0 < ncol; c0 += chunk) {
-        const int32_t kc = std::min(chunk, ncol - c0);
-        const int rc = distance_impl(g, kc, ids + c0, ids + ncol + c0, NVD_F64, &o, d2.data(), zb, cst.data() + c0,
-                                     s, true);
-        if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
-        if (rc != NVD_OK && overall != NVD_ERR_NUMERIC) overall = rc;
-        std::vector<int64_t> off;
-        for (int32_t c = c0; c < c0 + kc; ++c)
-            for (int32_t v : grp[col_grp[c]]) off.push_back((int64_t)(c - c0) * g->n + v);
-        const int64_t m = (int64_t)off.size();
-        int64_t *doff = (int64_t *)g->wsp("rmat_off", (size_t)m * 8, &st);
-        double *dval = (double *)g->wsp("rmat_val", (size_t)m * 8, &st);
+    if (ncol > 0) {
+        // columns per solve call: z of a batch is at most 2^28 doubles (2 GiB)
+        const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ncol, ((int64_t)1 << 28) / g->n));
+        double *zb = (double *)g->wsp("rmat_z", (size_t)chunk * g->n * 8, &st);
         if (st) return st;
-        std::vector<double> val(m);
-        NVD_TRY_CUDA(cudaMemcpyAsync(doff, off.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
-        k_gather_f64<<<(int)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, s>>>(zb, doff, dval, m);
-        note_launch();
-        NVD_TRY_CUDA(cudaGetLastError());
-        NVD_TRY_CUDA(cudaMemcpyAsync(val.data(), dval, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
-        NVD_TRY_CUDA(cudaStreamSynchronize(s));
-        int64_t t = 0;
-        for (int32_t c = c0; c < c0 + kc; ++c) {
-            zval[c].assign(val.begin() + t, val.begin() + t + grp[col_grp[c]].size());
-            t += (int64_t)grp[col_grp[c]].size();
+        std::vector<nvd_solve_stats> cst(ncol);
+        std::vector<double> d2(chunk);
+        for (int32_t c0 = 0; c0 < ncol; c0 += chunk) {
+            const int32_t kc = std::min(chunk, ncol - c0);
+            const int rc = distance_impl(g, kc, ids_u + c0, ids_v + c0, NVD_F64, &o, d2.data(), zb, cst.data() + c0,
+                                         s, true);
+            if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
+            if (rc != NVD_OK && overall != NVD_ERR_NUMERIC) overall = rc;
+            // offsets into zb of this batch's entries at the members of each column's group
+            std::vector<int64_t> off;
+            off.reserve((size_t)(kc ? (c0 + kc < ncol ? col_off[c0 + kc] : nval) - col_off[c0] : 0));
+            for (int32_t c = c0; c < c0 + kc; ++c)
+                for (int32_t v : grp[col_grp[c]]) off.push_back((int64_t)(c - c0) * g->n + v);
+            const int64_t m = (int64_t)off.size();
+            int64_t *doff = (int64_t *)g->wsp("rmat_off", (size_t)m * 8, &st);
+            if (st) return st;
+            NVD_TRY_CUDA(cudaMemcpyAsync(doff, off.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+            k_gather_f64<<<(int)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, s>>>(zb, doff, zval + col_off[c0],
+                                                                                         m);
+            note_launch();
+            NVD_TRY_CUDA(cudaGetLastError());
+            // the next batch overwrites zb and the offsets
+            NVD_TRY_CUDA(cudaStreamSynchronize(s));
         }
+        if (stats)
+            for (int32_t i = 0; i < s_n; ++i)
+                if (pos_q[i] >= 0 && pos_a[i] > 0) stats[i] = cst[col1[pos_q[i]] + pos_a[i] - 1];
     }
-    // Z(q, a, b) = z of member a of group q at member b (0 for the reference)
-    auto Z = [&](size_t q, size_t a, size_t b) { return a == 0 ? 0.0 : zval[col[q][a]][b]; };
-    for (int32_t i = 0; i < s_n; ++i) {
-        const int32_t sg = g->h_seg_of[nodes[i]];
-        if (sg < 0) continue;
-        const size_t q = (size_t)seg_slot[sg];
-        const size_t a = (size_t)mem[i];
-        if (stats && a > 0) stats[i] = cst[col[q][a]];
-        for (int32_t j = 0; j < s_n; ++j) {
-            if (g->h_seg_of[nodes[j]] != sg || nodes[j] == nodes[i]) continue;
-            const size_t b = (size_t)mem[j];
-            R[(int64_t)i * s_n + j] = Z(q, a, a) - Z(q, a, b) - Z(q, b, a) + Z(q, b, b);
-        }
-    }
+    const int64_t tot = (int64_t)s_n * s_n;
+    k_rmat_assemble<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(s_n, d_node, d_q, d_a, d_col1,
+                                                                                     doff_col, zval, R_dev);
+    note_launch();
+    NVD_TRY_CUDA(cudaGetLastError());
     if (overall != NVD_OK) set_error("nvd_resistance_matrix: some solve ended with status %d (%s)", overall,
                                      nvd_status_string(overall));
     return overall;
 }
 
+int rmat_check(nvd_graph_t g, int32_t s_n, const nvd_solve_opts *opts, nvd_solve_opts *o, const char *who) {
+    if (!g || s_n < 0) {
+        set_error("%s: invalid argument", who);
+        return NVD_ERR_INVALID_ARG;
+    }
+    if (opts) *o = *opts; else nvd_solve_opts_default(o);
+    NVD_TRY(check_opts(*o));
+    if (o->flags & (NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS | NVD_SOLVE_D2_STOP)) {
+        set_error("%s: NVD_SOLVE_D2_DEVICE, NVD_SOLVE_HOST_INPUTS and NVD_SOLVE_D2_STOP do not apply (host "
+                  "arrays; entries are combinations of solutions, not d^2 values)", who);
+        return NVD_ERR_INVALID_ARG;
+    }
+    return NVD_OK;
+}
+
+int resistance_matrix_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, const nvd_solve_opts *opts,
+                           double *R, nvd_solve_stats *stats, cudaStream_t s) {
+    nvd_solve_opts o;
+    NVD_TRY(rmat_check(g, s_n, opts, &o, "nvd_resistance_matrix"));
+    if (s_n == 0) return NVD_OK;
+    if (!nodes || !R) {
+        set_error("nvd_resistance_matrix: nodes and R_out are required");
+        return NVD_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(g->device);
+    int st = NVD_OK;
+    double *R_dev = (double *)g->wsp("rmat_R", (size_t)s_n * s_n * 8, &st);
+    if (st) return st;
+    const int rc = resistance_matrix_core(g, s_n, nodes, o, R_dev, stats, s);
+    if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
+    NVD_TRY_CUDA(cudaMemcpyAsync(R, R_dev, (size_t)s_n * s_n * 8, cudaMemcpyDeviceToHost, s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
 // Network variance of node weights p: (1/2) sum_ij p_i p_j R(i, j) over the nodes
-// with p_i > 0, from the resistance matrix of that support.
+// with p_i > 0, from the resistance matrix of that support (on the device).
 int network_variance_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, const double *p,
                           const nvd_solve_opts *opts, double *var_out, cudaStream_t s) {
-    if (!g || s_n < 0 || !var_out || (s_n > 0 && (!nodes || !p))) {
+    nvd_solve_opts o;
+    NVD_TRY(rmat_check(g, s_n, opts, &o, "nvd_network_variance"));
+    if (!var_out || (s_n > 0 && (!nodes || !p))) {
         set_error("nvd_network_variance: invalid argument");
         return NVD_ERR_INVALID_ARG;
     }
     std::vector<int32_t> sup;
     std::vector<double> ps;
     for (int32_t i = 0; i < s_n; ++i) {
+        if (nodes[i] < 0 || nodes[i] >= g->n) {
+            set_error("nvd_network_variance: nodes[%d] is outside [0, %lld)", i, (long long)g->n);
+            return NVD_ERR_INVALID_ARG;
+        }
         if (!(p[i] >= 0.0) || !std::isfinite(p[i])) {
             set_error("nvd_network_variance: p[%d] = %g is not a finite non-negative weight", i, p[i]);
             return NVD_ERR_INVALID_ARG;
@@ -529,13 +636,26 @@ int network_variance_impl(nvd_graph_t g, int32_t s_n, const int32_t *nodes, cons
     *var_out = 0.0;
     const int32_t m = (int32_t)sup.size();
     if (m == 0) return NVD_OK;
-    std::vector<double> R((size_t)m * m);
-    const int rc = resistance_matrix_impl(g, m, sup.data(), opts, R.data(), nullptr, s);
+    DeviceGuard guard(g->device);
+    int st = NVD_OK;
+    const int64_t tot = (int64_t)m * m;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((tot + QF_NT * 16 - 1) / (QF_NT * 16), 1024));
+    double *R_dev = (double *)g->wsp("rmat_R", (size_t)tot * 8, &st);
+    double *dp = (double *)g->wsp("var_p", (size_t)m * 8 + (size_t)nb * 8 + 8, &st);
+    int *dinf = (int *)g->wsp("var_inf", (size_t)nb * 4, &st);
+    if (st) return st;
+    double *part = dp + m, *dout = part + nb;
+    NVD_TRY_CUDA(cudaMemcpyAsync(dp, ps.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+    const int rc = resistance_matrix_core(g, m, sup.data(), o, R_dev, nullptr, s);
     if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
-    double v = 0.0;
-    for (int32_t i = 0; i < m; ++i)
-        for (int32_t j = 0; j < m; ++j) v += ps[i] * ps[j] * R[(size_t)i * m + j];
-    *var_out = 0.5 * v;
+    k_quadform_part<<<nb, QF_NT, 0, s>>>(m, dp, R_dev, part, dinf);
+    note_launch();
+    NVD_TRY_CUDA(cudaGetLastError());
+    k_quadform_final<<<1, QF_NT, 0, s>>>(nb, part, dinf, dout);
+    note_launch();
+    NVD_TRY_CUDA(cudaGetLastError());
+    NVD_TRY_CUDA(cudaMemcpyAsync(var_out, dout, 8, cudaMemcpyDeviceToHost, s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
     return rc;
 }
 

@@ -292,9 +292,10 @@ def test_network_variance(nvd):
     assert nvd.network_variance(G, [lab[5]], [1.0]) == 0.0
     assert nvd.network_variance(G, [lab[5], lab[310]], [0.5, 0.5]) == np.inf
     assert nvd.network_variance(G, [lab[5], lab[310]], [1.0, 0.0]) == 0.0
-    with pytest.raises(nvd.NvdError) as e:
-        nvd.network_variance(G, [0, 1], [0.5, -0.5])
-    assert e.value.status == 1
+    for bad_nodes, bad_p in (([0, 1], [0.5, -0.5]), ([0, g.n], [1.0, 0.0])):
+        with pytest.raises(nvd.NvdError) as e:
+            nvd.network_variance(G, bad_nodes, bad_p)
+        assert e.value.status == 1
     b = synth.workload_ba_small().graph
     bw = synth.csr_from_edges(b.n, b.eu, b.ev, rng.uniform(0.5, 2.0, b.m))
     B = nvd.Graph.from_csr(bw)
