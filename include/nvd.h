@@ -225,6 +225,27 @@ int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int3
                     nvd_solve_stats *stats, nvd_stream_t stream);
 
 /*
+ * nvd_ge_distance_warm -- nvd_ge_distance started from a saved solution z0
+ * instead of z = 0 (a warm start, e.g. the z_out of an earlier call when the
+ * vectors or the weights have changed a little).  CG runs on L c = P(delta - L z0)
+ * from z0; the residual test stays relative to |P delta|, so the same rtol gives
+ * the same accuracy in fewer iterations when z0 is close.  d^2 is the variational
+ * 2 delta^T z - z^T L z (error quadratic in the error of z); constants per
+ * component in z0 have no effect.
+ *
+ *   z0      [k][n] device array of xdtype (the layout of z_out; may be the same
+ *           buffer as z_out).
+ * Other arguments as nvd_ge_distance.  FP64 mode and device inputs only; the
+ * solve runs host-driven (NVD_SOLVE_PERSISTENT and a tuned persistent launch are
+ * not used).
+ * Errors: NVD_ERR_INVALID_ARG (z0 NULL with k > 0, FP32 or MIXED mode,
+ * NVD_SOLVE_HOST_INPUTS), otherwise as nvd_ge_distance.
+ */
+int nvd_ge_distance_warm(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdtype,
+                         const void *z0, const nvd_solve_opts *opts, double *d2_out, void *z_out,
+                         nvd_solve_stats *stats, nvd_stream_t stream);
+
+/*
  * nvd_effective_resistance -- R(u_j, v_j) = (e_u - e_v)^T L^+ (e_u - e_v) for j < k:
  * the GE distance (Section 3.1) of two indicator vectors, which on a graph with
  * conductances w is the effective resistance between the two nodes (the

@@ -102,6 +102,9 @@ _SIGS = {
     "nvd_ge_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
+    "nvd_ge_distance_warm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(SolveOpts),
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "nvd_effective_resistance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.POINTER(SolveOpts), ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -286,12 +289,14 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
                 d2_rtol: float = 1e-8, max_iter: int = 10000, max_refine: int = 8, kt: int = 0,
                 check_every: int = 4, single_rhs: bool = False, persistent: bool = False,
                 fold_direction: bool = False, test_timeout: bool = False, d2_stop: bool = False,
-                return_z: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
+                z0=None, return_z: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
     """Squared GE distances d^2 for the k pairs (rows) of x, y ([k, n] or [n]).
 
     CUDA tensors run on the device (d^2 returned as a CUDA float64 tensor); CPU
     tensors / numpy arrays go through the host-buffer path of the C ABI (copies
-    inside the call) and d^2 comes back on the host.
+    inside the call) and d^2 comes back on the host.  ``z0`` (CUDA, the shape and
+    dtype of x, FP64 mode) warm-starts every solve from a saved solution, e.g. the
+    z returned by an earlier call (nvd_ge_distance_warm).
     """
     torch = _torch()
     lib = load_library()
@@ -321,7 +326,18 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
         o.flags |= SOLVE_D2_STOP
     xdt = _dtype_code(X)
     stats = (SolveStats * max(k, 1))()
-    if X.is_cuda:
+    if z0 is not None:
+        Z0 = (z0[None] if one else z0).contiguous()
+        if not (X.is_cuda and Z0.is_cuda) or Z0.shape != X.shape or Z0.dtype != X.dtype:
+            raise ValueError("z0 must be a CUDA tensor of the shape and dtype of x (and x on the device)")
+        d2 = torch.empty(k, dtype=torch.float64, device=X.device)
+        Z = torch.empty_like(X) if return_z else None
+        o.flags |= SOLVE_D2_DEVICE
+        with torch.cuda.device(X.device):
+            rc = lib.nvd_ge_distance_warm(graph.handle, k, X.data_ptr(), Y.data_ptr(), xdt, Z0.data_ptr(),
+                                          ctypes.byref(o), d2.data_ptr(), None if Z is None else Z.data_ptr(),
+                                          stats, _stream_ptr(X.device))
+    elif X.is_cuda:
         d2 = torch.empty(k, dtype=torch.float64, device=X.device)
         Z = torch.empty_like(X) if return_z else None
         o.flags |= SOLVE_D2_DEVICE

@@ -344,16 +344,19 @@ struct FinMean {
 };
 
 // PCG start: rho = r^T D^-1 r, rr0 = |r|^2; a column iterates if it is a real
-// pair of this owner and its right-hand side is non-zero.
+// pair of this owner and its right-hand side is non-zero.  keep_rr0 (warm start,
+// r = P(delta - L z0)): rr0 stays |P delta|^2 from the first start, and a column
+// whose start already meets the residual test does not iterate.
 struct FinInit {
     int KT;
+    bool keep_rr0 = false;
     __device__ void operator()(const Ctx &c, int seg, int j, const double *s) const {
         const int64_t i = (int64_t)seg * KT + j;
         const bool valid = j < owner_of(c, seg).kc;
         const double rho = s[0], rr = s[1];
         c.rho[i] = rho;
         c.rr[i] = rr;
-        c.rr0[i] = rr;
+        if (!keep_rr0) c.rr0[i] = rr;
         c.alpha[i] = 0.0;
         c.beta[i] = 0.0;
         c.iters[i] = 0;
@@ -363,7 +366,7 @@ struct FinInit {
         }
         const bool finite = isfinite(rr) && isfinite(rho);
         c.status[i] = (valid && !finite) ? NVD_ERR_NUMERIC : NVD_OK;
-        const bool act = valid && finite && rr > 0.0 && rho > 0.0;
+        const bool act = valid && finite && rr > 0.0 && rho > 0.0 && !(keep_rr0 && rr <= c.rtol2 * c.rr0[i]);
         c.active[i] = act ? 1 : 0;
         if (act) atomicAdd(c.n_active, 1);
     }

@@ -87,7 +87,7 @@ int check_opts(const nvd_solve_opts &o) {
 // [k][n] of xdt).
 int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdt,
                   const nvd_solve_opts *opts, double *d2_out, void *z_out, nvd_solve_stats *stats,
-                  cudaStream_t s, bool idx = false) {
+                  cudaStream_t s, bool idx = false, const void *z0 = nullptr) {
     if (!g || k < 0 || (xdt != NVD_F32 && xdt != NVD_F64)) {
         set_error("nvd_ge_distance: invalid argument");
         return NVD_ERR_INVALID_ARG;
@@ -102,6 +102,10 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     if (opts) o = *opts; else nvd_solve_opts_default(&o);
     NVD_TRY(check_opts(o));
     if (g->tuned_fold[o.mode]) o.flags |= NVD_SOLVE_FOLD_DIRECTION;
+    if (z0 && (o.mode != NVD_MODE_FP64 || (o.flags & NVD_SOLVE_HOST_INPUTS) || idx)) {
+        set_error("nvd_ge_distance_warm: a warm start needs FP64 mode and device inputs");
+        return NVD_ERR_INVALID_ARG;
+    }
     DeviceGuard guard(g->device);
     const int KT = pick_kt(g, o, k);
     const bool mixed = o.mode == NVD_MODE_MIXED;
@@ -128,7 +132,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     }
     // persistent single-launch solve (FP64/FP32 modes; the launch timer needs the host loop)
     const bool persistent = ((o.flags & NVD_SOLVE_PERSISTENT) || g->tuned_persistent[o.mode]) && !mixed &&
-                            !prof_enabled();
+                            !prof_enabled() && !z0;
     const int64_t sk = (int64_t)std::max(g->nseg, 1) * KT;
     unsigned *bar = nullptr;
     if (persistent) {
@@ -212,6 +216,7 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
             io.x = (const char *)x + off;
             io.y = (const char *)y + off;
             io.z = z_out ? (char *)z_out + off : nullptr;
+            io.z0 = z0 ? (const char *)z0 + off : nullptr;
         }
         if (io.z && g->n_singleton > 0)
             NVD_TRY_CUDA(cudaMemsetAsync(io.z, 0, (size_t)kc * g->n * xsz, s));
@@ -721,6 +726,25 @@ extern "C" int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const vo
         return NVD_ERR_OOM;
     } catch (...) {
         set_error("nvd_ge_distance: unexpected host exception");
+        return NVD_ERR_CUDA;
+    }
+}
+
+extern "C" int nvd_ge_distance_warm(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdtype,
+                                    const void *z0, const nvd_solve_opts *opts, double *d2_out, void *z_out,
+                                    nvd_solve_stats *stats, nvd_stream_t stream) {
+    clear_error();
+    if (k > 0 && !z0) {
+        set_error("nvd_ge_distance_warm: z0 is required");
+        return NVD_ERR_INVALID_ARG;
+    }
+    try {
+        return distance_impl(g, k, x, y, xdtype, opts, d2_out, z_out, stats, (cudaStream_t)stream, false, z0);
+    } catch (const std::bad_alloc &) {
+        set_error("nvd_ge_distance_warm: host allocation failed");
+        return NVD_ERR_OOM;
+    } catch (...) {
+        set_error("nvd_ge_distance_warm: unexpected host exception");
         return NVD_ERR_CUDA;
     }
 }

@@ -11,6 +11,8 @@
 //          form 2 delta^T z - z^T L z.
 #pragma once
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 #include <utility>
@@ -291,6 +293,7 @@ struct TileIO {
     const void *x, *y;    // device, [kc][n], offset to the tile (idx: [kc] int32 node ids)
     void *z;              // device or NULL
     int32_t idx = 0;      // 1: x, y are node ids (indicator pairs)
+    const void *z0 = nullptr;  // device [kc][n] of the x type: warm start (FP64 mode), else NULL
 };
 
 // FP64 / FP32 PCG on one tile.  Results stay in the Ctx state (d2, rr, ...).
@@ -316,11 +319,43 @@ int tile_pcg(nvd_graph_s *g, Ctx c, SolveWs &w, const nvd_solve_opts &o, const T
     oi.src = delta; oi.writeback = delta; oi.x = x; oi.r = r; oi.p = fused ? u : p;
     oi.fin.KT = KT;
     NVD_TRY((launch_vec<TV, KT>(c, oi, s)));
+    bool warm = false;
+    if constexpr (std::is_same<TV, double>::value) {
+        if (io.z0) {
+            // warm start: x = z0, r = P(delta - L x) (q as scratch), the residual test
+            // still relative to |P delta|; the start leaves x alone
+            warm = true;
+            dev::OpLoadX<TV, TX, KT> ol;
+            ol.Z0 = reinterpret_cast<const TX *>(io.z0);
+            ol.x = x;
+            NVD_TRY((launch_vec<TV, KT>(c, ol, s)));
+            dev::EpiResid er;
+            er.delta = delta;
+            er.fin.KT = KT;
+            NVD_TRY((launch_spmm<double, TW, double, KT>(c, er, x, q, s, spmm_bytes(g, KT, 8, sizeof(TW), 8))));
+            NVD_TRY_CUDA(cudaMemsetAsync(c.n_active, 0, 4, s));
+            dev::OpInit<TV, KT> ow = oi;
+            ow.src = q; ow.writeback = nullptr; ow.zero_x = false;
+            ow.fin.keep_rr0 = true;
+            NVD_TRY((launch_vec<TV, KT>(c, ow, s)));
+        }
+    }
     const double bytes = spmm_bytes(g, KT, sizeof(TV), sizeof(TW), sizeof(TA), fused);
     NVD_TRY((pcg_loop<TV, TW, TA, KT>(c, x, r, p, q, u, fused, o.max_iter, o.check_every, bytes, s)));
+    if constexpr (std::is_same<TV, double>::value) {
+        if (warm) {
+            // from x0 != 0 delta^T x is only first-order accurate: take the variational
+            // d^2 = delta^T x + x^T (delta - L x) (error quadratic in the error of x) and
+            // the true residual for the statistics
+            dev::EpiResid er;
+            er.delta = delta;
+            er.fin.KT = KT;
+            NVD_TRY((launch_spmm<double, TW, double, KT>(c, er, x, q, s, spmm_bytes(g, KT, 8, sizeof(TW), 8))));
+        }
+    }
     dev::OpFinal<TV, KT> of;
     of.x = x; of.delta = delta;
-    of.fin.KT = KT; of.fin.set_d2 = true;
+    of.fin.KT = KT; of.fin.set_d2 = !warm;
     NVD_TRY((launch_vec<TV, KT>(c, of, s)));
     if (io.z) {
         dev::OpZout<TV, TX, KT> oz;

@@ -116,6 +116,7 @@ struct OpInit {
     const double *src;
     double *writeback;
     TV *x, *r, *p;
+    bool zero_x = true;   // false: keep x (warm start)
     FinInit fin;
     double mu[VEC];
     __device__ void setup(const Ctx &c, int seg, int col0) {
@@ -141,7 +142,42 @@ struct OpInit {
         if (writeback) stv(writeback + o, q.s);
         stv(r + o, rv);
         stv(p + o, uv);
-        stv(x + o, zv);
+        if (zero_x) stv(x + o, zv);
+    }
+};
+
+// x = z0, a saved solution in the user's layout ([kc][ld], e.g. z_out of an
+// earlier call) cast to TV, for a warm start; padding columns (j >= kc) get 0.
+template <class TV, class TX, int KT, class LD = LdPlain>
+struct OpLoadX {
+    static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = false;
+    struct R { double s[VEC]; };
+    typedef double D;
+    const TX *Z0;
+    TV *x;
+    FinNone fin;
+    int64_t base, ld;
+    int kc;
+    __device__ void setup(const Ctx &c, int seg, int) {
+        const Owner &o = owner_of(c, seg);
+        base = o.base;
+        ld = o.ld;
+        kc = o.kc;
+    }
+    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &g) const {
+        const int64_t u = (c.perm ? (int64_t)__ldg(c.perm + i) : i) - base;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const int j = col0 + v;
+            g.s[v] = j < kc ? (double)__ldg(Z0 + (int64_t)j * ld + u) : 0.0;
+        }
+    }
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
+        TV xv[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) xv[v] = (TV)g.s[v];
+        stv(x + i * KT + col0, xv);
     }
 };
 

@@ -67,6 +67,7 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert lib.nvd_effective_resistance(None, 1, None, None, None, None, None, None) == 1
     assert lib.nvd_resistance_matrix(None, 1, None, None, None, None, None) == 1
     assert lib.nvd_network_variance(None, 1, None, None, None, None, None) == 1
+    assert lib.nvd_ge_distance_warm(None, 1, None, None, 1, None, None, None, None, None, None) == 1
     assert lib.nvd_graph_set_tuning(None, 0, None) == 1
     assert lib.nvd_graph_destroy(None) == 0
     assert lib.nvd_profile_read(3, None, None, None) == 1
