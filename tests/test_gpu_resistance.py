@@ -132,6 +132,17 @@ def test_union_fp32_and_mixed(nvd, union_case):
     check(nvd.effective_resistance(G, U, V, mode=nvd.MODE_MIXED, rtol=1e-4, d2_rtol=1e-11), want, 1e-8)
 
 
+def test_union_d2_stop(nvd, union_case):
+    """The d^2 stop on node-id pairs: every resistance within its d2_rtol (1e-6) of the
+    closed forms, single right-hand side and tiles of 8."""
+    g, U, V, want = union_case
+    G = nvd.Graph.from_csr(g)
+    for kw in (dict(kt=1), dict(kt=8)):
+        R, st = nvd.effective_resistance(G, U, V, rtol=1e-12, d2_stop=True, d2_rtol=1e-6, return_stats=True, **kw)
+        check(R, want, 1e-6)
+        assert all(s["status"] == 0 for s in st)
+
+
 def test_equals_ge_distance_of_indicators(nvd):
     """On the BA workload graph: the node-id path and nvd_ge_distance on the dense
     indicator vectors run the same solve."""
