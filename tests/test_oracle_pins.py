@@ -203,6 +203,20 @@ def test_effective_resistance_foster_disconnected():
     assert float(np.sum(g.ew * R)) == pytest.approx(g.n - c, rel=1e-11)
 
 
+def test_network_variance_pin_catches_dropped_half(monkeypatch):
+    """A copy without the factor 1/2 (or with R replaced by R^2) fails the K_n pin."""
+    n, wgt = 9, 1.7
+    kn = graph(n, *synth.complete_graph(n), np.full(n * (n - 1) // 2, wgt))
+    want = (n - 1) / (n * n * wgt)
+    orig = dense.effective_resistance
+    monkeypatch.setattr(dense, "effective_resistance", lambda *a: 2.0 * orig(*a))
+    assert dense.network_variance(kn.n, kn.rowptr, kn.colidx, kn.w, np.arange(n), np.full(n, 1 / n)) != \
+        pytest.approx(want, rel=1e-6)
+    monkeypatch.setattr(dense, "effective_resistance", lambda *a: orig(*a) ** 2)
+    assert dense.network_variance(kn.n, kn.rowptr, kn.colidx, kn.w, np.arange(n), np.full(n, 1 / n)) != \
+        pytest.approx(want, rel=1e-6)
+
+
 def test_effective_resistance_pin_catches_sign_mistake(monkeypatch):
     """A copy with L^+_uu + L^+_vv + 2 L^+_uv (wrong sign) fails the path pin."""
     orig = dense.pinv_laplacian
