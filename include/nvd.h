@@ -121,6 +121,8 @@ typedef enum {
 #define NVD_SOLVE_FOLD_DIRECTION 32u /* two kernels per CG iteration: the direction update folded into
                                         an SpMV on D^-1 r (default: three, SpMV on p, x/r update,
                                         direction pass) */
+#define NVD_SOLVE_ELIMINATE 256u  /* solve on the handle's reduced graph (nvd_graph_eliminate): degree-1/2
+                                     nodes eliminated exactly; device x, y, no z_out */
 #define NVD_SOLVE_D2_STOP 128u    /* FP64/FP32: a pair also stops once its d^2 is estimated to be
                                      within d2_rtol: step k of CG from z = 0 adds exactly
                                      alpha_k r_k^T D^-1 r_k to delta^T z and the remaining gap is
@@ -223,6 +225,58 @@ int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_result *t);
 int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdtype,
                     const nvd_solve_opts *opts, double *d2_out, void *z_out,
                     nvd_solve_stats *stats, nvd_stream_t stream);
+
+/*
+ * nvd_graph_eliminate -- exact elimination of degree-1 and degree-2 nodes for
+ * later solves with NVD_SOLVE_ELIMINATE.  Eliminating a node of the Laplacian
+ * leaves the Schur complement, again a graph Laplacian with no fill for such a
+ * node: a leaf goes with its edge, a node with neighbours a, c becomes the edge
+ * a-c of conductance w_a w_c / d_v (series rule), and for b mean-zero per
+ * component b^T L^+ b = b'^T L'^+ b' + b_v^2 / d_v with b'_u = b_u + b_v w_vu / d_v,
+ * so d^2 (GE equation, Section 3.1) is the reduced graph's d^2 plus one term per
+ * eliminated node, and PCG (Section 3.2) runs on the reduced graph.  Nodes go in
+ * rounds of independent sets, so the per-solve forward pass is one parallel step
+ * per round.  Builds on the host from the handle's CSR (O(nnz) memory) and keeps
+ * the reduced graph in the handle; calling it again rebuilds.  Synchronous.
+ *   info    optional: kept nodes, their stored entries, eliminated nodes, rounds.
+ * Errors: NVD_ERR_INVALID_ARG (NULL handle), NVD_ERR_OOM, NVD_ERR_CUDA.
+ */
+typedef struct {
+    int64_t n_kept;
+    int64_t nnz_kept;
+    int64_t n_eliminated;
+    int32_t rounds;
+    int32_t reserved;
+} nvd_elim_info;
+int nvd_graph_eliminate(nvd_graph_t g, nvd_elim_info *info, nvd_stream_t stream);
+
+/*
+ * nvd_eliminate_host -- the same elimination on a host CSR (symmetric, no GPU
+ * work), for checking it: writes the kept nodes (increasing ids) and the reduced
+ * graph's CSR on their indices.  keep [n], red_rowptr [n + 1], red_colidx and
+ * red_w [rowptr[n]] (the reduced graph has at most as many entries); any output
+ * array may be NULL.  Errors: NVD_ERR_INVALID_ARG (n < 1, NULL rowptr or n_kept,
+ * NULL colidx / w with entries), NVD_ERR_OOM.
+ */
+int nvd_eliminate_host(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *w,
+                       int64_t *n_kept, int32_t *keep, int64_t *red_rowptr, int32_t *red_colidx,
+                       double *red_w, int32_t *rounds);
+
+/*
+ * nvd_eliminate_host_program -- the per-solve program of the same elimination, for
+ * checking it on the host: counts[5] = {records R, kept nodes K, record gather
+ * entries, kept-node gather entries, rounds}.  Record r eliminates node rec_v[r]
+ * (weighted degree rec_d[r]); records of round t are [round_ptr[t], round_ptr[t+1]);
+ * the forward pass computes b_r = b[rec_v[r]] + sum_{e in [rin_ptr[r], rin_ptr[r+1])}
+ * rin_f[e] b_{rin_src[e]} round by round, the reduced right-hand side of kept
+ * node i = b[keep[i]] + the same sum over kin_*, and d^2 = reduced d^2 + sum_r
+ * b_r^2 / rec_d[r].  With any array NULL only counts is written (sizes: R, R,
+ * rounds + 1, R + 1, counts[2] x2, K, K + 1, counts[3] x2).
+ */
+int nvd_eliminate_host_program(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *w,
+                               int64_t *counts, int32_t *rec_v, double *rec_d, int64_t *round_ptr,
+                               int64_t *rin_ptr, int32_t *rin_src, double *rin_f, int32_t *keep,
+                               int64_t *kin_ptr, int32_t *kin_src, double *kin_f);
 
 /*
  * nvd_ge_distance_warm -- nvd_ge_distance started from a saved solution z0

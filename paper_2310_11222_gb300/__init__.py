@@ -41,6 +41,7 @@ SOLVE_NO_SYNC = 16
 SOLVE_FOLD_DIRECTION = 32
 SOLVE_TEST_TIMEOUT = 64
 SOLVE_D2_STOP = 128
+SOLVE_ELIMINATE = 256
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_SYM_CHECK = 2
 TUNE_SINGLE_RHS = 1
@@ -68,6 +69,12 @@ class SolveStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("rel_resid", ctypes.c_double), ("status", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class ElimInfo(ctypes.Structure):
+    """Mirror of ``nvd_elim_info``."""
+    _fields_ = [("n_kept", ctypes.c_int64), ("nnz_kept", ctypes.c_int64), ("n_eliminated", ctypes.c_int64),
+                ("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -102,6 +109,11 @@ _SIGS = {
     "nvd_ge_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
+    "nvd_graph_eliminate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ElimInfo), ctypes.c_void_p]),
+    "nvd_eliminate_host": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "nvd_eliminate_host_program": (ctypes.c_int, [ctypes.c_int64] + [ctypes.c_void_p] * 14),
     "nvd_ge_distance_warm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(SolveOpts),
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -251,6 +263,17 @@ class Graph:
                                         ctypes.byref(nb)), "nvd_graph_info")
         return {"n": n.value, "nnz": nnz.value, "ncomp": nc.value, "device_bytes": nb.value}
 
+    def eliminate(self) -> dict:
+        """Eliminate degree-1/2 nodes exactly (nvd_graph_eliminate); later solves with
+        ``eliminate=True`` run PCG on the reduced graph."""
+        info = ElimInfo()
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            _check(self._lib.nvd_graph_eliminate(self.handle, ctypes.byref(info), _stream_ptr(self.device)),
+                   "nvd_graph_eliminate")
+        return {"n_kept": info.n_kept, "nnz_kept": info.nnz_kept, "n_eliminated": info.n_eliminated,
+                "rounds": info.rounds}
+
     def tune(self, *, mode: int = 0, k: int = 1, single_rhs: bool = False) -> dict:
         """Time the solve's work decompositions on this graph (``nvd_graph_tune``) and keep
         the fastest for later calls of ``mode``; returns the chosen setting."""
@@ -289,14 +312,16 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
                 d2_rtol: float = 1e-8, max_iter: int = 10000, max_refine: int = 8, kt: int = 0,
                 check_every: int = 4, single_rhs: bool = False, persistent: bool = False,
                 fold_direction: bool = False, test_timeout: bool = False, d2_stop: bool = False,
-                z0=None, return_z: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
+                z0=None, eliminate: bool = False, return_z: bool = False, return_stats: bool = False,
+                allow_not_converged: bool = False):
     """Squared GE distances d^2 for the k pairs (rows) of x, y ([k, n] or [n]).
 
     CUDA tensors run on the device (d^2 returned as a CUDA float64 tensor); CPU
     tensors / numpy arrays go through the host-buffer path of the C ABI (copies
     inside the call) and d^2 comes back on the host.  ``z0`` (CUDA, the shape and
     dtype of x, FP64 mode) warm-starts every solve from a saved solution, e.g. the
-    z returned by an earlier call (nvd_ge_distance_warm).
+    z returned by an earlier call (nvd_ge_distance_warm).  ``eliminate`` solves on
+    the reduced graph of ``graph.eliminate()`` (CUDA inputs, no z).
     """
     torch = _torch()
     lib = load_library()
@@ -324,6 +349,8 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
         o.flags |= SOLVE_TEST_TIMEOUT
     if d2_stop:
         o.flags |= SOLVE_D2_STOP
+    if eliminate:
+        o.flags |= SOLVE_ELIMINATE
     xdt = _dtype_code(X)
     stats = (SolveStats * max(k, 1))()
     if z0 is not None:

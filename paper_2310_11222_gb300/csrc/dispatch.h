@@ -32,6 +32,11 @@ int run_collect(const Ctx &c, int KT, ColResult *res, double *d2dev, int64_t d2_
 // nvd_ge_distance without z_out / stats (used by the tuner to time configurations).
 int ge_distance_internal(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdt,
                          const nvd_solve_opts *opts, double *d2_out, cudaStream_t s);
+// nvd_ge_distance with NVD_SOLVE_ELIMINATE: degree-1/2 nodes eliminated exactly,
+// PCG on the reduced graph (elim.cu).
+int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdt,
+                  const nvd_solve_opts *opts, double *d2_out, void *z_out, nvd_solve_stats *stats,
+                  cudaStream_t s);
 // y = L x for one contiguous column (internal order), dtype = F32 or F64.
 int run_apply(nvd_graph_s *g, const Ctx &c, const void *x, void *y, int dtype, cudaStream_t s);
 

@@ -88,6 +88,11 @@ struct Plan {
 
 }  // namespace nvd
 
+namespace nvd {
+struct ElimState;   // exact low-degree elimination (elim.cu)
+void elim_state_delete(ElimState *e);
+}  // namespace nvd
+
 struct nvd_graph_s {
     uint64_t id = 0;             // unique per handle (cache keys)
     int device = 0;
@@ -115,6 +120,8 @@ struct nvd_graph_s {
     // first use, so the next tile's host-to-device copy overlaps the current solve
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+    // degree-1/2 nodes eliminated exactly and the reduced graph (nvd_graph_eliminate)
+    std::unique_ptr<nvd::ElimState, void (*)(nvd::ElimState *)> elim{nullptr, nvd::elim_state_delete};
     ~nvd_graph_s();
 
     void *wsp(const std::string &name, size_t bytes, int *st);

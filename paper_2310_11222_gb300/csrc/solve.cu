@@ -69,7 +69,7 @@ int pick_kt(const nvd_graph_s *g, const nvd_solve_opts &o, int k) {
 int check_opts(const nvd_solve_opts &o) {
     const uint32_t known = NVD_SOLVE_SINGLE_RHS | NVD_SOLVE_D2_DEVICE | NVD_SOLVE_HOST_INPUTS |
                            NVD_SOLVE_PERSISTENT | NVD_SOLVE_NO_SYNC | NVD_SOLVE_FOLD_DIRECTION |
-                           NVD_SOLVE_TEST_TIMEOUT | NVD_SOLVE_D2_STOP;
+                           NVD_SOLVE_TEST_TIMEOUT | NVD_SOLVE_D2_STOP | NVD_SOLVE_ELIMINATE;
     const bool d2stop = (o.flags & NVD_SOLVE_D2_STOP) != 0;
     if (o.mode < NVD_MODE_FP64 || o.mode > NVD_MODE_MIXED || !(o.rtol > 0.0) || o.max_iter < 1 ||
         o.check_every < 1 || !(o.kt == 0 || o.kt == 1 || o.kt == 4 || o.kt == 8 || o.kt == 16 || o.kt == 32) ||
@@ -720,6 +720,11 @@ extern "C" int nvd_ge_distance(nvd_graph_t g, int32_t k, const void *x, const vo
                                nvd_solve_stats *stats, nvd_stream_t stream) {
     clear_error();
     try {
+        if (opts && (opts->flags & NVD_SOLVE_ELIMINATE)) {
+            nvd_solve_opts o = *opts;
+            NVD_TRY(check_opts(o));
+            return elim_distance(g, k, x, y, xdtype, &o, d2_out, z_out, stats, (cudaStream_t)stream);
+        }
         return distance_impl(g, k, x, y, xdtype, opts, d2_out, z_out, stats, (cudaStream_t)stream);
     } catch (const std::bad_alloc &) {
         set_error("nvd_ge_distance: host allocation failed");
