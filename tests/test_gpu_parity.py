@@ -65,6 +65,18 @@ def test_ba_small_fp64(nvd, ba_small, single, fold):
     assert all(abs(a - s["iters"]) <= 1 for a, s in zip(it, stc))
 
 
+def test_ba_small_against_stored_values(nvd, ba_small):
+    """The stored oracle values of tests/golden/ba_small_d2.txt (make_golden.py)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ba_small_d2.txt")
+    with open(path) as f:
+        stored = np.array([float(v) for v in f if v.strip() and not v.startswith("#")])
+    g, X, Y, _ = ba_small
+    G = nvd.Graph.from_csr(g)
+    d2 = nvd.ge_distance(G, on(X), on(Y), rtol=1e-10)
+    assert rel(d2.cpu().numpy(), stored) < 1e-8
+
+
 @pytest.mark.parametrize("kt", [1, 4, 8, 16, 32])
 def test_fp64_every_tile_width(nvd, ba_small, kt):
     g, X, Y, want = ba_small
