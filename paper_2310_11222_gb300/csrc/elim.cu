@@ -323,10 +323,11 @@ static int build_state(nvd_graph_s *g, cudaStream_t s) {
     NVD_TRY(upload_vec(st->kin_f, er.kin_f, s));
     NVD_TRY_CUDA(cudaStreamSynchronize(s));
     // the reduced graph: nodes = kept nodes of g's internal order (still
-    // component-contiguous), symmetric by construction
-    NVD_TRY(nvd_graph_create(&st->red, st->n_keep, (int64_t)er.red_col.size(), er.red_rowptr.data(),
-                             er.red_col.data(), er.red_w.data(), NVD_F64, NVD_GRAPH_SKIP_SYM_CHECK,
-                             (nvd_stream_t)s));
+    // component-contiguous), symmetric by construction; none when no edge is left
+    // (every component went down to one node: d^2 is the eliminated terms alone)
+    if (st->red_nnz > 0)
+        NVD_TRY(nvd_graph_create(&st->red, st->n_keep, st->red_nnz, er.red_rowptr.data(), er.red_col.data(),
+                                 er.red_w.data(), NVD_F64, NVD_GRAPH_SKIP_SYM_CHECK, (nvd_stream_t)s));
     g->elim = std::move(st);
     return NVD_OK;
 }
@@ -429,7 +430,7 @@ int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     nvd_solve_opts o2 = o;
     o2.flags = (o.flags & ~(NVD_SOLVE_ELIMINATE | NVD_SOLVE_HOST_INPUTS | NVD_SOLVE_NO_SYNC)) | NVD_SOLVE_D2_DEVICE;
     int rc = NVD_OK;
-    if (E.red_nnz > 0) {
+    if (E.red) {
         rc = nvd_ge_distance(E.red, k, bred, zero, NVD_F64, &o2, d2r, nullptr, stats, (nvd_stream_t)s);
         if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
     } else {
@@ -470,9 +471,7 @@ extern "C" int nvd_graph_eliminate(nvd_graph_t g, nvd_elim_info *info, nvd_strea
             info->n_kept = g->elim->n_keep;
             info->n_eliminated = g->elim->n_rec;
             info->rounds = (int32_t)g->elim->round_ptr.size() - 1;
-            int64_t nnz = 0;
-            nvd_graph_info(g->elim->red, nullptr, &nnz, nullptr, nullptr);
-            info->nnz_kept = nnz;
+            info->nnz_kept = g->elim->red_nnz;
         }
         return NVD_OK;
     } catch (const std::bad_alloc &) {
