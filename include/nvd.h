@@ -122,7 +122,7 @@ typedef enum {
                                         an SpMV on D^-1 r (default: three, SpMV on p, x/r update,
                                         direction pass) */
 #define NVD_SOLVE_ELIMINATE 256u  /* solve on the handle's reduced graph (nvd_graph_eliminate): degree-1/2
-                                     nodes eliminated exactly; device x, y, no z_out */
+                                     nodes eliminated exactly; device x, y; z_out by back-substitution */
 #define NVD_SOLVE_D2_STOP 128u    /* FP64/FP32: a pair also stops once its d^2 is estimated to be
                                      within d2_rtol: step k of CG from z = 0 adds exactly
                                      alpha_k r_k^T D^-1 r_k to delta^T z and the remaining gap is
@@ -270,13 +270,17 @@ int nvd_eliminate_host(int64_t n, const int64_t *rowptr, const int32_t *colidx, 
  * the forward pass computes b_r = b[rec_v[r]] + sum_{e in [rin_ptr[r], rin_ptr[r+1])}
  * rin_f[e] b_{rin_src[e]} round by round, the reduced right-hand side of kept
  * node i = b[keep[i]] + the same sum over kin_*, and d^2 = reduced d^2 + sum_r
- * b_r^2 / rec_d[r].  With any array NULL only counts is written (sizes: R, R,
- * rounds + 1, R + 1, counts[2] x2, K, K + 1, counts[3] x2).
+ * b_r^2 / rec_d[r].  The back-substitution (z_out) takes the records in reverse
+ * round order: z[rec_v[r]] = b_r / rec_d[r] + rec_f0[r] z[rec_t0[r]] + rec_f1[r]
+ * z[rec_t1[r]] (rec_t1 = -1: none), from the reduced solution on the kept nodes,
+ * then mean-zero per component.  With any array NULL only counts is written
+ * (sizes: R, R, rounds + 1, R + 1, counts[2] x2, K, K + 1, counts[3] x2, R x4).
  */
 int nvd_eliminate_host_program(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *w,
                                int64_t *counts, int32_t *rec_v, double *rec_d, int64_t *round_ptr,
                                int64_t *rin_ptr, int32_t *rin_src, double *rin_f, int32_t *keep,
-                               int64_t *kin_ptr, int32_t *kin_src, double *kin_f);
+                               int64_t *kin_ptr, int32_t *kin_src, double *kin_f, int32_t *rec_t0,
+                               int32_t *rec_t1, double *rec_f0, double *rec_f1);
 
 /*
  * nvd_ge_distance_warm -- nvd_ge_distance started from a saved solution z0

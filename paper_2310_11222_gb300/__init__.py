@@ -113,7 +113,7 @@ _SIGS = {
     "nvd_eliminate_host": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
-    "nvd_eliminate_host_program": (ctypes.c_int, [ctypes.c_int64] + [ctypes.c_void_p] * 14),
+    "nvd_eliminate_host_program": (ctypes.c_int, [ctypes.c_int64] + [ctypes.c_void_p] * 18),
     "nvd_ge_distance_warm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(SolveOpts),
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -321,7 +321,7 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
     inside the call) and d^2 comes back on the host.  ``z0`` (CUDA, the shape and
     dtype of x, FP64 mode) warm-starts every solve from a saved solution, e.g. the
     z returned by an earlier call (nvd_ge_distance_warm).  ``eliminate`` solves on
-    the reduced graph of ``graph.eliminate()`` (CUDA inputs, no z).
+    the reduced graph of ``graph.eliminate()`` (CUDA inputs; z by back-substitution).
     """
     torch = _torch()
     lib = load_library()

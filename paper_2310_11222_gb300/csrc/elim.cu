@@ -34,6 +34,8 @@ namespace nvd {
 struct ElimResult {
     std::vector<int32_t> rec_v;          // eliminated node of each record
     std::vector<double> rec_d;           // its weighted degree when eliminated
+    std::vector<int32_t> rec_t0, rec_t1; // its neighbours then (-1: none), for the back-substitution
+    std::vector<double> rec_f0, rec_f1;  // w_vt / d_v
     std::vector<int64_t> round_ptr;      // records of round t: [round_ptr[t], round_ptr[t+1])
     std::vector<int32_t> keep;           // kept nodes, increasing id
     std::vector<int64_t> red_rowptr;     // reduced graph on the indices of `keep`
@@ -57,8 +59,8 @@ static int eliminate_low_degree(int64_t n, const int64_t *rowptr, const int32_t 
             if (col[e] != v && w[e] != 0.0) adj[v].push_back({col[e], w[e]});
     std::vector<char> alive(n, 1);
     std::vector<int32_t> taken(n, -1), blocked(n, -1), rec_of(n, -1);
-    std::vector<int32_t> t0, t1;
-    std::vector<double> f0, f1;
+    std::vector<int32_t> &t0 = out->rec_t0, &t1 = out->rec_t1;
+    std::vector<double> &f0 = out->rec_f0, &f1 = out->rec_f1;
     // distinct live neighbours of v with their summed conductances (parallel entries
     // added); returns their number, or 3 for "more than two".  Entries of eliminated
     // nodes are dropped from the list on the way.
@@ -210,7 +212,7 @@ struct ElimState {
     nvd_graph_t red = nullptr;           // the reduced graph
     int64_t n_rec = 0, n_keep = 0, red_nnz = 0;
     std::vector<int64_t> round_ptr;
-    DevBuf rec_v, rec_d, rin_ptr, rin_src, rin_f, keep, kin_ptr, kin_src, kin_f;
+    DevBuf rec_v, rec_d, rin_ptr, rin_src, rin_f, keep, kin_ptr, kin_src, kin_f, rec_t0, rec_t1, rec_f0, rec_f1;
     ~ElimState() {
         if (red) nvd_graph_destroy(red);
     }
@@ -281,6 +283,29 @@ __global__ void k_elim_extra_final(int nb, const double *__restrict__ part, doub
     if (threadIdx.x == 0) *out = t;
 }
 
+// Back-substitution of one round (rounds in reverse order): an eliminated node's
+// solution from its right-hand side and its neighbours at elimination time,
+//     z_v = b_v / d_v + f_0 z_{t0} + f_1 z_{t1}   (f = w_vt / d_v),
+// whose solutions are known (kept, or eliminated in a later round).
+__global__ void k_elim_back(int64_t r0, int64_t r1, const int32_t *__restrict__ rec_v,
+                            const double *__restrict__ rec_d, const int32_t *__restrict__ t0,
+                            const int32_t *__restrict__ t1, const double *__restrict__ f0,
+                            const double *__restrict__ f1, const double *__restrict__ rb, double *__restrict__ z) {
+    for (int64_t r = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < r1;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double v = rb[r] / rec_d[r] + f0[r] * z[t0[r]];
+        if (t1[r] >= 0) v += f1[r] * z[t1[r]];
+        z[rec_v[r]] = v;
+    }
+}
+
+// z[keep[i]] = the reduced graph's solution at its node i.
+__global__ void k_elim_put_keep(int64_t K, const int32_t *__restrict__ keep, const double *__restrict__ zr,
+                                double *__restrict__ z) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x)
+        z[keep[i]] = zr[i];
+}
+
 // d2 = d2 of the reduced graph + the eliminated nodes' terms.
 __global__ void k_elim_add(int32_t k, const double *__restrict__ a, const double *__restrict__ b,
                            double *__restrict__ out) {
@@ -321,6 +346,10 @@ static int build_state(nvd_graph_s *g, cudaStream_t s) {
     NVD_TRY(upload_vec(st->kin_ptr, er.kin_ptr, s));
     NVD_TRY(upload_vec(st->kin_src, er.kin_src, s));
     NVD_TRY(upload_vec(st->kin_f, er.kin_f, s));
+    NVD_TRY(upload_vec(st->rec_t0, er.rec_t0, s));
+    NVD_TRY(upload_vec(st->rec_t1, er.rec_t1, s));
+    NVD_TRY(upload_vec(st->rec_f0, er.rec_f0, s));
+    NVD_TRY(upload_vec(st->rec_f1, er.rec_f1, s));
     NVD_TRY_CUDA(cudaStreamSynchronize(s));
     // the reduced graph: nodes = kept nodes of g's internal order (still
     // component-contiguous), symmetric by construction; none when no edge is left
@@ -345,8 +374,8 @@ int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         set_error("nvd_ge_distance: NVD_SOLVE_ELIMINATE needs nvd_graph_eliminate on the handle first");
         return NVD_ERR_INVALID_ARG;
     }
-    if (!x || !y || !d2_out || z_out || (o.flags & NVD_SOLVE_HOST_INPUTS)) {
-        set_error("nvd_ge_distance: NVD_SOLVE_ELIMINATE takes device x, y, gives no z_out and needs d2_out");
+    if (!x || !y || !d2_out || (o.flags & NVD_SOLVE_HOST_INPUTS)) {
+        set_error("nvd_ge_distance: NVD_SOLVE_ELIMINATE takes device x, y and needs d2_out");
         return NVD_ERR_INVALID_ARG;
     }
     TraceRange trace("nvd_ge_distance (eliminated)");
@@ -373,13 +402,18 @@ int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     const int nbx = (int)std::max<int64_t>(1, std::min<int64_t>((R + EL_NT * 8 - 1) / (EL_NT * 8), 1024));
     double *bred = (double *)g->wsp("elim_b", (size_t)k * K * 8, &st);
     double *zero = (double *)g->wsp("elim_zero", (size_t)k * K * 8, &st);
-    double *rb = (double *)g->wsp("elim_rb", (size_t)std::max<int64_t>(R, 1) * 8, &st);
+    // the records' right-hand sides of every pair stay for the back-substitution
+    // when z_out is asked for; otherwise one pair's at a time
+    const int64_t rbs = std::max<int64_t>(R, 1);
+    double *rb_all = (double *)g->wsp("elim_rb", (size_t)rbs * (z_out ? k : 1) * 8, &st);
     double *ex = (double *)g->wsp("elim_extra", (size_t)(3 * k + nbx) * 8, &st);
+    double *zred = z_out ? (double *)g->wsp("elim_zred", (size_t)k * K * 8, &st) : nullptr;
     if (st) return st;
     double *d2r = ex + k, *d2f = ex + 2 * k, *part = ex + 3 * k;
     NVD_TRY_CUDA(cudaMemsetAsync(zero, 0, (size_t)k * K * 8, s));
     const size_t xsz = xdt == NVD_F64 ? 8 : 4;
     for (int32_t j = 0; j < k; ++j) {
+        double *rb = rb_all + (z_out ? (size_t)j * rbs : 0);
         c.own0 = Owner{(const char *)x + (size_t)j * g->n * xsz, (const char *)y + (size_t)j * g->n * xsz,
                        nullptr, 0, g->n, 1, 0, g->nseg, 0};
         c.owners = nullptr;
@@ -431,13 +465,53 @@ int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     o2.flags = (o.flags & ~(NVD_SOLVE_ELIMINATE | NVD_SOLVE_HOST_INPUTS | NVD_SOLVE_NO_SYNC)) | NVD_SOLVE_D2_DEVICE;
     int rc = NVD_OK;
     if (E.red) {
-        rc = nvd_ge_distance(E.red, k, bred, zero, NVD_F64, &o2, d2r, nullptr, stats, (nvd_stream_t)s);
+        rc = nvd_ge_distance(E.red, k, bred, zero, NVD_F64, &o2, d2r, zred, stats, (nvd_stream_t)s);
         if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
     } else {
         // every component was eliminated down to one node: nothing left to solve
         NVD_TRY_CUDA(cudaMemsetAsync(d2r, 0, (size_t)k * 8, s));
+        if (zred) NVD_TRY_CUDA(cudaMemsetAsync(zred, 0, (size_t)k * K * 8, s));
         if (stats)
             for (int32_t j = 0; j < k; ++j) stats[j] = nvd_solve_stats{0, 0, 0.0, NVD_OK, 0};
+    }
+    if (z_out) {
+        // z of the full graph: the reduced solution on the kept nodes, the eliminated
+        // nodes by back-substitution (last round first), then mean-zero per
+        // component (OpFinal's means, OpZout's projection into the user layout)
+        double *zf = (double *)w.x;
+        for (int32_t j = 0; j < k; ++j) {
+            const double *rb = rb_all + (size_t)j * rbs;
+            NVD_TRY_CUDA(cudaMemsetAsync(zf, 0, (size_t)g->n * 8, s));
+            k_elim_put_keep<<<(int)std::min<int64_t>((K + 255) / 256, 4096), 256, 0, s>>>(
+                K, E.keep.as<int32_t>(), zred + (size_t)j * K, zf);
+            note_launch();
+            for (size_t t = E.round_ptr.size() - 1; t-- > 0;) {
+                const int64_t r0 = E.round_ptr[t], r1 = E.round_ptr[t + 1];
+                if (r1 <= r0) continue;
+                k_elim_back<<<(int)std::min<int64_t>((r1 - r0 + 255) / 256, 4096), 256, 0, s>>>(
+                    r0, r1, E.rec_v.as<int32_t>(), E.rec_d.as<double>(), E.rec_t0.as<int32_t>(),
+                    E.rec_t1.as<int32_t>(), E.rec_f0.as<double>(), E.rec_f1.as<double>(), rb, zf);
+                note_launch();
+            }
+            NVD_TRY_CUDA(cudaGetLastError());
+            c.own0 = Owner{(const char *)x + (size_t)j * g->n * xsz, (const char *)y + (size_t)j * g->n * xsz,
+                           (char *)z_out + (size_t)j * g->n * xsz, 0, g->n, 1, 0, g->nseg, 0};
+            if (g->n_singleton > 0)
+                NVD_TRY_CUDA(cudaMemsetAsync((char *)z_out + (size_t)j * g->n * xsz, 0, (size_t)g->n * xsz, s));
+            dev::OpFinal<double, 1> of;
+            of.x = zf; of.delta = w.delta;
+            of.fin.KT = 1; of.fin.set_d2 = false;
+            NVD_TRY((launch_vec<double, 1>(c, of, s)));
+            if (xdt == NVD_F64) {
+                dev::OpZout<double, double, 1> oz;
+                oz.src = zf; oz.meanv = c.meanx;
+                NVD_TRY((launch_vec<double, 1>(c, oz, s)));
+            } else {
+                dev::OpZout<double, float, 1> oz;
+                oz.src = zf; oz.meanv = c.meanx;
+                NVD_TRY((launch_vec<double, 1>(c, oz, s)));
+            }
+        }
     }
     const bool d2_dev = o.flags & NVD_SOLVE_D2_DEVICE;
     k_elim_add<<<(k + 127) / 128, 128, 0, s>>>(k, d2r, ex, d2_dev ? d2_out : d2f);
@@ -510,7 +584,8 @@ extern "C" int nvd_eliminate_host(int64_t n, const int64_t *rowptr, const int32_
 extern "C" int nvd_eliminate_host_program(int64_t n, const int64_t *rowptr, const int32_t *colidx,
                                           const double *w, int64_t *counts, int32_t *rec_v, double *rec_d,
                                           int64_t *round_ptr, int64_t *rin_ptr, int32_t *rin_src, double *rin_f,
-                                          int32_t *keep, int64_t *kin_ptr, int32_t *kin_src, double *kin_f) {
+                                          int32_t *keep, int64_t *kin_ptr, int32_t *kin_src, double *kin_f,
+                                          int32_t *rec_t0, int32_t *rec_t1, double *rec_f0, double *rec_f1) {
     clear_error();
     if (n < 1 || !rowptr || !counts || (rowptr[n] > 0 && (!colidx || !w))) {
         set_error("nvd_eliminate_host_program: invalid argument");
@@ -525,8 +600,12 @@ extern "C" int nvd_eliminate_host_program(int64_t n, const int64_t *rowptr, cons
         counts[3] = (int64_t)er.kin_src.size();
         counts[4] = (int64_t)er.round_ptr.size() - 1;
         if (!rec_v || !rec_d || !round_ptr || !rin_ptr || !rin_src || !rin_f || !keep || !kin_ptr || !kin_src ||
-            !kin_f)
+            !kin_f || !rec_t0 || !rec_t1 || !rec_f0 || !rec_f1)
             return NVD_OK;
+        std::copy(er.rec_t0.begin(), er.rec_t0.end(), rec_t0);
+        std::copy(er.rec_t1.begin(), er.rec_t1.end(), rec_t1);
+        std::copy(er.rec_f0.begin(), er.rec_f0.end(), rec_f0);
+        std::copy(er.rec_f1.begin(), er.rec_f1.end(), rec_f1);
         std::copy(er.rec_v.begin(), er.rec_v.end(), rec_v);
         std::copy(er.rec_d.begin(), er.rec_d.end(), rec_d);
         std::copy(er.round_ptr.begin(), er.round_ptr.end(), round_ptr);

@@ -133,14 +133,15 @@ def program(lib, g):
     ci = np.ascontiguousarray(g.colidx, np.int32)
     w = np.ascontiguousarray(g.w, np.float64)
     cnt = np.zeros(5, np.int64)
-    null = [None] * 10
+    null = [None] * 14
     assert lib.nvd_eliminate_host_program(ctypes.c_int64(n), rp.ctypes.data, ci.ctypes.data, w.ctypes.data,
                                           cnt.ctypes.data, *null) == 0
     R, K, NR, NK, T = (int(v) for v in cnt)
     a = dict(rec_v=np.zeros(max(R, 1), np.int32), rec_d=np.zeros(max(R, 1)), round_ptr=np.zeros(T + 1, np.int64),
              rin_ptr=np.zeros(R + 1, np.int64), rin_src=np.zeros(max(NR, 1), np.int32), rin_f=np.zeros(max(NR, 1)),
              keep=np.zeros(K, np.int32), kin_ptr=np.zeros(K + 1, np.int64), kin_src=np.zeros(max(NK, 1), np.int32),
-             kin_f=np.zeros(max(NK, 1)))
+             kin_f=np.zeros(max(NK, 1)), rec_t0=np.zeros(max(R, 1), np.int32), rec_t1=np.zeros(max(R, 1), np.int32),
+             rec_f0=np.zeros(max(R, 1)), rec_f1=np.zeros(max(R, 1)))
     assert lib.nvd_eliminate_host_program(ctypes.c_int64(n), rp.ctypes.data, ci.ctypes.data, w.ctypes.data,
                                           cnt.ctypes.data, *[a[k].ctypes.data for k in a]) == 0
     return R, K, T, a
@@ -156,7 +157,20 @@ def forward(R, K, T, a, b):
     bk = np.array([b[a["keep"][i]] + np.dot(a["kin_f"][a["kin_ptr"][i]:a["kin_ptr"][i + 1]],
                                              rb[a["kin_src"][a["kin_ptr"][i]:a["kin_ptr"][i + 1]]])
                    for i in range(K)])
-    return bk, float(np.sum(rb ** 2 / a["rec_d"][:R])) if R else 0.0
+    return bk, (float(np.sum(rb ** 2 / a["rec_d"][:R])) if R else 0.0), rb
+
+
+def backward(n, R, K, T, a, rb, zk):
+    """The device back-substitution, last round first, written out."""
+    z = np.zeros(n)
+    z[a["keep"]] = zk
+    for t in range(T - 1, -1, -1):
+        for r in range(a["round_ptr"][t], a["round_ptr"][t + 1]):
+            v = rb[r] / a["rec_d"][r] + a["rec_f0"][r] * z[a["rec_t0"][r]]
+            if a["rec_t1"][r] >= 0:
+                v += a["rec_f1"][r] * z[a["rec_t1"][r]]
+            z[a["rec_v"][r]] = v
+    return z
 
 
 @pytest.mark.parametrize("model,deg", [("er", 2), ("ws", 2), ("ba", 2), ("sbm", 2), ("er", 4)])
@@ -183,12 +197,18 @@ def test_program_gives_the_full_graph_d2(lib, model, deg):
     X, Y = rng.random((4, g.n)), rng.random((4, g.n))
     want = dense.ge_d2_eig(g.n, g.rowptr, g.colidx, g.w, X, Y)
     comp, c = dense.components(g.n, g.rowptr, g.colidx)
+    zwant = dense.ge_z_dense(g.n, g.rowptr, g.colidx, g.w, X, Y)
     for j in range(4):
         b = dense.project_mean_zero(X[j] - Y[j], comp, c)
-        bk, extra = forward(R, K, T, a, b)
+        bk, extra, rb = forward(R, K, T, a, b)
         d2_red = 0.0 if red is None else float(dense.ge_d2_eig(K, red.rowptr, red.colidx, red.w,
                                                                bk[None], np.zeros((1, K)))[0])
         assert d2_red + extra == pytest.approx(want[j], rel=1e-10)
+        # z: reduced solution on the kept nodes, back-substitution, mean-zero per component
+        zk = np.zeros(K) if red is None else dense.ge_z_dense(K, red.rowptr, red.colidx, red.w, bk[None],
+                                                              np.zeros((1, K)))[0]
+        z = dense.project_mean_zero(backward(g.n, R, K, T, a, rb, zk), comp, c)
+        assert np.max(np.abs(z - zwant[j])) <= 1e-9 * np.max(np.abs(zwant[j]))
 
 
 def csr_dense(K, rrp, rci, rw):

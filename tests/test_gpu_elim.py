@@ -1,9 +1,9 @@
 """Solves on the reduced graph after exact degree-1/2 elimination
 (nvd_graph_eliminate + NVD_SOLVE_ELIMINATE): d^2 must match the oracle on the full
-graph (FP64 1e-8, FP32 1e-4, MIXED 1e-8), including disconnected graphs with
-isolated nodes in a shuffled node order, with fewer PCG iterations on the sparse
-families where Jacobi PCG is slow (none at all once a graph reduces to one node
-per component)."""
+graph (FP64 1e-8, FP32 1e-4, MIXED 1e-8) and z_out (back-substitution) the dense
+oracle's z, including disconnected graphs with isolated nodes in a shuffled node
+order, with fewer PCG iterations on the sparse families where Jacobi PCG is slow
+(none at all once a graph reduces to one node per component)."""
 import numpy as np
 import pytest
 
@@ -106,19 +106,21 @@ def test_shuffled_disconnected_graph_with_isolated_nodes(nvd, xdtype):
     lab = rng.permutation(n)
     g = synth.csr_from_edges(n, lab[u0.eu], lab[u0.ev], u0.ew)
     X, Y = rng.random((13, n)), rng.random((13, n))
-    want = dense.ge_d2_eig(g.n, g.rowptr, g.colidx, g.w, X.astype(np.float64), Y.astype(np.float64))
     G = nvd.Graph.from_csr(g)
     info = G.eliminate()
     assert info["n_kept"] < n
+    npdt = np.float32 if xdtype == torch.float32 else np.float64       # the inputs as the GPU sees them
+    X64, Y64 = X.astype(npdt).astype(np.float64), Y.astype(npdt).astype(np.float64)
+    want = dense.ge_d2_eig(g.n, g.rowptr, g.colidx, g.w, X64, Y64)
+    zwant = dense.ge_z_dense(g.n, g.rowptr, g.colidx, g.w, X64, Y64)
     for kw in (dict(single_rhs=True), dict(kt=4)):
-        d2 = nvd.ge_distance(G, torch.as_tensor(X, dtype=xdtype, device=DEV),
-                             torch.as_tensor(Y, dtype=xdtype, device=DEV), rtol=1e-12, eliminate=True, **kw)
-        if xdtype == torch.float32:
-            want32 = dense.ge_d2_eig(g.n, g.rowptr, g.colidx, g.w, X.astype(np.float32).astype(np.float64),
-                                     Y.astype(np.float32).astype(np.float64))
-            assert rel(d2.cpu().numpy(), want32) < 1e-8
-        else:
-            assert rel(d2.cpu().numpy(), want) < 1e-8
+        d2, z = nvd.ge_distance(G, torch.as_tensor(X, dtype=xdtype, device=DEV),
+                                torch.as_tensor(Y, dtype=xdtype, device=DEV), rtol=1e-12, eliminate=True,
+                                return_z=True, **kw)
+        assert rel(d2.cpu().numpy(), want) < 1e-8
+        # z by back-substitution, mean-zero per component, in the user's node order
+        ztol = 1e-6 if xdtype == torch.float32 else 1e-8      # z_out is stored in the dtype of x
+        assert np.max(np.abs(z.cpu().numpy().astype(np.float64) - zwant)) <= ztol * np.max(np.abs(zwant))
 
 
 def test_nothing_to_eliminate_and_invalid_uses(nvd):
@@ -133,10 +135,6 @@ def test_nothing_to_eliminate_and_invalid_uses(nvd):
     assert info["n_eliminated"] == 0 and info["rounds"] == 0
     d2 = nvd.ge_distance(G, on(X), on(Y), rtol=1e-12, eliminate=True).cpu().numpy()
     assert rel(d2, nvd.ge_distance(G, on(X), on(Y), rtol=1e-12).cpu().numpy()) < 1e-10
-    for kw in (dict(return_z=True), ):
-        with pytest.raises(nvd.NvdError) as e:
-            nvd.ge_distance(G, on(X), on(Y), eliminate=True, **kw)
-        assert e.value.status == 1
     with pytest.raises(nvd.NvdError) as e:                      # host inputs
         nvd.ge_distance(G, X, Y, eliminate=True)
     assert e.value.status == 1
