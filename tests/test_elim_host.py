@@ -216,3 +216,36 @@ def csr_dense(K, rrp, rci, rw):
     for i in range(K):
         A[i, rci[rrp[i]:rrp[i + 1]]] = rw[rrp[i]:rrp[i + 1]]
     return A
+
+
+def test_random_small_graphs_property(lib):
+    """Hypothesis: random weighted graphs on up to 14 nodes (any density, isolated
+    nodes, several components): the reduced graph is the Schur complement and the
+    program reproduces the dense d^2."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=150, deadline=None, derandomize=True)
+    @hyp.given(st.integers(2, 14), st.floats(0.05, 0.9), st.integers(0, 2 ** 31 - 1))
+    def check(n, p, seed):
+        rng = np.random.default_rng(seed)
+        eu, ev = synth.random_gnp_small(n, p, rng)
+        g = synth.csr_from_edges(n, eu, ev, rng.uniform(0.3, 3.0, len(eu)))
+        keep, rrp, rci, rw, _ = eliminate(lib, g)
+        schur_check(g, keep, rrp, rci, rw)
+        R, K, T, a = program(lib, g)
+        comp, c = dense.components(g.n, g.rowptr, g.colidx)
+        X, Y = rng.random((1, n)), rng.random((1, n))
+        want = dense.ge_d2_eig(g.n, g.rowptr, g.colidx, g.w, X, Y)[0]
+        b = dense.project_mean_zero(X[0] - Y[0], comp, c)
+        bk, extra, _ = forward(R, K, T, a, b)
+        A = csr_dense(K, rrp, rci, rw)
+        if rrp[-1]:
+            iu = np.nonzero(np.triu(A))
+            red = synth.csr_from_edges(K, iu[0], iu[1], A[iu])
+            d2r = float(dense.ge_d2_eig(K, red.rowptr, red.colidx, red.w, bk[None], np.zeros((1, K)))[0])
+        else:
+            d2r = 0.0
+        assert d2r + extra == pytest.approx(want, rel=1e-9, abs=1e-12)
+
+    check()
