@@ -315,8 +315,9 @@ int nvd_ge_distance_warm(nvd_graph_t g, int32_t k, const void *x, const void *y,
  *           for u != v in different components (or an isolated node), which
  *           are not solved.
  *   stats   optional [k] host array (iters 0 for pairs that were not solved).
- * opts as for nvd_ge_distance; NVD_SOLVE_D2_DEVICE and NVD_SOLVE_HOST_INPUTS are
- * invalid here.  Synchronous.
+ * opts as for nvd_ge_distance (NVD_SOLVE_ELIMINATE: on the handle's reduced
+ * graph); NVD_SOLVE_D2_DEVICE and NVD_SOLVE_HOST_INPUTS are invalid here.
+ * Synchronous.
  * Errors: NVD_ERR_INVALID_ARG (NULL pointer, k < 0, an id outside [0, n), bad
  * opts), NVD_ERR_NOT_CONVERGED / NVD_ERR_NUMERIC (every output still written),
  * NVD_ERR_OOM, NVD_ERR_CUDA.

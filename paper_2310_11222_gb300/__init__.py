@@ -392,7 +392,8 @@ def ge_distance(graph: Graph, x, y, *, mode: int = MODE_FP64, rtol: Optional[flo
 
 def effective_resistance(graph: Graph, u, v, *, mode: int = MODE_FP64, rtol: Optional[float] = None,
                          d2_rtol: float = 1e-8, max_iter: int = 10000, kt: int = 0, persistent: bool = False,
-                         d2_stop: bool = False, return_stats: bool = False, allow_not_converged: bool = False):
+                         d2_stop: bool = False, eliminate: bool = False, return_stats: bool = False,
+                         allow_not_converged: bool = False):
     """Effective resistances R(u_j, v_j) = (e_u - e_v)^T L^+ (e_u - e_v) for node-id
     sequences u, v of equal length: 0 where u = v, inf across components.
     Returns a float64 numpy array."""
@@ -409,6 +410,8 @@ def effective_resistance(graph: Graph, u, v, *, mode: int = MODE_FP64, rtol: Opt
         o.flags |= SOLVE_PERSISTENT
     if d2_stop:
         o.flags |= SOLVE_D2_STOP
+    if eliminate:
+        o.flags |= SOLVE_ELIMINATE
     r = np.empty(k, np.float64)
     stats = (SolveStats * max(k, 1))()
     torch = _torch()

@@ -34,9 +34,10 @@ int ge_distance_internal(nvd_graph_t g, int32_t k, const void *x, const void *y,
                          const nvd_solve_opts *opts, double *d2_out, cudaStream_t s);
 // nvd_ge_distance with NVD_SOLVE_ELIMINATE: degree-1/2 nodes eliminated exactly,
 // PCG on the reduced graph (elim.cu).
+// idx: x, y are [k] device int32 node ids (indicator pairs), as in the resistance calls.
 int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdt,
                   const nvd_solve_opts *opts, double *d2_out, void *z_out, nvd_solve_stats *stats,
-                  cudaStream_t s);
+                  cudaStream_t s, bool idx = false);
 // y = L x for one contiguous column (internal order), dtype = F32 or F64.
 int run_apply(nvd_graph_s *g, const Ctx &c, const void *x, void *y, int dtype, cudaStream_t s);
 

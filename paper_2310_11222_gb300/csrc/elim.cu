@@ -363,7 +363,7 @@ static int build_state(nvd_graph_s *g, cudaStream_t s) {
 
 int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_t xdt,
                   const nvd_solve_opts *opts, double *d2_out, void *z_out, nvd_solve_stats *stats,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool idx) {
     if (!g || k < 0 || (xdt != NVD_F32 && xdt != NVD_F64)) {
         set_error("nvd_ge_distance: invalid argument");
         return NVD_ERR_INVALID_ARG;
@@ -412,10 +412,13 @@ int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     double *d2r = ex + k, *d2f = ex + 2 * k, *part = ex + 3 * k;
     NVD_TRY_CUDA(cudaMemsetAsync(zero, 0, (size_t)k * K * 8, s));
     const size_t xsz = xdt == NVD_F64 ? 8 : 4;
+    // pair j's inputs: [n] vectors of the x type, or (idx) one int32 node id each
+    auto px = [&](const void *p, int32_t j) -> const void * {
+        return idx ? (const void *)((const int32_t *)p + j) : (const void *)((const char *)p + (size_t)j * g->n * xsz);
+    };
     for (int32_t j = 0; j < k; ++j) {
         double *rb = rb_all + (z_out ? (size_t)j * rbs : 0);
-        c.own0 = Owner{(const char *)x + (size_t)j * g->n * xsz, (const char *)y + (size_t)j * g->n * xsz,
-                       nullptr, 0, g->n, 1, 0, g->nseg, 0};
+        c.own0 = Owner{px(x, j), px(y, j), nullptr, 0, g->n, 1, 0, g->nseg, idx ? 1 : 0};
         c.owners = nullptr;
         c.n_owner = 1;
         NVD_TRY_CUDA(cudaMemsetAsync(w.delta, 0, (size_t)g->n * 8, s));
@@ -494,8 +497,8 @@ int elim_distance(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
                 note_launch();
             }
             NVD_TRY_CUDA(cudaGetLastError());
-            c.own0 = Owner{(const char *)x + (size_t)j * g->n * xsz, (const char *)y + (size_t)j * g->n * xsz,
-                           (char *)z_out + (size_t)j * g->n * xsz, 0, g->n, 1, 0, g->nseg, 0};
+            c.own0 = Owner{px(x, j), px(y, j), (char *)z_out + (size_t)j * g->n * xsz, 0, g->n, 1, 0, g->nseg,
+                           idx ? 1 : 0};
             if (g->n_singleton > 0)
                 NVD_TRY_CUDA(cudaMemsetAsync((char *)z_out + (size_t)j * g->n * xsz, 0, (size_t)g->n * xsz, s));
             dev::OpFinal<double, 1> of;

@@ -361,8 +361,11 @@ int resistance_impl(nvd_graph_t g, int32_t k, const int32_t *u, const int32_t *v
     NVD_TRY_CUDA(cudaMemcpyAsync(ids + m, sv.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
     std::vector<double> r(m);
     std::vector<nvd_solve_stats> sst(stats ? m : 0);
-    const int rc = distance_impl(g, m, ids, ids + m, NVD_F64, &o, r.data(), nullptr, stats ? sst.data() : nullptr,
-                                 s, true);
+    const int rc = (o.flags & NVD_SOLVE_ELIMINATE)
+                       ? elim_distance(g, m, ids, ids + m, NVD_F64, &o, r.data(), nullptr,
+                                       stats ? sst.data() : nullptr, s, true)
+                       : distance_impl(g, m, ids, ids + m, NVD_F64, &o, r.data(), nullptr,
+                                       stats ? sst.data() : nullptr, s, true);
     if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED && rc != NVD_ERR_NUMERIC) return rc;
     for (int32_t i = 0; i < m; ++i) {
         r_out[where[i]] = r[i];

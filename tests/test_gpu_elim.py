@@ -138,3 +138,32 @@ def test_nothing_to_eliminate_and_invalid_uses(nvd):
     with pytest.raises(nvd.NvdError) as e:                      # host inputs
         nvd.ge_distance(G, X, Y, eliminate=True)
     assert e.value.status == 1
+
+
+def test_effective_resistance_on_the_reduced_graph(nvd):
+    """Node-id pairs through the eliminated graph: a weighted tree, a cycle with
+    pendant paths and an ER graph of mean degree 3 with isolated nodes, against
+    the dense oracle (0 on the diagonal, inf across components)."""
+    rng = np.random.default_rng(23)
+    pu, cv = synth.random_tree(80, rng)
+    eu, ev = synth.cycle_graph(50)
+    er_u, er_v = synth.erdos_renyi_gnm(150, 225, rng)
+    parts = [synth.csr_from_edges(80, pu, cv, rng.uniform(0.5, 2.0, 79)),
+             synth.csr_from_edges(53, np.concatenate([eu, [0, 50, 51]]), np.concatenate([ev, [50, 51, 52]]),
+                                  rng.uniform(0.5, 2.0, 53)),
+             synth.csr_from_edges(150, er_u, er_v, rng.uniform(0.5, 2.0, len(er_u)))]
+    u0, _ = synth.disjoint_union(parts)
+    lab = rng.permutation(u0.n)
+    g = synth.csr_from_edges(u0.n, lab[u0.eu], lab[u0.ev], u0.ew)
+    U = rng.integers(0, g.n, 60)
+    V = rng.integers(0, g.n, 60)
+    V[:3] = U[:3]
+    want = dense.effective_resistance(g.n, g.rowptr, g.colidx, g.w, U, V)
+    G = nvd.Graph.from_csr(g)
+    G.eliminate()
+    R = nvd.effective_resistance(G, U, V, rtol=1e-12, eliminate=True)
+    fin = np.isfinite(want)
+    assert np.array_equal(np.isinf(R), ~fin)
+    assert np.all(R[want == 0] == 0)
+    nz = fin & (want > 0)
+    assert rel(R[nz], want[nz]) < 1e-8
