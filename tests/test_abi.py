@@ -79,3 +79,44 @@ def test_package_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(nvd, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         nvd.load_library()
+
+
+def test_plain_c_program_uses_the_library(lib, tmp_path):
+    """The boundary is a C ABI: a C99 program that includes only include/nvd.h links
+    against libnvd.so and calls its host-only entry points."""
+    import shutil
+    import subprocess
+    import paper_2310_11222_gb300 as nvd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_nvd.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "nvd.h"
+int main(void) {
+    nvd_solve_opts o;
+    nvd_solve_opts_default(&o);
+    if (o.mode != NVD_MODE_FP64 || o.max_iter != 10000) return 2;
+    if (strcmp(nvd_status_string(0), "NVD_OK") != 0) return 3;
+    /* a path 0-1-2-3 eliminates down to one node, with no device work */
+    int64_t rp[5] = {0, 1, 3, 5, 6};
+    int32_t ci[6] = {1, 0, 2, 1, 3, 2};
+    double w[6] = {1, 1, 2, 2, 4, 4};
+    int64_t kept = -1;
+    int32_t rounds = -1;
+    if (nvd_eliminate_host(4, rp, ci, w, &kept, NULL, NULL, NULL, NULL, &rounds) != NVD_OK) return 4;
+    if (kept != 1) return 5;
+    if (nvd_ge_distance(NULL, 1, NULL, NULL, NVD_F64, NULL, NULL, NULL, NULL, NULL) != NVD_ERR_INVALID_ARG) return 6;
+    printf("%s\n", nvd_version());
+    return 0;
+}
+''')
+    exe = tmp_path / "use_nvd"
+    libdir = os.path.dirname(nvd.library_path())
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-L", libdir, "-lnvd", "-Wl,-rpath," + libdir, "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert "sm_103a" in out.stdout
