@@ -16,7 +16,9 @@ for an undirected graph with positive weights.  Two routes:
 * ``oracle.dense`` -- forms L^+ by a dense FP64 symmetric eigendecomposition (the
   costly route the paper replaces, Section 3.1), plus an independent second dense
   route through the grounded Laplacian and a Cholesky factorisation; also the
-  dense gradient of d^2 with respect to the vectors and the edge weights.
+  dense gradient of d^2 with respect to the vectors and the edge weights, the
+  effective resistance of node-id pairs (the GE equation on indicator vectors)
+  and the network variance (1/2) sum_ij p_i p_j R(i, j) of node weights.
 * ``oracle.cg`` -- a plain C FP64 Jacobi-preconditioned conjugate gradient on the
   sparse Laplacian (the "CG" Laplacian solver of Section 3.2 and Table 1), for
   graphs too large for the dense route.
@@ -28,5 +30,6 @@ Readings of points the paper leaves open (each is also listed in the design note
 * disconnected graphs: L^+ annihilates per-component constants, so the result
   is (P delta)^T L^+ (P delta) with P the per-component mean-zero projector;
   exactly c zero eigenvalues are dropped, c = number of connected components;
-* d = sqrt(max(d^2, 0)).
+* d = sqrt(max(d^2, 0));
+* effective resistance between different components: +inf (no current flows).
 """
