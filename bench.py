@@ -221,7 +221,7 @@ def run_other_workload(args, nvd, synth, torch, np, local):
     prof = True
     tuning = None
     if name == "powerlaw":
-        wl = synth.workload_powerlaw()
+        wl = synth.workload_powerlaw(scale=args.scale)
         g = wl.graph
         k = 128
         X, Y = wl.pairs(0, k)
@@ -560,6 +560,8 @@ def main():
                                            "resistance_matrix"],
                     default="er_large",
                     help="er_large (default) is the bench line; the others measure the method's other workloads")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="--workload powerlaw: node-count multiplier (profiling runs on a smaller graph)")
     ap.add_argument("--eliminate", action="store_true",
                     help="--workload powerlaw: eliminate degree-1/2 nodes exactly and solve on the reduced graph")
     ap.add_argument("--sweep", choices=["size", "density"], default=None,

@@ -435,7 +435,10 @@ int nvd_laplacian_apply(nvd_graph_t g, int32_t k, const void *x, void *y, int32_
  * that array and it keeps the last call's contents; calls that overlap on the GPU
  * (different streams, or several threads) race on it and must be serialised by
  * the caller.  The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make that
+ * first call before any stream capture.  A device reset (cudaDeviceReset)
+ * releases the array with the context: after one, this entry point must not be
+ * called again in that process (the kept address would point at freed memory).
  * The work is ordered on `stream` and the call returns without waiting for it.
  */
 int nvd_laplacian_quadform_noalloc(nvd_graph_t g, int32_t k, const double *x, double *y, double *q,

@@ -149,7 +149,10 @@ static int eliminate_low_degree(int64_t n, const int64_t *rowptr, const int32_t 
         }
         out->round_ptr.push_back((int64_t)out->rec_v.size());
     }
-    // reduced graph on the kept nodes (parallel entries merged)
+    // reduced graph on the kept nodes (parallel entries merged).  Rows a and c hold
+    // the same multiset of conductances for their pair (every entry was added to
+    // both rows), so sorting by (neighbour, conductance) and adding in that order
+    // gives bitwise equal w_ac and w_ca: the reduced Laplacian is exactly symmetric.
     std::vector<int32_t> kidx(n, -1);
     for (int64_t v = 0; v < n; ++v)
         if (alive[v]) {
@@ -162,7 +165,8 @@ static int eliminate_low_degree(int64_t n, const int64_t *rowptr, const int32_t 
         row.clear();
         for (const E &x : adj[v])
             if (alive[x.u] && x.u != v) row.push_back({kidx[x.u], x.w});
-        std::sort(row.begin(), row.end(), [](const E &a, const E &b) { return a.u < b.u; });
+        std::sort(row.begin(), row.end(),
+                  [](const E &a, const E &b) { return a.u < b.u || (a.u == b.u && a.w < b.w); });
         for (size_t q = 0; q < row.size(); ++q) {
             if (q > 0 && row[q].u == row[q - 1].u) {
                 out->red_w.back() += row[q].w;
@@ -352,7 +356,8 @@ static int build_state(nvd_graph_s *g, cudaStream_t s) {
     NVD_TRY(upload_vec(st->rec_f1, er.rec_f1, s));
     NVD_TRY_CUDA(cudaStreamSynchronize(s));
     // the reduced graph: nodes = kept nodes of g's internal order (still
-    // component-contiguous), symmetric by construction; none when no edge is left
+    // component-contiguous), bitwise symmetric by construction (parallel entries
+    // merged in a fixed order both rows share); none when no edge is left
     // (every component went down to one node: d^2 is the eliminated terms alone)
     if (st->red_nnz > 0)
         NVD_TRY(nvd_graph_create(&st->red, st->n_keep, st->red_nnz, er.red_rowptr.data(), er.red_col.data(),

@@ -50,7 +50,8 @@ def schur_check(g, keep, rrp, rci, rw):
             assert rci[e] != i
             Lr[i, rci[e]] -= rw[e]
             Lr[i, i] += rw[e]
-    assert np.allclose(Lr, Lr.T, rtol=0, atol=1e-13)
+    A = csr_dense(K, rrp, rci, rw)
+    assert np.array_equal(A, A.T)          # bitwise: w_ac and w_ca merged in the same order
     assert np.max(np.abs(S - Lr)) <= 1e-12 * max(1.0, np.max(np.abs(L)))
     return Lr
 

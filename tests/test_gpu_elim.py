@@ -12,11 +12,7 @@ from oracle import cg as ocg
 from oracle import dense
 
 torch = pytest.importorskip("torch")
-# The device path of the elimination (forward-pass kernels, reduced solve) has not
-# run on a GPU yet; the host elimination and the exact program those kernels run
-# are checked on the host in test_elim_host.py.  Remove the skip once it has run.
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="elimination device path not yet run on a GPU (host side: test_elim_host.py)")]
+pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 

@@ -3,9 +3,11 @@ cannot allocate device memory when they call: its partial sums live in a fixed
 device array inside the library instead of handle workspace).
 
 Called through the C ABI twice in a row and compared with the existing entry
-point nvd_laplacian_apply (y = L x) and with x^T y from that output.  This file
-is collected last so a run that stops at the first failure has run every other
-test first.
+point nvd_laplacian_apply (y = L x), with x^T y from that output and with the
+oracle's dense Laplacian (y = L x, q = x^T L x in FP64 on the host).  A larger
+graph reaches the launch's block cap (every partial-sum slot in use) with the
+maximum of 32 columns and no y.  This file is collected last so a run that stops
+at the first failure has run every other test first.
 """
 import ctypes
 
@@ -13,6 +15,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import dense
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -67,6 +70,34 @@ def test_noalloc_matches_existing_entry_point_twice(nvd, gi):
         torch.cuda.synchronize()
         assert float((y - y_ref).abs().max()) <= 1e-12 * scale
         assert torch.allclose(q, q_ref, rtol=1e-10, atol=1e-12 * float(q_ref.abs().max()))
+    # the oracle's dense L (FP64, host): y = L x and q = x^T L x column by column
+    L = dense.laplacian_dense(g.n, g.rowptr, g.colidx, g.w.astype(np.float64))
+    Xh = X.cpu().numpy()
+    y_or = Xh @ L                                                      # L is symmetric
+    q_or = np.einsum("kn,kn->k", Xh, y_or)
+    assert np.max(np.abs(y.cpu().numpy() - y_or)) <= 1e-12 * np.max(np.abs(y_or))
+    assert np.max(np.abs(q.cpu().numpy() - q_or) / np.abs(q_or)) <= 1e-10
+
+
+def test_noalloc_at_the_block_cap_with_32_columns_and_no_y(nvd):
+    """n = 50,000 (BA m = 4): the launch is capped (1024 blocks, or 8 per SM), every
+    one of the 32 partial-sum columns is in use and y is NULL; q against x^T (L x)
+    of the existing entry point, twice in a row."""
+    r = np.random.default_rng(41)
+    eu, ev = synth.barabasi_albert(50_000, 4, r)
+    g = synth.csr_from_edges(50_000, eu, ev, r.uniform(0.5, 2.0, size=len(eu)))
+    G = nvd.Graph.from_csr(g)
+    lib = nvd.load_library()
+    k = 32
+    X = torch.as_tensor(r.standard_normal((k, g.n)), device=DEV)
+    q_ref = (X * nvd.laplacian_apply(G, X)).sum(dim=1)
+    for _ in range(2):
+        q = torch.full((k,), float("nan"), dtype=torch.float64, device=DEV)
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        rc = lib.nvd_laplacian_quadform_noalloc(G.handle, k, X.data_ptr(), None, q.data_ptr(), stream)
+        assert rc == 0, lib.nvd_last_error()
+        torch.cuda.synchronize()
+        assert torch.allclose(q, q_ref, rtol=1e-10, atol=0.0)
 
 
 def test_noalloc_rejects_too_many_columns(nvd):
