@@ -25,9 +25,9 @@ int g_every = 1;     // time one SpMV launch in g_every
 int64_t g_seq = 0;   // SpMV launches seen while enabled
 std::vector<cudaEvent_t> g_pool;
 std::vector<Pending> g_pending;
-constexpr int NCLS = 2;
-int64_t g_launches[NCLS] = {0, 0};
-double g_ms[NCLS] = {0.0, 0.0}, g_bytes[NCLS] = {0.0, 0.0};
+constexpr int NCLS = 3;   // 0 the CG SpMV/SpMM, 1 the vector passes, 2 the FP64 refinement residual SpMM
+int64_t g_launches[NCLS] = {0, 0, 0};
+double g_ms[NCLS] = {0.0, 0.0, 0.0}, g_bytes[NCLS] = {0.0, 0.0, 0.0};
 
 cudaEvent_t take_event() {
     if (!g_pool.empty()) {

@@ -105,24 +105,31 @@ __device__ void persistent_solve(const Ctx &c, const PersistArgs &a, char *smem)
     ou.q = q;
     ou.u = u;
     ou.fin.KT = KT;
-    OpDir<TV, KT, LdCoh> od;
+    OpResid<TV, KT, LdCoh> orr;
+    orr.r = r;
+    orr.q = q;
+    orr.fin.KT = KT;
+    OpStepDir<TV, KT, LdCoh> od;
+    od.x = x;
     od.r = r;
     od.p = p;
-    od.u = u;
     // the device deactivates every column by max_iter, so this loop is bounded;
     // a.fold: two phases per iteration (SpMV on u with the direction update folded
-    // in, then the x/r/u update), else three (SpMV on p, update, direction)
+    // in, then the x/r/u update), else three (SpMV on p, residual, direction with
+    // the x step -- always run, it takes the last step of a converged column)
     for (int it = 0; it <= c.max_iter; ++it) {
         if (__ldcg(c.n_active) == 0) break;
-        if (a.fold)
+        if (a.fold) {
             spmm_phase<TV, TW, TA, KT>(c, epd, u, q, smem);
-        else
-            spmm_phase<TV, TW, TA, KT>(c, epi, p, q, smem);
+            if (!grid_sync(c)) return;
+            vec_phase<TV, KT, decltype(ou), PU>(c, ou, smem);
+            if (!grid_sync(c)) return;
+            continue;
+        }
+        spmm_phase<TV, TW, TA, KT>(c, epi, p, q, smem);
         if (!grid_sync(c)) return;
-        vec_phase<TV, KT, decltype(ou), PU>(c, ou, smem);
+        vec_phase<TV, KT, decltype(orr), PU>(c, orr, smem);
         if (!grid_sync(c)) return;
-        if (a.fold) continue;
-        if (__ldcg(c.n_active) == 0) break;
         vec_phase<TV, KT, decltype(od), PU>(c, od, smem);
         if (!grid_sync(c)) return;
     }

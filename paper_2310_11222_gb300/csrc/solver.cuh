@@ -182,15 +182,16 @@ inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixe
 
 // ------------------------------------------------------------------ launchers
 
+// cls: timer class (0 the CG iteration's SpMV/SpMM, 2 the refinement residual).
 template <class TV, class TW, class TA, int KT, class Epi>
 inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cudaStream_t s,
-                       double bytes) {
+                       double bytes, int cls = 0) {
     if (c.n_sblk == 0) return NVD_OK;
     if (c.sl_h != sp_slice_rows(KT, (int)sizeof(TV))) {
         set_error("internal: SpMV plan built for another tile width or precision");
         return NVD_ERR_UNSUPPORTED;
     }
-    const bool prof = prof_enabled() && prof_begin(s);
+    const bool prof = prof_enabled() && prof_begin(s, cls);
     NVD_TRY_CUDA(launch_dependent(k_spmm<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, s, c, epi, src, dst));
     note_launch();
     if (prof) prof_end(s, bytes);
@@ -247,7 +248,9 @@ int pcg_loop(const Ctx &c, TV *x, TV *r, TV *p, TV *q, TV *u, bool fold, int max
     NVD_TRY(pb.init());
     // fold: two kernels per iteration, the SpMV on u = D^-1 r with the direction
     // update folded into it (EpiLapDir), then the x/r/u update.  Otherwise three:
-    // the SpMV on p, the x/r/u update and the direction pass p = u + beta p.
+    // the SpMV on p, the residual pass r -= alpha q and the direction pass with the
+    // x step, x += alpha p, p = D^-1 r + beta p (every iteration's residual pass is
+    // followed by its direction pass, so the last x step is always taken).
     dev::EpiLap epi;
     epi.fin.KT = KT;
     dev::EpiLapDir<TV, KT> epd;
@@ -256,8 +259,11 @@ int pcg_loop(const Ctx &c, TV *x, TV *r, TV *p, TV *q, TV *u, bool fold, int max
     dev::OpUpdate<TV, KT> ou;
     ou.x = x; ou.r = r; ou.p = p; ou.q = q; ou.u = u;
     ou.fin.KT = KT;
-    dev::OpDir<TV, KT> od;
-    od.r = r; od.p = p; od.u = u;
+    dev::OpResid<TV, KT> orr;
+    orr.r = r; orr.q = q;
+    orr.fin.KT = KT;
+    dev::OpStepDir<TV, KT> od;
+    od.x = x; od.r = r; od.p = p;
     const int C = std::max(1, check_every);
     int64_t issued = 0;
     int batch = 0;
@@ -270,7 +276,7 @@ int pcg_loop(const Ctx &c, TV *x, TV *r, TV *p, TV *q, TV *u, bool fold, int max
                 NVD_TRY((launch_vec<TV, KT>(c, ou, s)));
             } else {
                 NVD_TRY((launch_spmm<TV, TW, TA, KT>(c, epi, p, q, s, bytes)));
-                NVD_TRY((launch_vec<TV, KT>(c, ou, s)));
+                NVD_TRY((launch_vec<TV, KT>(c, orr, s)));
                 NVD_TRY((launch_vec<TV, KT>(c, od, s)));
             }
         }
@@ -332,7 +338,7 @@ int tile_pcg(nvd_graph_s *g, Ctx c, SolveWs &w, const nvd_solve_opts &o, const T
             dev::EpiResid er;
             er.delta = delta;
             er.fin.KT = KT;
-            NVD_TRY((launch_spmm<double, TW, double, KT>(c, er, x, q, s, spmm_bytes(g, KT, 8, sizeof(TW), 8))));
+            NVD_TRY((launch_spmm<double, TW, double, KT>(c, er, x, q, s, spmm_bytes(g, KT, 8, sizeof(TW), 8), 2)));
             NVD_TRY_CUDA(cudaMemsetAsync(c.n_active, 0, 4, s));
             dev::OpInit<TV, KT> ow = oi;
             ow.src = q; ow.writeback = nullptr; ow.zero_x = false;
@@ -350,7 +356,7 @@ int tile_pcg(nvd_graph_s *g, Ctx c, SolveWs &w, const nvd_solve_opts &o, const T
             dev::EpiResid er;
             er.delta = delta;
             er.fin.KT = KT;
-            NVD_TRY((launch_spmm<double, TW, double, KT>(c, er, x, q, s, spmm_bytes(g, KT, 8, sizeof(TW), 8))));
+            NVD_TRY((launch_spmm<double, TW, double, KT>(c, er, x, q, s, spmm_bytes(g, KT, 8, sizeof(TW), 8), 2)));
         }
     }
     dev::OpFinal<TV, KT> of;
@@ -435,7 +441,7 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
         dev::EpiResid er;
         er.delta = delta;
         er.fin.KT = KT;
-        NVD_TRY((launch_spmm<double, TWN, double, KT>(cr, er, w.z64, w.r64, s, bytes64)));
+        NVD_TRY((launch_spmm<double, TWN, double, KT>(cr, er, w.z64, w.r64, s, bytes64, 2)));
         k_collect<KT><<<1, 128, 0, s>>>(c, w.res, nullptr, 0);
         note_launch();
         NVD_TRY_CUDA(cudaMemcpyAsync(res.data(), w.res, KT * sizeof(ColResult), cudaMemcpyDeviceToHost, s));

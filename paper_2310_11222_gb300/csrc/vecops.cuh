@@ -13,11 +13,32 @@ namespace dev {
 
 // ------------------------------------------------------------------ vector passes
 
+// Does a segment need this pass?  NEEDS_LIVE: while a column iterates;
+// LIVE_ON_STEP (optional member): while a column has a step to take (alpha != 0);
+// otherwise always.
+template <class Op, class = void> struct LiveOnStep { static constexpr bool value = false; };
+template <class Op> struct LiveOnStep<Op, decltype((void)Op::LIVE_ON_STEP)> {
+    static constexpr bool value = Op::LIVE_ON_STEP;
+};
+template <int KT>
+__device__ __forceinline__ bool seg_stepped(const Ctx &c, int seg) {
+    bool a = false;
+#pragma unroll
+    for (int j = 0; j < KT; ++j) a = a || __ldcg(c.alpha + (int64_t)seg * KT + j) != 0.0;
+    return a;
+}
+template <int KT, class Op>
+__device__ __forceinline__ bool op_live(const Ctx &c, int seg) {
+    if constexpr (LiveOnStep<Op>::value) return seg_stepped<KT>(c, seg);
+    else if constexpr (Op::NEEDS_LIVE) return seg_live<KT>(c, seg);
+    else return true;
+}
+
 // Generic streaming pass over rows [i0, i1) of one segment.  Op provides ND,
-// NEEDS_LIVE, a register type R, setup(c, seg, col0), load(c, i, col0, R&) and
-// apply(c, i, col0, R&, dot) with per-thread partial sums of type Op::D (see DotOf).
-// Each thread handles U lane-vectors per trip with all U loads issued before the
-// first use.
+// NEEDS_LIVE (see op_live), a register type R, setup(c, seg, col0), load(c, i,
+// col0, R&) and apply(c, i, col0, R&, dot) with per-thread partial sums of type
+// Op::D (see DotOf).  Each thread handles U lane-vectors per trip with all U loads
+// issued before the first use.
 template <class TV, int KT, class Op, int U = 4>
 __device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
     constexpr int VEC = VecCfg<TV, KT>::VEC, CG = KT / VEC, ND = Op::ND;
@@ -31,7 +52,7 @@ __device__ void vec_block(const Ctx &c, Op op, int64_t b, char *smem) {
     for (int d = 0; d < (ND > 0 ? ND : 1); ++d)
 #pragma unroll
         for (int v = 0; v < VEC; ++v) dot_zero(dot[d][v]);
-    if (!Op::NEEDS_LIVE || seg_live<KT>(c, seg)) {
+    if (op_live<KT, Op>(c, seg)) {
         op.setup(c, seg, col0);
         const int64_t t1 = blk.i1 * CG;
         for (int64_t t = blk.i0 * CG + threadIdx.x; t < t1; t += (int64_t)NT * U) {
@@ -223,47 +244,90 @@ struct OpUpdate {
     }
 };
 
-// p = D^-1 r + beta p on the columns still iterating (D^-1 r read from u when the
-// update pass stored it: one read and one FP64 multiply fewer per element).
+// The three-kernel iteration moves as few [n][KT] vectors as it can: after the
+// SpMV (q = L p, p^T q) the residual pass only reads r, q and D^-1 and writes r;
+// the direction pass then takes the x step with the p it reads anyway and forms
+// the next direction from r and D^-1 (no stored D^-1 r):
+//     residual pass   r -= alpha q;  r^T D^-1 r, |r|^2          (3 vectors)
+//     direction pass  x += alpha p;  p = D^-1 r + beta p        (5 vectors)
+// against 7 + 3 when the update pass also moves x and stores u = D^-1 r.
+
+// r -= alpha q; r^T D^-1 r and |r|^2 for beta and the convergence test.
 template <class TV, int KT, class LD = LdPlain>
-struct OpDir {
-    static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
+struct OpResid {
+    static constexpr int ND = 2, VEC = VecCfg<TV, KT>::VEC;
     static constexpr bool NEEDS_LIVE = true;
-    struct R { TV r[VEC], p[VEC]; TV di; };
+    struct R { TV r[VEC], q[VEC]; TV di; };
+    typedef typename DotOf<TV>::type D;
+    TV *r;
+    const TV *q;
+    FinBeta fin;
+    TV al[VEC];
+    __device__ void setup(const Ctx &c, int seg, int col0) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) al[v] = (TV)__ldcg(c.alpha + (int64_t)seg * KT + col0 + v);
+    }
+    __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &g) const {
+        const int64_t o = i * KT + col0;
+        ldv<LD, TV, VEC>(r + o, g.r);
+        ldv<LD, TV, VEC>(q + o, g.q);
+        g.di = __ldg(dinv_of<TV>(c) + i);
+    }
+    __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, D (&dot)[2][VEC]) const {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            g.r[v] -= al[v] * g.q[v];
+            const TV uv = g.di * g.r[v];
+            dot_fma(dot[0][v], g.r[v], uv);
+            dot_fma(dot[1][v], g.r[v], g.r[v]);
+        }
+        stv(r + i * KT + col0, g.r);
+    }
+};
+
+// x += alpha p (the step whose alpha the last SpMV set), then p = D^-1 r + beta p
+// on the columns still iterating.  A segment runs this pass while any of its
+// columns has a non-zero alpha -- also when its last column converged in the
+// residual pass just before, whose x step is still due; alpha is 0 for columns
+// that had stopped before the SpMV, so their x and p stay as they are.
+template <class TV, int KT, class LD = LdPlain>
+struct OpStepDir {
+    static constexpr int ND = 0, VEC = VecCfg<TV, KT>::VEC;
+    static constexpr bool NEEDS_LIVE = false;
+    static constexpr bool LIVE_ON_STEP = true;
+    struct R { TV x[VEC], r[VEC], p[VEC]; TV di; };
     typedef double D;
+    TV *x;
     const TV *r;
     TV *p;
-    const TV *u = nullptr;
     FinNone fin;
-    TV be[VEC];
+    TV al[VEC], be[VEC];
     bool act[VEC];
     __device__ void setup(const Ctx &c, int seg, int col0) {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            be[v] = (TV)__ldcg(c.beta + (int64_t)seg * KT + col0 + v);
-            act[v] = __ldcg(c.active + (int64_t)seg * KT + col0 + v) != 0;
+            const int64_t i = (int64_t)seg * KT + col0 + v;
+            al[v] = (TV)__ldcg(c.alpha + i);
+            be[v] = (TV)__ldcg(c.beta + i);
+            act[v] = __ldcg(c.active + i) != 0;
         }
     }
     __device__ __forceinline__ void load(const Ctx &c, int64_t i, int col0, R &g) const {
         const int64_t o = i * KT + col0;
-        if (u) {
-            ldv<LD, TV, VEC>(u + o, g.r);
-            g.di = (TV)1;
-        } else {
-            ldv<LD, TV, VEC>(r + o, g.r);
-            g.di = __ldg(dinv_of<TV>(c) + i);
-        }
+        ldv<LD, TV, VEC>(x + o, g.x);
+        ldv<LD, TV, VEC>(r + o, g.r);
         ldv<LD, TV, VEC>(p + o, g.p);
+        g.di = __ldg(dinv_of<TV>(c) + i);
     }
     __device__ __forceinline__ void apply(const Ctx &, int64_t i, int col0, R &g, double (&)[1][VEC]) const {
-        if (u) {
+        const int64_t o = i * KT + col0;
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) g.p[v] = act[v] ? g.r[v] + be[v] * g.p[v] : g.p[v];
-        } else {
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) g.p[v] = act[v] ? g.di * g.r[v] + be[v] * g.p[v] : g.p[v];
+        for (int v = 0; v < VEC; ++v) {
+            g.x[v] += al[v] * g.p[v];
+            g.p[v] = act[v] ? g.di * g.r[v] + be[v] * g.p[v] : g.p[v];
         }
-        stv(p + i * KT + col0, g.p);
+        stv(x + o, g.x);
+        stv(p + o, g.p);
     }
 };
 
