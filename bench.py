@@ -1,23 +1,28 @@
 #!/usr/bin/env python
 """Throughput of the GE node-vector distance on GB300.
 
-Workload (one "step"): the Erdos-Renyi graph with n = 1,000,000 nodes and
-m = 5,000,000 edges (mean degree 10, largest component), FP64 weights
-Uniform[0.5, 2), and 8 vector pairs whose x and y have Uniform[0,1) values on 1%
-of the nodes, normalised to sum 1.  Each pair is solved on its own (one
-right-hand side at a time) by FP64 Jacobi-PCG to relative residual 1e-10 and
-d^2 = delta^T L^+ delta is returned (Section 3.1 GE equation via the Laplacian
-solve of Section 3.2).  Inputs are seeded and synthetic (no dataset).
+Workload (one "step", the default line): the erased configuration-model graph
+with n = 10,000,000 nodes and a power-law degree sequence (exponent 2.3 on
+[2, 10,000], largest component, lognormal(0,1) FP32 weights) and 128 vector pairs
+whose x and y have Uniform[0,1) values on 0.1% of the nodes, normalised to sum 1.
+All 128 distances d^2 = delta^T L^+ delta (Section 3.1 GE equation via the
+Laplacian solve of Section 3.2) are computed by FP32 block-PCG (32 right-hand
+sides per SpMM) inside an FP64 iterative-refinement loop to d^2 relative change
+1e-8.  Inputs are seeded and synthetic (no dataset).
 
-Metric: GE distances per second (whole job).  Beside it: the live roofline of
-the SpMV kernel (algorithmic bytes / CUDA-event time of its launches in the
+Metric: GE distances per second (whole job).  Beside it: the live roofline of the
+FP32 multi-column SpMM (algorithmic bytes / CUDA-event time of its launches in the
 timed region, against the measured HBM copy bandwidth), the end-to-end rate
-through the C ABI with host buffers, and the oracle (plain FP64 CPU CG) timed
-on this machine's cores.
+through the C ABI with host buffers, the oracle (plain FP64 CPU CG) timed on this
+machine's cores, and the other workloads' headline numbers (the n = 10^6
+Erdos-Renyi graph solved one right-hand side at a time in FP64, the multiple of
+batched mixed precision over it, and the power-law graph after exact elimination
+of its degree-1/2 nodes).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload powerlaw|er_large|batched|grad|resistance|resistance_matrix]
 
-With N > 1 (torchrun, one rank per GPU) every rank solves its own 8 pairs on its
+With N > 1 (torchrun, one rank per GPU) every rank solves its own 128 pairs on its
 own copy of the graph (weak scaling, no data-path collective).
 """
 from __future__ import annotations
@@ -38,6 +43,10 @@ if ROOT not in sys.path:
 
 METRIC = "GE distances/s on 1 GB300 at d² rel.err≤1e-6; SpMV HBM GB/s vs peak"
 UNIT = "distances/s"
+PL_PAIRS = 128         # power-law workload: pairs per step (per rank)
+PL_RTOL_IN = 1e-5      # its inner FP32 solve tolerance
+PL_D2_RTOL = 1e-8      # its refinement stop (relative change of d^2)
+PL_ORACLE_PAIRS = 2    # pairs the oracle solves for the CPU baseline and the error check
 PAIRS_PER_STEP = 8
 RTOL = 1e-10
 CHECK_EVERY = 2   # PCG iterations between the host's convergence polls (polled one batch behind)
@@ -91,20 +100,24 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the sources that decide the SpMV kernel's code and its work layout."""
+SPMV_SOURCES = ("paper_2310_11222_gb300/csrc/kernels.cuh", "paper_2310_11222_gb300/csrc/common.h",
+                "paper_2310_11222_gb300/csrc/solver.cuh", "paper_2310_11222_gb300/csrc/graph.cu")
+SPMM_STREAM_SOURCES = SPMV_SOURCES + ("paper_2310_11222_gb300/csrc/tma.cuh", "paper_2310_11222_gb300/csrc/stream.cuh")
+
+
+def kernel_source_hash(sources=SPMV_SOURCES):
+    """Hash of the sources that decide a kernel's code and its work layout."""
     h = hashlib.sha256()
-    for rel in ("paper_2310_11222_gb300/csrc/kernels.cuh", "paper_2310_11222_gb300/csrc/common.h",
-                "paper_2310_11222_gb300/csrc/solver.cuh", "paper_2310_11222_gb300/csrc/graph.cu"):
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per SpMV launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "spmv_er_large_traffic.txt")
+def ncu_traffic(name="spmv_er_large_traffic.txt", sources=SPMV_SOURCES):
+    """DRAM bytes per launch from a committed ncu summary under profiles/, if it was
+    taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     d = {}
@@ -113,7 +126,7 @@ def ncu_traffic():
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 d[k.strip()] = v.strip()
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash(sources):
         return None
     try:
         return float(d["dram_bytes_per_launch"])
@@ -185,9 +198,10 @@ class ClockSampler:
 
 def cpu_baseline(g, X, Y, budget_s=12.0, max_solves=200):
     """The oracle (plain FP64 CPU Jacobi-PCG, oracle/pcg.c) on this host's cores over a
-    bounded sample of the same pairs (the step's pairs in turn, repeated until about
-    budget_s of CPU work): returns (distances/s, threads, solves, seconds, d2 of the
-    first pass over the pairs)."""
+    bounded sample of the same pairs (the given pairs in turn, repeated until about
+    budget_s of CPU work, every pair at least once): returns (distances/s, threads,
+    solves, seconds, d2 of the first pass over the pairs)."""
+    import numpy as np
     from oracle import cg as ocg
     ocg.build()
     threads = ocg.default_threads()
@@ -197,8 +211,8 @@ def cpu_baseline(g, X, Y, budget_s=12.0, max_solves=200):
     solves = 0
     while solves < max_solves:
         j = solves % k
-        d2, it, rr = ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X[j:j + 1], Y[j:j + 1], rtol=RTOL,
-                                  threads=threads)
+        d2, it, rr = ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), X[j:j + 1], Y[j:j + 1],
+                                  rtol=RTOL, threads=threads)
         if solves < k:
             d2s.append(float(d2[0]))
         solves += 1
@@ -210,56 +224,17 @@ def cpu_baseline(g, X, Y, budget_s=12.0, max_solves=200):
 
 def run_other_workload(args, nvd, synth, torch, np, local):
     """Measurement of the other workloads of the method (not the default bench line):
-    the power-law precision workload (MIXED), the 64-graph batched workload (one
-    persistent graph-captured launch), the differentiation workload (forward +
-    adjoint backward), effective resistances on node-id pairs and the resistance
-    matrix of a node subset.  Same JSON fields as the default line."""
+    the 64-graph batched workload (one persistent graph-captured launch), the
+    differentiation workload (forward + adjoint backward), effective resistances on
+    node-id pairs and the resistance matrix of a node subset.  Same JSON fields as
+    the default line."""
     from oracle import cg as ocg
     dev = torch.device("cuda", local)
     name = args.workload
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     prof = True
     tuning = None
-    if name == "powerlaw":
-        wl = synth.workload_powerlaw(scale=args.scale)
-        g = wl.graph
-        k = 128
-        X, Y = wl.pairs(0, k)
-        G = nvd.Graph.from_csr(g)
-        if not args.no_tune:
-            tuning = G.tune(mode=nvd.MODE_MIXED, k=k)
-        xt, yt = torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)
-        xh, yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()
-        kw = dict(mode=nvd.MODE_MIXED, rtol=1e-5, d2_rtol=1e-8)
-        elim_info = None
-        if args.eliminate:
-            # degree-1/2 nodes eliminated exactly once (set-up, not timed); PCG on the reduced graph
-            elim_info = G.eliminate()
-            kw["eliminate"] = True
-
-        def step():
-            return nvd.ge_distance(G, xt, yt, **kw)
-
-        def step_e2e():
-            xt.copy_(xh, non_blocking=True)
-            yt.copy_(yh, non_blocking=True)
-            return nvd.ge_distance(G, xt, yt, **kw).cpu()
-        h2d, d2h = 2 * X.nbytes, 8 * k
-        cfg = {"workload": "powerlaw: erased configuration model n=1e7, gamma 2.3 on [2, 1e4], largest "
-                           "component, lognormal(0,1) FP32 weights, 128 pairs U[0,1) on 0.1% of nodes; "
-                           "FP32 block-PCG (rtol 1e-5) inside FP64 refinement to d2_rtol 1e-8"
-                           + ("; degree-1/2 nodes eliminated exactly, PCG on the reduced graph" if args.eliminate
-                              else ""),
-               "n": g.n, "nnz": int(g.rowptr[-1]), "pairs_per_step": k, "tuning": tuning,
-               "elimination": elim_info}
-        unit = UNIT
-        dtype = "f32+f64"
-
-        def oracle_sample():
-            t0 = time.perf_counter()
-            ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w.astype(np.float64), X[:1], Y[:1], rtol=RTOL)
-            return 1.0 / (time.perf_counter() - t0), "1 pair, FP64 oracle CG at rtol 1e-10"
-    elif name == "batched":
+    if name == "batched":
         wl = synth.workload_batched()
         graphs = wl.graphs
         X, Y = wl.pairs(0, 32)
@@ -511,28 +486,38 @@ def run_sweep(args, nvd, synth, torch, np, local):
 
 
 def run_reference(args):
-    """Reference arm: the oracle timed as it stands on the host cores."""
+    """Reference arm: the oracle (plain FP64 CPU Jacobi-PCG, oracle/pcg.c) timed as it
+    stands on the host cores, on the same workload as the default line; one step is a
+    bounded sample of it: one pair solved to rtol 1e-10 (rank 0 only)."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
+    import numpy as np
     import synth
     from oracle import cg as ocg
-    wl = synth.workload_er_large()
-    g = wl.graph
-    X, Y = wl.pairs(0, PAIRS_PER_STEP)
+    if args.workload == "er_large":
+        wl = synth.workload_er_large()
+        g = wl.graph
+        per = PAIRS_PER_STEP
+        cfg = workload_config(g, wl.meta["n_generated"])
+    else:
+        wl = synth.workload_powerlaw(scale=args.scale)
+        g = wl.graph
+        per = PL_PAIRS
+        cfg = powerlaw_config(g, wl, args, None, None)
+    X, Y = wl.pairs(0, per)
+    w64 = g.w.astype(np.float64)
     ocg.build()
     threads = ocg.default_threads()
-    # one step = one pair of the workload (a bounded sample), oracle CG at rtol 1e-10
     for s in range(args.warmup):
-        j = s % PAIRS_PER_STEP
-        ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X[j:j + 1], Y[j:j + 1], rtol=RTOL, threads=threads)
+        j = s % per
+        ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, w64, X[j:j + 1], Y[j:j + 1], rtol=RTOL, threads=threads)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        j = s % PAIRS_PER_STEP
-        ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, g.w, X[j:j + 1], Y[j:j + 1], rtol=RTOL, threads=threads)
+        j = (args.warmup + s) % per
+        ocg.ge_d2_cg(g.n, g.rowptr, g.colidx, w64, X[j:j + 1], Y[j:j + 1], rtol=RTOL, threads=threads)
     dt = time.perf_counter() - t0
     value = args.steps / dt
-    cfg = workload_config(g, wl.meta["n_generated"])
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
@@ -547,56 +532,208 @@ def run_reference(args):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS comparison runs")
-    ap.add_argument("--no-tune", action="store_true", help="default work decomposition (no autotuning)")
-    ap.add_argument("--workload", choices=["er_large", "powerlaw", "batched", "grad", "resistance",
-                                           "resistance_matrix"],
-                    default="er_large",
-                    help="er_large (default) is the bench line; the others measure the method's other workloads")
-    ap.add_argument("--scale", type=float, default=1.0,
-                    help="--workload powerlaw: node-count multiplier (profiling runs on a smaller graph)")
-    ap.add_argument("--eliminate", action="store_true",
-                    help="--workload powerlaw: eliminate degree-1/2 nodes exactly and solve on the reduced graph")
-    ap.add_argument("--sweep", choices=["size", "density"], default=None,
-                    help="the paper's synthetic runtime sweeps (one GE per point) instead of the bench line")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
-        return run_reference(args)
+def powerlaw_config(g, wl, args, tuning, elim):
+    return {
+        "workload": "powerlaw: erased configuration model n=1e7, degree exponent 2.3 on [2, 1e4], largest "
+                    "component, lognormal(0,1) FP32 weights, 128 pairs x,y U[0,1) on 0.1% of nodes normalised; "
+                    f"FP32 block-PCG (32 right-hand sides per SpMM, rtol {PL_RTOL_IN}) inside FP64 iterative "
+                    f"refinement to d^2 relative change {PL_D2_RTOL}"
+                    + ("; degree-1/2 nodes eliminated exactly, PCG on the reduced graph" if args.eliminate else ""),
+        "n": int(g.n), "nnz": int(g.rowptr[-1]), "n_generated": int(wl.meta["n_generated"]),
+        "pairs_per_step": PL_PAIRS, "mode": "MIXED", "rtol_inner": PL_RTOL_IN, "d2_rtol": PL_D2_RTOL,
+        "scale": args.scale, "tuning": tuning, "elimination": elim,
+        "l2": "L2 flushed (256 MB write) between timed steps; working set ~30 GB > 129 MB L2",
+    }
 
-    import numpy as np
-    import torch
 
-    rank, world, local = env_rank()
-    torch.cuda.set_device(local)
+def run_powerlaw(args, nvd, synth, torch, np, rank, world, local, dist):
+    """The default line: the power-law precision workload, 128 pairs per step (per rank),
+    FP32 block-PCG inside FP64 refinement (MIXED), inputs resident on the device."""
     dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    import __graft_entry__
-    if rank == 0:
-        __graft_entry__.build()
+    wl = synth.workload_powerlaw(scale=args.scale)
+    g = wl.graph
+    X, Y = wl.pairs(rank * PL_PAIRS, PL_PAIRS)                 # each rank its own pairs
+    G = nvd.Graph.from_csr(g)
+    # work decomposition picked by the autotuner on this graph (set-up, not timed)
+    tuning = None if args.no_tune else G.tune(mode=nvd.MODE_MIXED, k=PL_PAIRS)
+    elim = G.eliminate() if args.eliminate else None
+    xt = torch.from_numpy(X).to(dev)
+    yt = torch.from_numpy(Y).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    kw = dict(mode=nvd.MODE_MIXED, rtol=PL_RTOL_IN, d2_rtol=PL_D2_RTOL, eliminate=args.eliminate)
+
+    def step():
+        return nvd.ge_distance(G, xt, yt, return_stats=True, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    import paper_2310_11222_gb300 as nvd
-    import synth
-    nvd.load_library()
-    if args.sweep:
-        return run_sweep(args, nvd, synth, torch, np, local)
-    if args.workload != "er_large":
-        if world > 1:
-            raise SystemExit("--workload other than er_large runs on one GPU")
-        return run_other_workload(args, nvd, synth, torch, np, local)
+    clocks = ClockSampler(local)
+    clocks.start()
+    nvd.profile_enable(True)
+    for cls in (0, 1, 2):
+        nvd.profile_read(cls)
+    launches0 = nvd.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_wall0 = time.perf_counter()
+    last = None
+    for k in range(args.steps):
+        flush.zero_()                                   # evict L2 between steps (not timed)
+        ev[k][0].record()
+        last = step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = nvd.kernel_launches() - launches0
+    n_spmm, spmm_ms, spmm_bytes = nvd.profile_read(0)
+    n_res, res_ms, res_bytes = nvd.profile_read(2)
+    nvd.profile_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = job_time(sum(step_ms), dist, dev)
+    d2_last, stats = last
 
+    # ---- end to end through the C ABI: pinned host x, y copied to the device inside
+    #      the call (overlapped with the previous tile's solve), d^2 back to the host
+    xh = torch.from_numpy(X).pin_memory()
+    yh = torch.from_numpy(Y).pin_memory()
+
+    def step_e2e():
+        if args.eliminate:                # the elimination path takes device inputs
+            xt.copy_(xh, non_blocking=True)
+            yt.copy_(yh, non_blocking=True)
+            return nvd.ge_distance(G, xt, yt, **kw).cpu()
+        return nvd.ge_distance(G, xh, yh, **kw)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        d2_host = step_e2e()
+    torch.cuda.synchronize()
+    te = job_time(time.perf_counter() - te0, dist, dev)
+
+    value = job_rate(PL_PAIRS, world, args.steps, total_ms)
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = (spmm_bytes / n_spmm) / (spmm_ms / n_spmm / 1e3) / 1e9 if n_spmm else None
+    gather = 0 if tuning is None else int(tuning.get("gather", 0))
+    folded = bool(tuning and tuning.get("fold_direction"))
+    kt = (tuning or {}).get("kt") or 32
+    kbase = {0: "k_spmm", 1: "k_spmm_stream", 2: "k_spmm_tma"}[gather]
+    traffic = (ncu_traffic(f"spmm_powerlaw_kt{kt}_g{gather}_traffic.txt", SPMM_STREAM_SOURCES)
+               if not folded else None)
+    kname = (f"{kbase}<float,float,float,{kt},{'EpiLapDir' if folded else 'EpiLap'}> (FP32 multi-column "
+             f"Laplacian SpMM, {['register loads per slice', 'register loads over each warp stream', 'TMA gathers over each warp stream'][gather]}, fused p^T q)")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": powerlaw_config(g, wl, args, tuning, elim),
+        "e2e": {"value": job_rate(PL_PAIRS, world, args.steps, 1e3 * te), "unit": UNIT,
+                "h2d_bytes_per_step": int(xh.numel() * 8 * 2), "d2h_bytes_per_step": PL_PAIRS * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": kname, "launches": n_spmm,
+                     "avg_launch_us": 1e3 * spmm_ms / n_spmm if n_spmm else None,
+                     "algorithmic_bytes_per_launch": spmm_bytes / n_spmm if n_spmm else None,
+                     "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy) of MEASURED_PEAKS.json"},
+        "solver": {"inner_iters_per_pair": [s_["iters"] for s_ in stats],
+                   "refine_steps": sorted({s_["refine_steps"] for s_ in stats}),
+                   "status": sorted({s_["status"] for s_ in stats}), "wall_s_timed": t_wall,
+                   "spmm_ms_per_step": spmm_ms / args.steps,
+                   "residual_spmm": {"launches": n_res, "ms_per_step": res_ms / args.steps,
+                                     "algorithmic_bytes_per_launch": res_bytes / n_res if n_res else None}},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Xo, Yo = X[:PL_ORACLE_PAIRS], Y[:PL_ORACLE_PAIRS]
+        v, th, nsolves, dt, d2_or = cpu_baseline(g, Xo, Yo, budget_s=10.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+                                "sample": f"{nsolves} solves over the step's first {len(d2_or)} pairs ({dt:.1f} s), "
+                                          f"oracle FP64 Jacobi-PCG (oracle/pcg.c) at rtol 1e-10"}
+        got = d2_last.cpu().numpy()[:len(d2_or)]
+        line["max_rel_err_vs_oracle"] = float(np.max(np.abs(got - d2_or) / np.abs(d2_or)))
+        line["max_rel_err_e2e_vs_oracle"] = float(np.max(np.abs(d2_host.numpy()[:len(d2_or)] - d2_or)
+                                                         / np.abs(d2_or)))
+    if rank == 0 and not args.no_extra:
+        line["other_workloads"] = powerlaw_extras(args, nvd, synth, torch, np, dev, G, xt, yt, kw, d2_last)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def powerlaw_extras(args, nvd, synth, torch, np, dev, G, xt, yt, kw, d2_ref):
+    """The other headline numbers, measured in the same process: the Erdos-Renyi
+    workload solved one right-hand side at a time in FP64 (the plain method at scale)
+    against batched mixed precision on the same graph and pairs (the stated
+    multiple), and the power-law solve on the graph reduced by exact elimination of
+    its degree-1/2 nodes."""
+    out = {}
+
+    def rate(Gh, x, y, k, reps, **kw2):
+        nvd.ge_distance(Gh, x, y, **kw2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            res = nvd.ge_distance(Gh, x, y, **kw2)
+        b.record()
+        torch.cuda.synchronize()
+        return k * reps / (a.elapsed_time(b) / 1e3), res
+
+    wl = synth.workload_er_large()
+    ge = wl.graph
+    Xe, Ye = wl.pairs(0, PAIRS_PER_STEP)
+    Ge = nvd.Graph.from_csr(ge)
+    xe, ye = torch.from_numpy(Xe).to(dev), torch.from_numpy(Ye).to(dev)
+    t_single = None if args.no_tune else Ge.tune(mode=nvd.MODE_FP64, k=PAIRS_PER_STEP, single_rhs=True)
+    r1, d1 = rate(Ge, xe, ye, PAIRS_PER_STEP, 5, rtol=RTOL, single_rhs=True, check_every=CHECK_EVERY)
+    t_mixed = None if args.no_tune else Ge.tune(mode=nvd.MODE_MIXED, k=PAIRS_PER_STEP)
+    rm, dm = rate(Ge, xe, ye, PAIRS_PER_STEP, 5, mode=nvd.MODE_MIXED, rtol=MIXED_RTOL_IN, d2_rtol=MIXED_D2_RTOL)
+    d1, dm = d1.cpu().numpy(), dm.cpu().numpy()
+    out["er_large"] = {
+        "workload": "Erdos-Renyi G(n=1e6, m=5e6) largest component, FP64 weights U[0.5,2), 8 pairs on 1% of nodes",
+        "fp64_single_rhs_distances_per_s": r1,
+        "mixed_multi_rhs_distances_per_s": rm,
+        "multiple_mixed_vs_single_rhs_fp64": rm / r1,
+        "mixed": f"FP32 block-PCG to rtol {MIXED_RTOL_IN} inside FP64 refinement to d2_rtol {MIXED_D2_RTOL}",
+        "max_rel_diff_mixed_vs_fp64": float(np.max(np.abs(dm - d1) / np.abs(d1))),
+        "tuning_single": t_single, "tuning_mixed": t_mixed}
+    del Ge
+    if not args.eliminate:
+        t0 = time.perf_counter()
+        info = G.eliminate()
+        t_elim = time.perf_counter() - t0
+        kw_e = dict(kw, eliminate=True)
+        re, (de, st) = rate(G, xt, yt, PL_PAIRS, 2, return_stats=True, **kw_e)
+        _, st_plain = nvd.ge_distance(G, xt, yt, return_stats=True, **kw)
+        de = de.cpu().numpy()
+        ref = d2_ref.cpu().numpy()
+        out["powerlaw_eliminated"] = {
+            "distances_per_s": re, "elimination": info, "elimination_host_s": t_elim,
+            "inner_iters_mean": float(np.mean([s_["iters"] for s_ in st])),
+            "inner_iters_mean_plain": float(np.mean([s_["iters"] for s_ in st_plain])),
+            "max_rel_diff_vs_plain": float(np.max(np.abs(de - ref) / np.abs(ref)))}
+    return out
+
+
+def run_er_large(args, nvd, synth, torch, np, rank, world, local, dist):
+    """The Erdos-Renyi workload (n = 10^6, 8 pairs, one right-hand side at a time in
+    FP64) as its own line, with the multi-RHS FP64 and MIXED comparisons."""
+    dev = torch.device("cuda", local)
     wl = synth.workload_er_large()
     g = wl.graph
     X, Y = wl.pairs(*rank_pair_range(rank))                    # each rank its own pairs
@@ -754,6 +891,60 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS comparison runs")
+    ap.add_argument("--no-tune", action="store_true", help="default work decomposition (no autotuning)")
+    ap.add_argument("--workload", choices=["er_large", "powerlaw", "batched", "grad", "resistance",
+                                           "resistance_matrix"],
+                    default="powerlaw",
+                    help="powerlaw (default) is the bench line; the others measure the method's other workloads")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="--workload powerlaw: node-count multiplier (profiling runs on a smaller graph)")
+    ap.add_argument("--eliminate", action="store_true",
+                    help="--workload powerlaw: eliminate degree-1/2 nodes exactly and solve on the reduced graph")
+    ap.add_argument("--sweep", choices=["size", "density"], default=None,
+                    help="the paper's synthetic runtime sweeps (one GE per point) instead of the bench line")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2310_11222_gb300 as nvd
+    import synth
+    nvd.load_library()
+    if args.sweep:
+        return run_sweep(args, nvd, synth, torch, np, local)
+    if args.workload == "powerlaw":
+        return run_powerlaw(args, nvd, synth, torch, np, rank, world, local, dist)
+    if args.workload == "er_large":
+        return run_er_large(args, nvd, synth, torch, np, rank, world, local, dist)
+    if world > 1:
+        raise SystemExit("--workload other than powerlaw and er_large runs on one GPU")
+    return run_other_workload(args, nvd, synth, torch, np, local)
 
 
 if __name__ == "__main__":

@@ -102,6 +102,34 @@ int nvd_graph_destroy(nvd_graph_t g);
 int nvd_graph_info(nvd_graph_t g, int64_t *n, int64_t *nnz, int32_t *ncomp,
                    int64_t *device_bytes);
 
+/*
+ * nvd_graph_set_weights -- new edge weights for the same sparsity pattern (the
+ * weighted graphs of Section 3.1; a training loop that updates w between
+ * distance evaluations), without rebuilding the handle: no new components,
+ * relabelling, plans or tuning.
+ *
+ *   w       [nnz] weights in the entry order of the CSR given to nvd_graph_create
+ *           (the caller's nnz, before cleaning), host memory, or device memory with
+ *           NVD_GRAPH_DEVICE_PTRS in flags.
+ *   wdtype  must be the handle's weight type (the wdtype of nvd_graph_create).
+ *   flags   NVD_GRAPH_DEVICE_PTRS, NVD_GRAPH_SKIP_SYM_CHECK.
+ *
+ * Entries are mapped as at creation: self-loop entries are dropped (their weight
+ * must still be finite and > 0) and repeated (u, v) entries are summed in entry
+ * order.  The degrees, D^-1, the FP32 copy of FP64 weights and the sliced copies of
+ * every cached work plan are recomputed.  An elimination made by
+ * nvd_graph_eliminate is dropped (it depends on the weights): call it again before
+ * solving with NVD_SOLVE_ELIMINATE.  Synchronous: returns once the handle holds the
+ * new weights.
+ *
+ * Errors: NVD_ERR_INVALID_ARG (NULL pointer, other dtype, unknown flag),
+ * NVD_ERR_BAD_WEIGHT (a weight <= 0, NaN or infinite), NVD_ERR_NOT_SYMMETRIC
+ * (w_uv != w_vu after merging), NVD_ERR_OOM, NVD_ERR_CUDA.  On an error the
+ * handle keeps its old weights.
+ */
+int nvd_graph_set_weights(nvd_graph_t g, const void *w, int32_t wdtype, uint32_t flags,
+                          nvd_stream_t stream);
+
 /* ------------------------------------------------------------------ solving */
 
 typedef enum {
@@ -167,6 +195,10 @@ typedef struct {
     int32_t persistent;    /* 1: one persistent launch per tile was faster */
     int32_t candidates;    /* configurations timed */
     int32_t fold_direction; /* 1: two kernels per iteration (NVD_SOLVE_FOLD_DIRECTION) were faster */
+    int32_t gather;        /* multi-column SpMM: 0 register loads per slice (default), 1 register loads
+                              over each warp's step stream, 2 TMA gathers over the stream (tiles whose
+                              rows are 64 or 128 bytes; others use 1) */
+    int32_t reserved;
     double ms_per_iter;    /* device time of one PCG iteration of one tile, chosen setting */
     double ms_per_pair_iter; /* ms_per_iter / kt */
 } nvd_tune_result;
@@ -174,9 +206,11 @@ typedef struct {
 /*
  * nvd_graph_tune -- choose the work decomposition of the solve (Section 3.2) for
  * this graph by timing it: tile width (k-blocking) for k pairs, the row-split
- * limit (longer rows become split sub-items), the number of SpMV blocks, and
- * host-driven versus persistent iterations, and two versus three kernels per
- * iteration (NVD_SOLVE_FOLD_DIRECTION).  Candidates run real solves with
+ * limit (longer rows become split sub-items), the number of SpMV blocks, the
+ * gather engine of multi-column SpMMs (register loads per slice, register loads
+ * over a warp's step stream, TMA row gathers into shared memory), host-driven
+ * versus persistent iterations, and two versus three kernels per iteration
+ * (NVD_SOLVE_FOLD_DIRECTION).  Candidates run real solves with
  * seeded synthetic right-hand sides for a fixed number of iterations on
  * `stream`; the winner is stored in the handle and used by later calls of
  * mode `mode` (MIXED is timed as its FP32 inner solve): plans built afterwards
@@ -200,7 +234,7 @@ int nvd_graph_tune(nvd_graph_t g, int32_t mode, int32_t k, uint32_t flags, nvd_t
  * nvd_graph_set_tuning -- apply a setting (for example one nvd_graph_tune chose
  * earlier for the same graph) without timing anything.  Reads kt (0 = no
  * preference), row_max_pct and blocks_pct (10..1000), persistent and
- * fold_direction (0/1); the other fields are ignored.  Host only; plans built
+ * fold_direction (0/1), gather (0..2); the other fields are ignored.  Host only; plans built
  * afterwards use it.
  * Errors: NVD_ERR_INVALID_ARG (NULL pointer, bad mode or field).
  */
@@ -458,8 +492,10 @@ const char *nvd_last_error(void);
  * (on = 2: the vector passes too, class 1);
  * nvd_profile_read returns the launch count, summed event time in ms and summed
  * algorithmic bytes of those launches since the last read (and resets them).
- * Class 0 = the SpMV/SpMM kernel, class 1 = the streaming vector passes (bytes
- * not tracked).  SpMV launches issued after every pair of a tile had converged
+ * Class 0 = the SpMV/SpMM kernel of the CG iterations, class 1 = the streaming
+ * vector passes (bytes not tracked), class 2 = the FP64 residual SpMM of the
+ * MIXED refinement steps and of warm starts (every launch, no sampling).  SpMV
+ * launches issued after every pair of a tile had converged
  * (they find nothing to do) are dropped from the count.  Bits 8..15 of `on`
  * give a sampling period s (0 or 1 = every launch): only every s-th SpMV launch
  * is bracketed, so the events disturb the launch sequence less (a bracketed

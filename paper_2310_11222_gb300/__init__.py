@@ -45,6 +45,7 @@ SOLVE_ELIMINATE = 256
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_SYM_CHECK = 2
 TUNE_SINGLE_RHS = 1
+GATHER_SLICES, GATHER_STREAM, GATHER_TMA = 0, 1, 2   # nvd_tune_result.gather
 
 STATUS = {0: "NVD_OK", 1: "NVD_ERR_INVALID_ARG", 2: "NVD_ERR_NOT_SYMMETRIC", 3: "NVD_ERR_BAD_WEIGHT",
           4: "NVD_ERR_OOM", 5: "NVD_ERR_CUDA", 6: "NVD_ERR_NOT_CONVERGED", 7: "NVD_ERR_NUMERIC",
@@ -81,6 +82,7 @@ class TuneResult(ctypes.Structure):
     """Mirror of ``nvd_tune_result``."""
     _fields_ = [("kt", ctypes.c_int32), ("row_max_pct", ctypes.c_int32), ("blocks_pct", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("candidates", ctypes.c_int32), ("fold_direction", ctypes.c_int32),
+                ("gather", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("ms_per_iter", ctypes.c_double), ("ms_per_pair_iter", ctypes.c_double)]
 
 
@@ -95,6 +97,8 @@ _SIGS = {
     "nvd_graph_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int64)]),
+    "nvd_graph_set_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32,
+                                             ctypes.c_void_p]),
     "nvd_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "nvd_graph_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
                                       ctypes.POINTER(TuneResult), ctypes.c_void_p]),
@@ -197,6 +201,14 @@ def default_opts(mode: int = MODE_FP64, **kw) -> SolveOpts:
     return o
 
 
+def _weight_key(w):
+    """(address, version) of a torch weight tensor: a changed key means new values
+    (an optimizer step bumps the version); None for numpy or no weights."""
+    if w is None or isinstance(w, np.ndarray) or not hasattr(w, "_version"):
+        return None
+    return (w.data_ptr(), int(w._version))
+
+
 class Graph:
     """Handle on a graph held in device memory (``nvd_graph_create``).
 
@@ -246,6 +258,8 @@ class Graph:
         self.wdtype = wdt
         self.n_user = int(n)
         self.nnz_user = int(nnz)
+        # the torch weight tensor (address, version) the handle's weights came from
+        self._w_key = _weight_key(w)
         with torch.cuda.device(self.device):
             rc = lib.nvd_graph_create(ctypes.byref(self.handle), int(n), int(nnz), p_rp, p_ci, p_w, wdt,
                                       flags, _stream_ptr(self.device))
@@ -256,6 +270,29 @@ class Graph:
     def from_csr(cls, g, **kw):
         """From an object with ``rowptr``, ``colidx``, ``w`` numpy attributes."""
         return cls(g.rowptr, g.colidx, g.w, **kw)
+
+    def set_weights(self, w, *, skip_sym_check: bool = False):
+        """New weights for the same sparsity pattern (``nvd_graph_set_weights``), in the
+        entry order of the CSR the graph was built from: numpy (host) or torch (host
+        or this graph's device).  Converted to the graph's weight type."""
+        torch = _torch()
+        flags = GRAPH_SKIP_SYM_CHECK if skip_sym_check else 0
+        if isinstance(w, np.ndarray):
+            wv = np.ascontiguousarray(w, dtype=np.float64 if self.wdtype == F64 else np.float32)
+            ptr = wv.ctypes.data
+            key = None
+        else:
+            key = _weight_key(w)
+            wv = w.detach().to(torch.float64 if self.wdtype == F64 else torch.float32).contiguous()
+            if wv.is_cuda:
+                flags |= GRAPH_DEVICE_PTRS
+            ptr = wv.data_ptr()
+        if wv.shape[0] != self.nnz_user:
+            raise ValueError(f"expected {self.nnz_user} weights, got {wv.shape[0]}")
+        with torch.cuda.device(self.device):
+            rc = self._lib.nvd_graph_set_weights(self.handle, ptr, self.wdtype, flags, _stream_ptr(self.device))
+        _check(rc, "nvd_graph_set_weights")
+        self._w_key = key
 
     def info(self):
         n, nnz, nc, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
@@ -286,10 +323,12 @@ class Graph:
         return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
     def set_tuning(self, *, mode: int = 0, kt: int = 0, row_max_pct: int = 100, blocks_pct: int = 100,
-                   persistent: bool = False, fold_direction: bool = False):
-        """Apply a work-decomposition setting without timing (``nvd_graph_set_tuning``)."""
+                   persistent: bool = False, fold_direction: bool = False, gather: int = GATHER_SLICES):
+        """Apply a work-decomposition setting without timing (``nvd_graph_set_tuning``).
+        ``gather``: GATHER_SLICES (default), GATHER_STREAM or GATHER_TMA."""
         r = TuneResult(kt=int(kt), row_max_pct=int(row_max_pct), blocks_pct=int(blocks_pct),
-                       persistent=int(bool(persistent)), fold_direction=int(bool(fold_direction)))
+                       persistent=int(bool(persistent)), fold_direction=int(bool(fold_direction)),
+                       gather=int(gather))
         _check(self._lib.nvd_graph_set_tuning(self.handle, int(mode), ctypes.byref(r)), "nvd_graph_set_tuning")
 
     @property
@@ -566,14 +605,19 @@ def _make_autograd():
     class GEDistance(torch.autograd.Function):
         """d^2 = (x - y)^T L^+ (x - y) with gradients for x, y and the CSR weights.
 
-        forward(x, y, w, graph, opts) -> d^2 [k]; ``w`` must be the weight tensor the
-        graph was built from (its values are read at graph creation; pass it here so
-        autograd tracks it).  Backward reuses the forward z = L^+ delta (no new
-        solve) through ``nvd_ge_grad``.
+        forward(x, y, w, graph, opts) -> d^2 [k]; ``w`` holds the graph's weights in
+        the entry order of its CSR.  When its values differ from the ones the graph
+        holds (another tensor, or the same one after an in-place update such as an
+        optimizer step) they are copied into the graph first
+        (``nvd_graph_set_weights``), so the solve always uses the current ``w``.
+        Backward reuses the forward z = L^+ delta (no new solve) through
+        ``nvd_ge_grad``.
         """
 
         @staticmethod
         def forward(ctx, x, y, w, graph, opts):
+            if w is not None and _weight_key(w) != graph._w_key:
+                graph.set_weights(w)
             d2, z = ge_distance(graph, x, y, return_z=True, **(opts or {}))
             ctx.graph = graph
             ctx.save_for_backward(z)

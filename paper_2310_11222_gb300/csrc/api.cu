@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "graph.h"
@@ -44,6 +45,24 @@ cudaEvent_t take_event() {
 std::atomic<int64_t> g_kernel_launches{0};
 
 void note_launch(int64_t n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int allow_dynamic_smem(const void *kern, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::tuple<const void *, int, int>> done;   // kernel, device, bytes
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto &d : done)
+        if (std::get<0>(d) == kern && std::get<1>(d) == dev && std::get<2>(d) >= bytes) return NVD_OK;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaFuncSetAttribute(MaxDynamicSharedMemorySize, %d) failed: %s", bytes, cudaGetErrorString(e));
+        return NVD_ERR_CUDA;
+    }
+    done.emplace_back(kern, dev, bytes);
+    return NVD_OK;
+}
 
 bool prof_enabled() { return g_enabled != 0; }
 bool prof_vec_enabled() { return g_enabled >= 2; }

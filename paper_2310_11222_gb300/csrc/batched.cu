@@ -249,7 +249,7 @@ int batched_impl(const nvd_graph_t *gs, int32_t G, const int32_t *k_per, const v
     const size_t szv = o.mode == NVD_MODE_FP64 ? 8 : 4;
     const size_t xsz = xdt == NVD_F64 ? 8 : 4;
     Plan *pl = nullptr;
-    NVD_TRY(get_plan(U, KT, (int)szv, (int)szv, &pl));
+    NVD_TRY(get_plan(U, KT, (int)szv, (int)szv, &pl, false));   // the persistent kernel's register-path SpMM
     Ctx c;
     memset(&c, 0, sizeof(c));
     fill_graph_ctx(U, pl, &c);

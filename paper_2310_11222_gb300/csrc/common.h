@@ -42,6 +42,13 @@ constexpr int red_doubles(int KT) {
     return KT == 1 ? 4 * NT : (NWARP * 4 * KT) > 256 ? NWARP * 4 * KT : 256;
 }
 constexpr int vec_smem_bytes(int KT) { return (red_doubles(KT) + 4 * KT) * 8; }
+// Stream plans of multi-column tiles (stream.cuh): light rows of at most
+// 256 / H entries (longer slices would unbalance the warps of a block), heavy rows cut
+// into chunks of 64 steps (64 * H entries), one warp each.  Tiles whose rows are 64 or
+// 128 bytes (8 or 4 rows per slice, 512 bytes per step) can also gather with TMA.
+constexpr int sp_row_max_stream(int KT, int szv) { return 256 / sp_slice_rows(KT, szv); }
+constexpr int sp_chunk_stream(int KT, int szv) { return 64 * sp_slice_rows(KT, szv); }
+constexpr bool tma_tile(int KT, int szv) { return KT > 1 && (KT * szv == 64 || KT * szv == 128); }
 
 // Heavy sub-item of the Laplacian SpMV/SpMM (rows above the light-row limit; the
 // light rows are in the sliced layout).
@@ -116,7 +123,7 @@ struct Ctx {
     double *hs_sum, *hs_hist;       // d^2 stop: sum of alpha_k rho_k; [nseg*KT][d2_window] last terms
     int32_t *active, *iters, *status;
     int32_t *n_active;              // number of (segment, column) pairs still iterating
-    int32_t *err;                   // sticky device error code (grid-barrier timeout)
+    int32_t *err;                   // sticky device error code (a bounded wait that gave up)
     double rtol2;
     double d2stop;                  // > 0: also stop when the estimated d^2 error <= d2stop * d^2
     int32_t max_iter;
@@ -134,6 +141,10 @@ struct Ctx {
     const int32_t *sl_col;
     const void *sl_w;
     int32_t sl_h;                   // H of the plan the pointers above belong to
+    int32_t sl_stream;              // 1: stream plan (stream.cuh): sl_* hold every warp's steps
+    int32_t sl_tma;                 // 1: a stream plan gathered by TMA (tma.cuh)
+    const int32_t *sl_wsplit;       // [n_sblk][NWARP + 1] first slice of each warp, relative to the block's
+    const longlong2 *sl_wrun;       // stream plans: [n_sblk][NWARP] {first entry, steps} of each warp
     // ---- persistent-kernel grid barrier
     unsigned *bar_count, *bar_gen;
     int32_t bar_extra;              // arrivals awaited beyond the grid (0; 1 only to test the timeout)

@@ -7,12 +7,17 @@
 // constants span the null space of L) and, if a component is not a contiguous
 // node range, relabels the nodes so that every component is one -- the solver
 // then treats each component as an independent "segment".
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 
 #include "graph.h"
 
@@ -140,6 +145,30 @@ __global__ void k_round_w32(const double *__restrict__ w, float *w32, int64_t n)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         w32[i] = (float)w[i];
+}
+
+// flag = 1 if some weight is <= 0, NaN or infinite.
+template <class TW>
+__global__ void k_check_weights(int64_t n, const TW *__restrict__ w, int *flag) {
+    int f = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = (double)w[i];
+        if (!(x > 0.0) || !isfinite(x)) f = 1;
+    }
+    if (__any_sync(0xffffffffu, f) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// New weights of the handle's entries from the caller's entries: internal entry e
+// sums the user entries isrc[iptr[e] .. iptr[e+1]) in that (increasing) order in
+// FP64, as the creation's cleaning merged repeated entries.
+template <class TW>
+__global__ void k_gather_weights(int64_t nnz, const int64_t *__restrict__ iptr, const int64_t *__restrict__ isrc,
+                                 const TW *__restrict__ wu, TW *__restrict__ wi) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int64_t q = iptr[e]; q < iptr[e + 1]; ++q) t += (double)wu[isrc[q]];
+        wi[e] = (TW)t;
+    }
 }
 
 // Connected components by hooking and pointer jumping.  parent[] only ever
@@ -280,12 +309,12 @@ int run_checks(nvd_graph_s *g, bool have_w, int *flags_h, cudaStream_t s) {
 }
 
 template <class TW>
-int run_sym(nvd_graph_s *g, int *bad_h, cudaStream_t s) {
+int run_sym(nvd_graph_s *g, int *bad_h, cudaStream_t s, const TW *w = nullptr) {
     nvd::DevBuf bad;
     NVD_TRY(bad.alloc(sizeof(int)));
     NVD_TRY_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
     k_check_sym<TW><<<nvd::grid_for(g->n, 32, g->num_sms), 256, 0, s>>>(
-        g->n, g->rowptr.as<int64_t>(), g->colidx.as<int32_t>(), g->w.as<TW>(), bad.as<int>());
+        g->n, g->rowptr.as<int64_t>(), g->colidx.as<int32_t>(), w ? w : g->w.as<TW>(), bad.as<int>());
     NVD_TRY_CUDA(cudaGetLastError());
     NVD_TRY_CUDA(cudaMemcpyAsync(bad_h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     NVD_TRY_CUDA(cudaStreamSynchronize(s));
@@ -294,10 +323,10 @@ int run_sym(nvd_graph_s *g, int *bad_h, cudaStream_t s) {
 
 int run_degree(nvd_graph_s *g, cudaStream_t s) {
     const int64_t n = g->n;
-    NVD_TRY(g->deg64.alloc(n * 8));
-    NVD_TRY(g->dinv64.alloc(n * 8));
-    NVD_TRY(g->deg32.alloc(n * 4));
-    NVD_TRY(g->dinv32.alloc(n * 4));
+    NVD_TRY(g->deg64.ensure(n * 8));
+    NVD_TRY(g->dinv64.ensure(n * 8));
+    NVD_TRY(g->deg32.ensure(n * 4));
+    NVD_TRY(g->dinv32.ensure(n * 4));
     const int grid = nvd::grid_for(n, 32, g->num_sms);
     if (g->wdtype == NVD_F64)
         k_degree<double><<<grid, 256, 0, s>>>(n, g->rowptr.as<int64_t>(), g->w.as<double>(),
@@ -345,6 +374,55 @@ int run_components(nvd_graph_s *g, std::vector<int32_t> &root, cudaStream_t s) {
 
 int target_blocks(const nvd_graph_s *g) { return 2 * g->num_sms * 8; }
 
+// ------------------------------------------------------------------ TMA tensor maps
+
+int tma_map(const void *base, int64_t rows, int kt, int szv, CUtensorMap *out) {
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::map<std::tuple<uintptr_t, int64_t, int, int>, CUtensorMap> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple((uintptr_t)base, rows, kt, szv);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = it->second;
+        return NVD_OK;
+    }
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                               cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            set_error("TMA: cuTensorMapEncodeTiled is not available from the driver");
+            return NVD_ERR_UNSUPPORTED;
+        }
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    if (((uintptr_t)base & 15) || rows < 1 || rows > (int64_t)1 << 31 || (kt * szv) % 16 || kt > 256) {
+        set_error("TMA: unsupported array for a tensor map (base %p, %lld rows of %d x %d bytes)", base,
+                  (long long)rows, kt, szv);
+        return NVD_ERR_UNSUPPORTED;
+    }
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)kt, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kt * (cuuint64_t)szv};
+    const cuuint32_t box[2] = {(cuuint32_t)kt, 1u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = encode(&m, szv == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                              const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("TMA: cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return NVD_ERR_CUDA;
+    }
+    if (cache.size() > 256) cache.clear();
+    cache[key] = m;
+    *out = m;
+    return NVD_OK;
+}
+
 // CTAs per SM of one vector pass: one column 4 (64 registers each), several
 // columns 2 (128 registers each), i.e. one full wave either way.
 #ifndef VEC_PER_SM
@@ -387,9 +465,142 @@ __global__ void k_fill_slices(int64_t n_slices, int H, const int64_t *__restrict
     }
 }
 
-int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
-    const int64_t key = ((int64_t)(KT * 256 + szv * 16 + sza) << 32) | ((int64_t)g->sp.row_max_pct << 16) |
-                        (int64_t)g->sp.blocks_pct;
+// Light slices of a stream plan (stream.cuh): step 0 holds the slice's rows -- their own
+// rows of the vector are gathered first -- with the rows' degrees as weights (-0
+// marks an empty lane group, whose column is the slice's first row); steps 1..L the
+// rows' entries, padded with zero weights on the row's own column; the weights of
+// the last step are negated (sign bit set: the slice ends there, -0 for padding).
+template <class TWI, class TA>
+__global__ void k_fill_slices_tma(int64_t n_slices, int H, const int64_t *__restrict__ sl_base,
+                                  const int32_t *__restrict__ sl_row, const int64_t *__restrict__ rowptr,
+                                  const int32_t *__restrict__ colidx, const TWI *__restrict__ w,
+                                  const TA *__restrict__ deg, int32_t *__restrict__ sl_col, TA *__restrict__ sl_w) {
+    const int64_t nt = n_slices * H;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = t / H;
+        const int r = (int)(t % H);
+        const int64_t base = sl_base[sl];
+        const int64_t L = (sl_base[sl + 1] - base) / H - 1;
+        const int32_t row = sl_row[t];
+        const int32_t own = row >= 0 ? row : sl_row[sl * H];
+        sl_col[base + r] = own;
+        sl_w[base + r] = row >= 0 ? deg[row] : -(TA)0;
+        const int64_t e0 = row >= 0 ? rowptr[row] : 0;
+        const int64_t d = row >= 0 ? rowptr[row + 1] - e0 : 0;
+        for (int64_t j = 0; j < L; ++j) {
+            const bool in = j < d;
+            const TA wv = in ? (TA)w[e0 + j] : (TA)0;
+            sl_col[base + (j + 1) * H + r] = in ? colidx[e0 + j] : own;
+            sl_w[base + (j + 1) * H + r] = j == L - 1 ? -wv : wv;
+        }
+    }
+}
+
+// Heavy-row chunks of a stream plan as slices of their own (item.pad = the slice): entry
+// j*H + g of the chunk at step j, lane group g (the CSR order), padded past the chunk
+// with zero weights on the row's own column, the last step's weights negated.
+template <class TWI, class TA>
+__global__ void k_fill_chunks_tma(int64_t n_items, int H, const SpItem *__restrict__ items,
+                                  const int64_t *__restrict__ sl_base, const int32_t *__restrict__ colidx,
+                                  const TWI *__restrict__ w, int32_t *__restrict__ sl_col, TA *__restrict__ sl_w) {
+    const int64_t nt = n_items * H;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const SpItem it = items[t / H];
+        const int r = (int)(t % H);
+        const int64_t base = sl_base[it.pad];
+        const int64_t S = (sl_base[it.pad + 1] - base) / H;
+        for (int64_t j = 0; j < S; ++j) {
+            const int64_t e = it.e0 + j * H + r;
+            const bool in = e < it.e1;
+            const TA wv = in ? (TA)w[e] : (TA)0;
+            sl_col[base + j * H + r] = in ? colidx[e] : it.r0;
+            sl_w[base + j * H + r] = j == S - 1 ? -wv : wv;
+        }
+    }
+}
+
+// (Re)write the sliced copy of a plan's light rows from the handle's CSR (after the
+// plan is built, and after new weights).
+static int fill_plan_slices(nvd_graph_s *g, Plan *pl, cudaStream_t s) {
+    if (pl->n_slices == 0) return NVD_OK;
+    const int H = sp_slice_rows(pl->KT, pl->szv);
+    if (pl->stream) {
+        // stream plans: weights in the solve's accumulator type (they carry the degrees)
+        const int64_t *rpd = g->rowptr.as<int64_t>();
+        const int32_t *cid = g->colidx.as<int32_t>();
+        const int64_t *sb = pl->sl_base.as<int64_t>();
+        const int32_t *sr = pl->sl_row.as<int32_t>();
+        int32_t *sc = pl->sl_col.as<int32_t>();
+        const SpItem *it = pl->items.as<SpItem>();
+        const int gl = grid_for(std::max<int64_t>(pl->n_light_slices * H, 1), 1, g->num_sms);
+        const int gh = grid_for(std::max<int64_t>(pl->n_items * H, 1), 1, g->num_sms);
+        if (pl->szv == 8) {
+            double *sw = pl->sl_w.as<double>();
+            if (g->wdtype == NVD_F64) {
+                if (pl->n_light_slices)
+                    k_fill_slices_tma<double, double><<<gl, 256, 0, s>>>(pl->n_light_slices, H, sb, sr, rpd, cid,
+                                                                         g->w.as<double>(), g->deg64.as<double>(), sc, sw);
+                if (pl->n_items)
+                    k_fill_chunks_tma<double, double><<<gh, 256, 0, s>>>(pl->n_items, H, it, sb, cid, g->w.as<double>(),
+                                                                         sc, sw);
+            } else {
+                if (pl->n_light_slices)
+                    k_fill_slices_tma<float, double><<<gl, 256, 0, s>>>(pl->n_light_slices, H, sb, sr, rpd, cid,
+                                                                        g->w.as<float>(), g->deg64.as<double>(), sc, sw);
+                if (pl->n_items)
+                    k_fill_chunks_tma<float, double><<<gh, 256, 0, s>>>(pl->n_items, H, it, sb, cid, g->w.as<float>(),
+                                                                        sc, sw);
+            }
+        } else {
+            float *sw = pl->sl_w.as<float>();
+            if (g->wdtype == NVD_F64) {
+                if (pl->n_light_slices)
+                    k_fill_slices_tma<double, float><<<gl, 256, 0, s>>>(pl->n_light_slices, H, sb, sr, rpd, cid,
+                                                                        g->w.as<double>(), g->deg32.as<float>(), sc, sw);
+                if (pl->n_items)
+                    k_fill_chunks_tma<double, float><<<gh, 256, 0, s>>>(pl->n_items, H, it, sb, cid, g->w.as<double>(),
+                                                                        sc, sw);
+            } else {
+                if (pl->n_light_slices)
+                    k_fill_slices_tma<float, float><<<gl, 256, 0, s>>>(pl->n_light_slices, H, sb, sr, rpd, cid,
+                                                                       g->w.as<float>(), g->deg32.as<float>(), sc, sw);
+                if (pl->n_items)
+                    k_fill_chunks_tma<float, float><<<gh, 256, 0, s>>>(pl->n_items, H, it, sb, cid, g->w.as<float>(),
+                                                                       sc, sw);
+            }
+        }
+        NVD_TRY_CUDA(cudaGetLastError());
+        return NVD_OK;
+    }
+    const bool w64 = pl->szv == 8 && g->wdtype == NVD_F64;
+    const int grid = grid_for(pl->n_slices * H, 1, g->num_sms);
+    const int64_t *rpd = g->rowptr.as<int64_t>();
+    const int32_t *cid = g->colidx.as<int32_t>();
+    const int64_t *sb = pl->sl_base.as<int64_t>();
+    const int32_t *sr = pl->sl_row.as<int32_t>();
+    int32_t *sc = pl->sl_col.as<int32_t>();
+    if (g->wdtype == NVD_F64 && w64)
+        k_fill_slices<double, double><<<grid, 256, 0, s>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<double>(), sc,
+                                                           pl->sl_w.as<double>());
+    else if (g->wdtype == NVD_F64)
+        k_fill_slices<double, float><<<grid, 256, 0, s>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<double>(), sc,
+                                                          pl->sl_w.as<float>());
+    else
+        k_fill_slices<float, float><<<grid, 256, 0, s>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<float>(), sc,
+                                                         pl->sl_w.as<float>());
+    NVD_TRY_CUDA(cudaGetLastError());
+    return NVD_OK;
+}
+
+int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out, bool allow_stream) {
+    // gather mode of this plan: 0 register slices, 1 register stream, 2 TMA stream
+    const int gm = (!allow_stream || KT == 1 || g->sp.gather <= 0) ? 0
+                   : (g->sp.gather >= 2 && tma_tile(KT, szv)) ? 2 : 1;
+    const bool tma = gm != 0;   // stream layout (the name of the TMA plans it began with)
+    const int64_t key = ((int64_t)(KT * 256 + szv * 16 + sza) << 32) | ((int64_t)gm << 30) |
+                        ((int64_t)g->sp.row_max_pct << 16) | (int64_t)g->sp.blocks_pct;
     auto it = g->plans.find(key);
     if (it != g->plans.end()) {
         *out = it->second.get();
@@ -400,9 +611,10 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     pl->szv = szv;
     pl->sza = sza;
     pl->sp = g->sp;
-    const int64_t RMAX = std::max<int64_t>(1, (int64_t)sp_row_max(KT, szv) * g->sp.row_max_pct / 100);
+    const int64_t RMAX = std::max<int64_t>(
+        1, (int64_t)(tma ? sp_row_max_stream(KT, szv) : sp_row_max(KT, szv)) * g->sp.row_max_pct / 100);
     const int64_t LONG = sp_long_max(KT);
-    const int64_t CH = sp_chunk(KT, szv);
+    const int64_t CH = tma ? sp_chunk_stream(KT, szv) : sp_chunk(KT, szv);
     const int H = sp_slice_rows(KT, szv);
     const std::vector<int64_t> &rp = g->h_rowptr;
     const int nseg = g->nseg;
@@ -456,7 +668,9 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     // warp rounds (NWARP slices of H rows) of about `target` work (entries + rows);
     // inside a block the rows are sorted by length (longest first, ties by row) and
     // dealt into slices.  Heavy blocks follow their segment's light blocks.
-    const int T = std::max(1, target_blocks(g) * g->sp.blocks_pct / 100);
+    // (stream plans: half as many, larger light blocks; their warps split a block's
+    // slices statically, which balances better on more work)
+    const int T = std::max(1, (tma ? target_blocks(g) / 2 : target_blocks(g)) * g->sp.blocks_pct / 100);
     const double target = ltot / T;
     // block sizes in whole slices (warps take a block's slices as they free up)
     const int64_t QR = (int64_t)H;
@@ -477,7 +691,8 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
                 sl_row.push_back(q < ord.size() ? (int32_t)rows[ord[q]] : -1);
                 if (q < ord.size()) L = std::max(L, lens[ord[q]]);
             }
-            sl_base.push_back(sl_base.back() + L * H);
+            // stream plans: one step more for the rows' own vector rows, at least one entry step
+            sl_base.push_back(sl_base.back() + (tma ? std::max<int64_t>(L, 1) + 1 : L) * H);
         }
         sblk.push_back(Block{first, (int64_t)sl_base.size() - 1, s, 0, (int32_t)rows.front(),
                              (int32_t)(rows.back() - rows.front() + 1)});
@@ -505,7 +720,7 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
             }
         }
         if (!rows.empty()) emit_block(s);
-        const size_t per = KT == 1 ? (size_t)NWARP : 4;
+        const size_t per = (KT == 1 || tma) ? (size_t)NWARP : 4;   // stream plans: one chunk per warp
         const int64_t h0 = seg_item_off[s], h1 = seg_item_off[s + 1];
         for (int64_t q = h0; q < h1; q += (int64_t)per)
             sblk.push_back(Block{q, std::min<int64_t>(h1, q + (int64_t)per), s, 1, 0, 0});
@@ -531,6 +746,59 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     }
     seg_vblk_off[nseg] = (int32_t)vblk.size();
 
+    // each warp of a light block takes a contiguous run of its slices (register-slice
+    // and stream plans), the runs cut where the running entry count is closest to an
+    // equal share
+    std::vector<int32_t> wsplit(std::max<size_t>(sblk.size(), 1) * (NWARP + 1), 0);
+    for (size_t bi = 0; bi < sblk.size(); ++bi) {
+        const Block &bk = sblk[bi];
+        if (bk.pad != 0) continue;
+        const int64_t ns = bk.i1 - bk.i0, e0 = sl_base[bk.i0], tot = sl_base[bk.i1] - e0;
+        int32_t *w = &wsplit[bi * (NWARP + 1)];
+        int64_t q = 0;
+        for (int k = 1; k < NWARP; ++k) {
+            const int64_t target = e0 + tot * k / NWARP;
+            while (q < ns && sl_base[bk.i0 + q + 1] <= target) ++q;
+            // slice q straddles the target (or ends on it): cut before or after it
+            int64_t cut = q;
+            if (q < ns && sl_base[bk.i0 + q + 1] - target < target - sl_base[bk.i0 + q]) cut = q + 1;
+            w[k] = (int32_t)std::max<int64_t>(cut, w[k - 1]);
+        }
+        w[NWARP] = (int32_t)ns;
+        for (int k = 1; k < NWARP; ++k) w[k] = std::min(w[k], w[NWARP]);
+    }
+    // stream plans: every heavy chunk is a slice of its own after the light slices
+    // (item.pad = its slice), and each warp's stream is one contiguous run of steps:
+    // {first entry, steps} per (block, warp) -- its slices of a light block, or the
+    // chunk it takes in a heavy block
+    const int64_t n_light_slices = (int64_t)sl_base.size() - 1;
+    std::vector<longlong2> wrun;
+    if (tma) {
+        for (SpItem &si : items) {
+            si.pad = (int32_t)(sl_base.size() - 1);
+            sl_base.push_back(sl_base.back() + ((si.e1 - si.e0 + H - 1) / H) * H);
+            for (int r = 0; r < H; ++r) sl_row.push_back(-1);
+        }
+        wrun.assign(std::max<size_t>(sblk.size(), 1) * NWARP, make_longlong2(0, 0));
+        for (size_t bi = 0; bi < sblk.size(); ++bi) {
+            const Block &bk = sblk[bi];
+            for (int k = 0; k < NWARP; ++k) {
+                int64_t a = 0, z = 0;
+                if (bk.pad == 0) {
+                    a = sl_base[bk.i0 + wsplit[bi * (NWARP + 1) + k]];
+                    z = sl_base[bk.i0 + wsplit[bi * (NWARP + 1) + k + 1]];
+                } else if (bk.i0 + k < bk.i1) {
+                    const int64_t sc = items[bk.i0 + k].pad;
+                    a = sl_base[sc];
+                    z = sl_base[sc + 1];
+                }
+                wrun[bi * NWARP + k] = make_longlong2(a, (z - a) / H);
+            }
+        }
+    }
+    pl->stream = tma;
+    pl->tma = gm == 2;
+    pl->n_light_slices = n_light_slices;
     pl->n_items = (int64_t)items.size();
     pl->n_sblk = (int64_t)sblk.size();
     pl->n_heavy = nheavy;
@@ -552,30 +820,17 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out) {
     NVD_TRY(pl->hcount.alloc((size_t)std::max<int32_t>(nheavy, 1) * 4));
     NVD_TRY_CUDA(cudaMemset(pl->hcount.p, 0, pl->hcount.bytes));
     NVD_TRY(up(pl->sl_base, sl_base.data(), sl_base.size() * 8));
+    NVD_TRY(up(pl->sl_wsplit, wsplit.data(), wsplit.size() * 4));
+    NVD_TRY(up(pl->sl_wrun, wrun.data(), wrun.size() * sizeof(longlong2)));
     NVD_TRY(up(pl->sl_row, sl_row.data(), sl_row.size() * 4));
-    const bool w64 = szv == 8 && g->wdtype == NVD_F64;
+    // sliced weights: the graph's type (FP64 only for FP64 vectors), the solve's
+    // accumulator type in stream plans (a slice's first step carries the degrees)
+    const bool w64 = tma ? szv == 8 : (szv == 8 && g->wdtype == NVD_F64);
     const int64_t ne = std::max<int64_t>(pl->n_sl_entries, 1);
     NVD_TRY(pl->sl_col.alloc((size_t)ne * 4));
     NVD_TRY(pl->sl_w.alloc((size_t)ne * (w64 ? 8 : 4)));
-    if (pl->n_slices > 0) {
-        const int grid = grid_for(pl->n_slices * H, 1, g->num_sms);
-        const int64_t *rpd = g->rowptr.as<int64_t>();
-        const int32_t *cid = g->colidx.as<int32_t>();
-        const int64_t *sb = pl->sl_base.as<int64_t>();
-        const int32_t *sr = pl->sl_row.as<int32_t>();
-        int32_t *sc = pl->sl_col.as<int32_t>();
-        if (g->wdtype == NVD_F64 && w64)
-            k_fill_slices<double, double><<<grid, 256>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<double>(), sc,
-                                                         pl->sl_w.as<double>());
-        else if (g->wdtype == NVD_F64)
-            k_fill_slices<double, float><<<grid, 256>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<double>(), sc,
-                                                        pl->sl_w.as<float>());
-        else
-            k_fill_slices<float, float><<<grid, 256>>>(pl->n_slices, H, sb, sr, rpd, cid, g->w.as<float>(), sc,
-                                                       pl->sl_w.as<float>());
-        NVD_TRY_CUDA(cudaGetLastError());
-        NVD_TRY_CUDA(cudaDeviceSynchronize());
-    }
+    NVD_TRY(fill_plan_slices(g, pl.get(), 0));
+    NVD_TRY_CUDA(cudaDeviceSynchronize());
     *out = pl.get();
     g->plans[key] = std::move(pl);
     return NVD_OK;
@@ -610,6 +865,10 @@ void set_sp_plan(Ctx *c, const Plan *pl) {
     c->sl_col = pl->sl_col.as<int32_t>();
     c->sl_w = pl->sl_w.p;
     c->sl_h = sp_slice_rows(pl->KT, pl->szv);
+    c->sl_stream = pl->stream ? 1 : 0;
+    c->sl_tma = pl->tma ? 1 : 0;
+    c->sl_wsplit = pl->sl_wsplit.as<int32_t>();
+    c->sl_wrun = pl->sl_wrun.as<longlong2>();
 }
 
 void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c) {
@@ -664,7 +923,8 @@ int64_t nvd_graph_s::device_bytes() const {
         for (const nvd::DevBuf *d : {&kv.second->items, &kv.second->sblk, &kv.second->vblk,
                                      &kv.second->seg_sblk_off, &kv.second->seg_heavy_off,
                                      &kv.second->seg_vblk_off, &kv.second->hcount, &kv.second->sl_base,
-                                     &kv.second->sl_row, &kv.second->sl_col, &kv.second->sl_w})
+                                     &kv.second->sl_row, &kv.second->sl_col, &kv.second->sl_w,
+                                     &kv.second->sl_wsplit, &kv.second->sl_wrun})
             b += (int64_t)d->bytes;
     for (auto &kv : ws) b += (int64_t)kv.second->bytes;
     return b;
@@ -897,6 +1157,124 @@ extern "C" int nvd_graph_create(nvd_graph_t *out, int64_t n, int64_t nnz, const 
         return NVD_ERR_OOM;
     } catch (...) {
         set_error("nvd_graph_create: unexpected host exception");
+        return NVD_ERR_CUDA;
+    }
+}
+
+// New weights for the same sparsity pattern: validate them, map them onto the
+// handle's entries (repeated entries summed, self-loops dropped, node relabelling
+// applied, as at creation), check symmetry, then replace the weights, the degrees,
+// the FP32 copy and the sliced copies of every cached plan.  Nothing is replaced
+// when a check fails.
+static int set_weights_impl(nvd_graph_t g, const void *w, int32_t wdtype, uint32_t flags, cudaStream_t s) {
+    if (!g || !w || wdtype != g->wdtype || (flags & ~(NVD_GRAPH_DEVICE_PTRS | NVD_GRAPH_SKIP_SYM_CHECK))) {
+        set_error("nvd_graph_set_weights: invalid argument (the weight type must be the handle's, %s)",
+                  g && g->wdtype == NVD_F64 ? "NVD_F64" : "NVD_F32");
+        return NVD_ERR_INVALID_ARG;
+    }
+    const size_t wsz = g->wdtype == NVD_F64 ? 8 : 4;
+    const int64_t nu = g->nnz_user, ni = g->nnz;
+    int st = NVD_OK;
+    void *wu = g->wsp("setw_user", (size_t)std::max<int64_t>(nu, 1) * wsz, &st);
+    const int64_t npad = ((ni + 3) / 4) * 4 + 4;
+    void *wi = g->wsp("setw_new", (size_t)npad * wsz, &st);
+    int *flag = (int *)g->wsp("setw_flag", 16, &st);
+    if (st) return st;
+    if (nu > 0)
+        NVD_TRY_CUDA(cudaMemcpyAsync(wu, w, (size_t)nu * wsz,
+                                     (flags & NVD_GRAPH_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    NVD_TRY_CUDA(cudaMemsetAsync(flag, 0, 16, s));
+    NVD_TRY_CUDA(cudaMemsetAsync(wi, 0, (size_t)npad * wsz, s));
+    const int grid = grid_for(std::max<int64_t>(nu, ni), 1, g->num_sms);
+    if (nu > 0) {
+        if (g->wdtype == NVD_F64)
+            k_check_weights<double><<<grid, 256, 0, s>>>(nu, (const double *)wu, flag);
+        else
+            k_check_weights<float><<<grid, 256, 0, s>>>(nu, (const float *)wu, flag);
+        NVD_TRY_CUDA(cudaGetLastError());
+    }
+    int bad_w = 0;
+    NVD_TRY_CUDA(cudaMemcpyAsync(&bad_w, flag, 4, cudaMemcpyDeviceToHost, s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    if (bad_w) {
+        set_error("nvd_graph_set_weights: weights must be finite and > 0");
+        return NVD_ERR_BAD_WEIGHT;
+    }
+    if (ni > 0) {
+        if (!g->uent.p) {
+            NVD_TRY_CUDA(cudaMemcpyAsync(wi, wu, (size_t)ni * wsz, cudaMemcpyDeviceToDevice, s));
+        } else {
+            if (!g->ient_ptr.p) {
+                std::vector<int64_t> ue(nu);
+                NVD_TRY_CUDA(cudaMemcpyAsync(ue.data(), g->uent.p, (size_t)nu * 8, cudaMemcpyDeviceToHost, s));
+                NVD_TRY_CUDA(cudaStreamSynchronize(s));
+                std::vector<int64_t> ptr(ni + 1, 0), src;
+                for (int64_t e = 0; e < nu; ++e)
+                    if (ue[e] >= 0) ++ptr[ue[e] + 1];
+                for (int64_t e = 0; e < ni; ++e) ptr[e + 1] += ptr[e];
+                src.resize(std::max<int64_t>(ptr[ni], 1));
+                std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+                for (int64_t e = 0; e < nu; ++e)
+                    if (ue[e] >= 0) src[fill[ue[e]]++] = e;
+                NVD_TRY(g->ient_ptr.alloc((size_t)(ni + 1) * 8));
+                NVD_TRY(g->ient_src.alloc(src.size() * 8));
+                NVD_TRY_CUDA(cudaMemcpyAsync(g->ient_ptr.p, ptr.data(), (size_t)(ni + 1) * 8, cudaMemcpyHostToDevice, s));
+                NVD_TRY_CUDA(cudaMemcpyAsync(g->ient_src.p, src.data(), src.size() * 8, cudaMemcpyHostToDevice, s));
+                NVD_TRY_CUDA(cudaStreamSynchronize(s));
+            }
+            if (g->wdtype == NVD_F64)
+                k_gather_weights<double><<<grid, 256, 0, s>>>(ni, g->ient_ptr.as<int64_t>(), g->ient_src.as<int64_t>(),
+                                                              (const double *)wu, (double *)wi);
+            else
+                k_gather_weights<float><<<grid, 256, 0, s>>>(ni, g->ient_ptr.as<int64_t>(), g->ient_src.as<int64_t>(),
+                                                             (const float *)wu, (float *)wi);
+            NVD_TRY_CUDA(cudaGetLastError());
+        }
+        if (!(flags & NVD_GRAPH_SKIP_SYM_CHECK)) {
+            int bad = 0;
+            if (g->wdtype == NVD_F64)
+                NVD_TRY(run_sym<double>(g, &bad, s, (const double *)wi));
+            else
+                NVD_TRY(run_sym<float>(g, &bad, s, (const float *)wi));
+            if (bad) {
+                set_error("nvd_graph_set_weights: the new weights are not symmetric");
+                return NVD_ERR_NOT_SYMMETRIC;
+            }
+        }
+    }
+    // commit
+    NVD_TRY_CUDA(cudaMemcpyAsync(g->w.p, wi, (size_t)npad * wsz, cudaMemcpyDeviceToDevice, s));
+    NVD_TRY(run_degree(g, s));
+    if (g->w32.p && g->wdtype == NVD_F64 && ni > 0) {
+        k_round_w32<<<grid_for(ni, 1, g->num_sms), 256, 0, s>>>(g->w.as<double>(), g->w32.as<float>(), ni);
+        NVD_TRY_CUDA(cudaGetLastError());
+    }
+    for (auto &kv : g->plans) NVD_TRY(fill_plan_slices(g, kv.second.get(), s));
+    NVD_TRY_CUDA(cudaStreamSynchronize(s));
+    g->elim.reset();            // the reduced graph depends on the weights
+    g->id = next_graph_id();    // caches keyed by the handle (batched unions, captured launches) miss
+    return NVD_OK;
+}
+
+extern "C" int nvd_graph_set_weights(nvd_graph_t g, const void *w, int32_t wdtype, uint32_t flags,
+                                     nvd_stream_t stream) {
+    clear_error();
+    if (!g) {
+        set_error("nvd_graph_set_weights: NULL handle");
+        return NVD_ERR_INVALID_ARG;
+    }
+    try {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != g->device) cudaSetDevice(g->device);
+        const int rc = set_weights_impl(g, w, wdtype, flags, (cudaStream_t)stream);
+        if (cur >= 0 && cur != g->device) cudaSetDevice(cur);
+        return rc;
+    } catch (const std::bad_alloc &) {
+        set_error("nvd_graph_set_weights: host allocation failed");
+        return NVD_ERR_OOM;
+    } catch (...) {
+        set_error("nvd_graph_set_weights: unexpected host exception");
         return NVD_ERR_CUDA;
     }
 }

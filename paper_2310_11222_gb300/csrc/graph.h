@@ -1,6 +1,7 @@
 // Internal graph handle, device buffers and work plans (host side).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <map>
@@ -70,6 +71,8 @@ struct DevBuf {
 struct SpParams {
     int32_t row_max_pct = 100;
     int32_t blocks_pct = 100;
+    int32_t gather = 0;          // multi-column SpMM: 0 register slices, 1 register stream, 2 TMA stream
+                                 // (2 only where tma_tile holds, else 1); the tuner tries the others
 };
 
 // Work decomposition for one (KT, vector size, accumulator size, SpParams).
@@ -80,6 +83,11 @@ struct Plan {
     int64_t n_slices = 0, n_sl_entries = 0;
     DevBuf items, sblk, vblk, seg_sblk_off, seg_heavy_off, seg_vblk_off, hcount;
     DevBuf sl_base, sl_row, sl_col, sl_w;   // sliced light rows (weights in the plan's TW)
+    DevBuf sl_wsplit;                       // per light block, the warps' contiguous slice runs
+    DevBuf sl_wrun;                         // stream plans: per (block, warp) {first entry, steps}
+    bool stream = false;                    // stream layout (stream.cuh)
+    bool tma = false;                       // stream plan gathered by TMA
+    int64_t n_light_slices = 0;             // stream plans: heavy-chunk slices follow the light ones
     int64_t part_slots() const {
         int64_t a = n_sblk + n_heavy;
         return a > n_vblk ? a : n_vblk;
@@ -105,6 +113,9 @@ struct nvd_graph_s {
     nvd::DevBuf deg64, dinv64, deg32, dinv32;
     nvd::DevBuf perm;            // int32 internal -> user node; empty when identity
     nvd::DevBuf uent;            // int64 user entry -> internal entry (-1 dropped); empty when identity
+    // inverse of uent for nvd_graph_set_weights (built on first use): the user entries
+    // of internal entry e are ient_src[ient_ptr[e] .. ient_ptr[e+1]), increasing
+    nvd::DevBuf ient_ptr, ient_src;
     int32_t ncomp = 0, nseg = 0;
     int64_t n_singleton = 0;
     std::vector<int64_t> h_rowptr, h_seg_begin, h_seg_end;
@@ -130,14 +141,22 @@ struct nvd_graph_s {
 
 namespace nvd {
 
-// Work plan for (KT, szv, sza), built on first use and cached in the handle.
-int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out);
+// Work plan for (KT, szv, sza), built on first use and cached in the handle.  A stream
+// plan (SpParams::gather >= 1, KT > 1) is laid out for the stream SpMM only
+// (k_spmm_stream, k_spmm_tma); launches that run the register-slice path (the
+// persistent kernel) ask for allow_stream = false.
+int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out, bool allow_stream = true);
 // FP32 weights for the FP32 paths (the FP64 weights rounded once, cached).
 int get_w32(nvd_graph_s *g, const float **out, cudaStream_t s);
 // Ctx fields that depend only on the graph and a plan.
 void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c);
 // Only the SpMV/SpMM work-decomposition fields of a Ctx.
 void set_sp_plan(Ctx *c, const Plan *pl);
+
+// Tensor map of a [rows][kt] array of szv-byte values (row-major, 16-byte aligned
+// base) for TMA row gathers: one box = one whole row.  Encoded once per
+// (address, shape) and cached.
+int tma_map(const void *base, int64_t rows, int kt, int szv, CUtensorMap *out);
 
 // Blocks per kernel launch the planner aims for (about two waves of 8 CTAs per SM).
 int target_blocks(const nvd_graph_s *g);

@@ -963,27 +963,23 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
     const bool live = !Epi::NEEDS_LIVE || seg_live<KT>(c, seg);
     if (live) {
         if (blk.pad == 0) {
-            // light slices [i0, i1): a warp takes the next slice of G rows; the
-            // LPR lanes of group `gid` own its row gid, lane `sub` of the group
-            // columns col0..col0+VEC-1, so a row needs no cross-lane sum; entry j of
-            // the G rows is one load of columns and of weights, SPMM_UNROLL_* gathered
-            // neighbour rows are in flight, products are added in entry order
+            // light slices: warp w takes its fixed run of the block's slices (cut
+            // where the running entry count is closest to an equal share, as the TMA
+            // path does), so every thread adds the same rows in the same order on
+            // every run; a slice has G rows, the LPR lanes of group `gid` own its row
+            // gid, lane `sub` of the group columns col0..col0+VEC-1, so a row needs
+            // no cross-lane sum; entry j of the G rows is one load of columns and of
+            // weights, SPMM_UNROLL_* gathered neighbour rows are in flight, products
+            // are added in entry order
             const int gid = lane / LPR, col0 = (lane % LPR) * VEC;
             const TA *__restrict__ deg = deg_of<TA>(c);
             const TW *__restrict__ slw = reinterpret_cast<const TW *>(c.sl_w);
-            const int64_t ns = blk.i1 - blk.i0;
             Epi e = epi;
             e.prep(c, seg, col0);
-            int *s_next = reinterpret_cast<int *>(tot + C::ND_MAX * KT);
-            if (threadIdx.x == 0) *s_next = 0;
-            __syncthreads();
-            for (;;) {
-                // the next slice of the block (longest first) to whichever warp is free
-                int q = 0;
-                if (lane == 0) q = atomicAdd(s_next, 1);
-                q = __shfl_sync(NVD_FULLMASK, q, 0);
-                if (q >= ns) break;
-                const int64_t sl = blk.i0 + q;
+            const int32_t *split = c.sl_wsplit + b * (NWARP + 1);
+            const int warp = threadIdx.x >> 5;
+            const int64_t s_hi = blk.i0 + __ldg(split + warp + 1);
+            for (int64_t sl = blk.i0 + __ldg(split + warp); sl < s_hi; ++sl) {
                 const int64_t base = __ldg(c.sl_base + sl);
                 const int L = (int)((__ldg(c.sl_base + sl + 1) - base) / G);
                 const int32_t i = __ldg(c.sl_row + sl * G + gid);

@@ -20,15 +20,12 @@ static int launch_persistent(nvd_graph_s *g, const Ctx &c, const PersistArgs &a,
         set_error("persistent kernel does not fit on an SM");
         return NVD_ERR_UNSUPPORTED;
     }
+    // one co-resident wave (the grid barrier needs every CTA resident); every phase and
+    // the per-(owner, column) results loop over the grid, so any number of owners fits
     const int64_t resident = (int64_t)per_sm * g->num_sms;
     const int64_t need_res = ((int64_t)a.n_owner * KT + NT - 1) / NT;
-    int64_t grid = std::max<int64_t>({c.n_sblk, c.n_vblk, 1});
+    int64_t grid = std::max<int64_t>({c.n_sblk, c.n_vblk, need_res, 1});
     grid = std::min(grid, resident);
-    if (need_res > resident) {
-        set_error("persistent kernel: %d owners x %d columns exceed one wave", a.n_owner, KT);
-        return NVD_ERR_UNSUPPORTED;
-    }
-    grid = std::max(grid, need_res);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(NT);

@@ -148,9 +148,9 @@ __device__ void persistent_solve(const Ctx &c, const PersistArgs &a, char *smem)
         oz.meanv = c.meanx;
         vec_phase<TV, KT, decltype(oz), PU>(c, oz, smem);
     }
-    // per (owner, column) results
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid < (int64_t)a.n_owner * KT) {
+    // per (owner, column) results (grid-stride: any number of owners)
+    for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < (int64_t)a.n_owner * KT;
+         tid += (int64_t)gridDim.x * blockDim.x) {
         const int o = (int)(tid / KT), j = (int)(tid % KT);
         const Owner &ow = c.owners ? c.owners[o] : c.own0;
         ColResult rs{0.0, 0.0, 0.0, 0, NVD_OK};

@@ -113,8 +113,12 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     const size_t xsz = xdt == NVD_F64 ? 8 : 4;
     const bool host_in = o.flags & NVD_SOLVE_HOST_INPUTS;
     const bool d2_dev = o.flags & NVD_SOLVE_D2_DEVICE;
+    // persistent single-launch solve (FP64/FP32 modes; the launch timer needs the host
+    // loop); it runs the register-path SpMM, so it takes a plan laid out for that
+    const bool persistent = ((o.flags & NVD_SOLVE_PERSISTENT) || g->tuned_persistent[o.mode]) && !mixed &&
+                            !prof_enabled() && !z0;
     Plan *pl = nullptr, *pl64 = nullptr;
-    NVD_TRY(get_plan(g, KT, (int)szv, (int)szv, &pl));
+    NVD_TRY(get_plan(g, KT, (int)szv, (int)szv, &pl, !persistent));
     if (mixed) NVD_TRY(get_plan(g, KT, 8, 8, &pl64));
     Ctx c;
     memset(&c, 0, sizeof(c));
@@ -130,9 +134,6 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
         c.part = w.part;
         c.hsum = w.hsum;
     }
-    // persistent single-launch solve (FP64/FP32 modes; the launch timer needs the host loop)
-    const bool persistent = ((o.flags & NVD_SOLVE_PERSISTENT) || g->tuned_persistent[o.mode]) && !mixed &&
-                            !prof_enabled() && !z0;
     const int64_t sk = (int64_t)std::max(g->nseg, 1) * KT;
     unsigned *bar = nullptr;
     if (persistent) {
@@ -293,13 +294,14 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
             }
         }
     }
-    if (persistent) {
-        // a grid barrier that gave up (bounded wait) leaves its status in c.err
+    if (persistent || !(o.flags & NVD_SOLVE_NO_SYNC) || need_host) {
+        // a bounded device wait that gave up (the persistent kernel's grid barrier, a
+        // TMA gather that never arrived) leaves its status in c.err
         int32_t err = 0;
         NVD_TRY_CUDA(cudaMemcpyAsync(&err, c.err, 4, cudaMemcpyDeviceToHost, s));
         NVD_TRY_CUDA(cudaStreamSynchronize(s));
         if (err != 0) {
-            set_error("nvd_ge_distance: the persistent kernel's grid barrier gave up (status %d)", err);
+            set_error("nvd_ge_distance: a bounded device wait gave up (status %d)", err);
             return err;
         }
     }

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "graph.h"
+#include "stream.cuh"
 #include "vecops.cuh"
 
 namespace nvd {
@@ -59,6 +60,32 @@ __global__ void __launch_bounds__(NT, KT == 1 ? NVD_SPMV1_MINB : NVD_SPMM_MINB) 
     dev::spmm_block<dev::LdRO, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, smem);
 }
 
+// The multi-column SpMM over a stream plan (stream.cuh).  Register engine: three CTAs
+// per SM (85 registers a thread).  TMA engine (rows of 64 or 128 bytes): two CTAs per
+// SM, each with NWARP rings of TMA_SLOTS 512-byte steps in dynamic shared memory.
+#ifndef NVD_STREAM_MINB
+#define NVD_STREAM_MINB 3
+#endif
+template <class TV, class TW, class TA, int KT, class Epi>
+__global__ void __launch_bounds__(NT, NVD_STREAM_MINB) k_spmm_stream(Ctx c, Epi epi, const TV *src, TV *dst) {
+    __shared__ __align__(16) char smem[dev::SpCfg<TV, TA, KT>::SMEM];
+    pdl_trigger_and_wait();
+    dev::spmm_block_stream<false, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, nullptr, smem, nullptr);
+}
+
+template <class TV, class TA, int KT>
+constexpr int tma_kernel_smem() { return tma_ring_bytes() + dev::SpCfg<TV, TA, KT>::SMEM; }
+
+template <class TV, class TW, class TA, int KT, class Epi>
+__global__ void __launch_bounds__(NT, 2)
+    k_spmm_tma(Ctx c, Epi epi, const TV *src, TV *dst, const __grid_constant__ CUtensorMap tm) {
+    extern __shared__ __align__(128) char dsm[];
+    pdl_trigger_and_wait();
+    char *ring = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(dsm) + 127) & ~(uintptr_t)127);
+    dev::spmm_block_stream<true, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, ring, dsm + tma_ring_bytes(),
+                                                      &tm);
+}
+
 // lane vectors per thread per trip of the vector passes (one column / several)
 #ifndef NVD_VEC_U1
 #define NVD_VEC_U1 4
@@ -77,11 +104,12 @@ __global__ void __launch_bounds__(NT, NVD_VEC_MINB(KT)) k_vec(Ctx c, Op op) {
 // Launch one of the kernels above on NT threads, with the programmatic-dependent-
 // launch attribute when enabled.
 template <class... KArgs, class... Args>
-inline cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args &&...args) {
+inline cudaError_t launch_dependent_smem(void (*kern)(KArgs...), unsigned grid, size_t smem, cudaStream_t s,
+                                         Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -89,6 +117,10 @@ inline cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, cudaS
     cfg.attrs = at;
     cfg.numAttrs = NVD_USE_PDL ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+template <class... KArgs, class... Args>
+inline cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args &&...args) {
+    return launch_dependent_smem(kern, grid, 0, s, std::forward<Args>(args)...);
 }
 
 // Per (owner, column): sum d^2 and residual norms over the owner's segments, the
@@ -182,6 +214,11 @@ inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixe
 
 // ------------------------------------------------------------------ launchers
 
+// Let kernel `kern` use `bytes` of dynamic shared memory (once per kernel: every
+// translation unit that instantiates a kernel template has its own copy of it, so
+// the record is kept by function address).
+int allow_dynamic_smem(const void *kern, int bytes);
+
 // cls: timer class (0 the CG iteration's SpMV/SpMM, 2 the refinement residual).
 template <class TV, class TW, class TA, int KT, class Epi>
 inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cudaStream_t s,
@@ -190,6 +227,31 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
     if (c.sl_h != sp_slice_rows(KT, (int)sizeof(TV))) {
         set_error("internal: SpMV plan built for another tile width or precision");
         return NVD_ERR_UNSUPPORTED;
+    }
+    if constexpr (KT > 1) {
+        if (c.sl_stream && !c.sl_tma) {
+            const bool prof = prof_enabled() && prof_begin(s, cls);
+            NVD_TRY_CUDA(launch_dependent(k_spmm_stream<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, s, c, epi, src,
+                                          dst));
+            note_launch();
+            if (prof) prof_end(s, bytes);
+            return NVD_OK;
+        }
+    }
+    if constexpr (tma_tile(KT, (int)sizeof(TV))) {
+        if (c.sl_stream && c.sl_tma) {
+            // neighbour rows gathered by TMA; the tensor map describes src as [n][KT]
+            CUtensorMap tm;
+            NVD_TRY(tma_map(src, c.n, KT, (int)sizeof(TV), &tm));
+            auto kern = k_spmm_tma<TV, TW, TA, KT, Epi>;
+            constexpr int SM = tma_kernel_smem<TV, TA, KT>();
+            NVD_TRY(allow_dynamic_smem((const void *)kern, SM));
+            const bool prof = prof_enabled() && prof_begin(s, cls);
+            NVD_TRY_CUDA(launch_dependent_smem(kern, (unsigned)c.n_sblk, (size_t)SM, s, c, epi, src, dst, tm));
+            note_launch();
+            if (prof) prof_end(s, bytes);
+            return NVD_OK;
+        }
     }
     const bool prof = prof_enabled() && prof_begin(s, cls);
     NVD_TRY_CUDA(launch_dependent(k_spmm<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, s, c, epi, src, dst));

@@ -8,6 +8,8 @@
 //     sub-items (whole-row warp items or fixed-size chunks) instead of being
 //     stored in the sliced layout, where it would make its whole slice as long;
 //   * the number of light CTA blocks per SpMV launch;
+//   * the gather engine of the multi-column SpMM (register slices, register stream,
+//     TMA stream);
 //   * host-driven iterations versus one persistent cooperative launch per tile;
 //   * two kernels per iteration (direction update folded into the SpMV) or three.
 // Each candidate runs real solves on this graph with seeded synthetic
@@ -211,6 +213,37 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
             }
         }
     }
+    // 3b. gathers of the multi-column SpMM: register slices (default), register stream
+    //     and, where the tile width allows it, TMA stream
+    if (best_kt > 1) {
+        std::vector<int> modes = {0, 1};
+        if (tma_tile(best_kt, b.mode == NVD_MODE_FP64 ? 8 : 4)) modes.push_back(2);
+        for (int gmode : modes) {
+            if (gmode == g->sp.gather) continue;
+            SpParams cand = g->sp;
+            cand.gather = gmode;
+            const SpParams keep = g->sp;
+            double base = INFINITY, alt = INFINITY;
+            for (int rep = 0; rep < 2; ++rep) {
+                double it = 0;
+                g->sp = keep;
+                int rc = b.per_iter(best_kt, false, &it);
+                if (rc) return fail(rc);
+                base = std::min(base, it);
+                g->sp = cand;
+                rc = b.per_iter(best_kt, false, &it);
+                if (rc) return fail(rc);
+                alt = std::min(alt, it);
+            }
+            ++ntried;
+            if (alt < base * 0.98) {
+                best_iter = alt;
+            } else {
+                g->sp = keep;
+                best_iter = std::min(best_iter, base);
+            }
+        }
+    }
     // 4. one persistent launch per tile (not for the mixed mode, whose outer loop
     //    runs on the host)
     int pers = 0;
@@ -269,7 +302,8 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
     // drop the plans of the losing candidates
     for (auto it = g->plans.begin(); it != g->plans.end();) {
         const SpParams &p = it->second->sp;
-        if (p.row_max_pct != g->sp.row_max_pct || p.blocks_pct != g->sp.blocks_pct) it = g->plans.erase(it);
+        if (p.row_max_pct != g->sp.row_max_pct || p.blocks_pct != g->sp.blocks_pct || p.gather != g->sp.gather)
+            it = g->plans.erase(it);
         else ++it;
     }
     g->tuned_kt[mode] = single ? 0 : best_kt;
@@ -282,6 +316,8 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
         out->persistent = pers;
         out->candidates = ntried;
         out->fold_direction = fold;
+        out->gather = g->sp.gather;
+        out->reserved = 0;
         out->ms_per_iter = best_iter;
         out->ms_per_pair_iter = best_iter / best_kt;
     }
@@ -295,12 +331,14 @@ extern "C" int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_
     if (!g || !t || mode < NVD_MODE_FP64 || mode > NVD_MODE_MIXED ||
         !(t->kt == 0 || t->kt == 1 || t->kt == 4 || t->kt == 8 || t->kt == 16 || t->kt == 32) ||
         t->row_max_pct < 10 || t->row_max_pct > 1000 || t->blocks_pct < 10 || t->blocks_pct > 1000 ||
-        (t->persistent != 0 && t->persistent != 1) || (t->fold_direction != 0 && t->fold_direction != 1)) {
+        (t->persistent != 0 && t->persistent != 1) || (t->fold_direction != 0 && t->fold_direction != 1) ||
+        t->gather < 0 || t->gather > 2) {
         set_error("nvd_graph_set_tuning: invalid argument");
         return NVD_ERR_INVALID_ARG;
     }
     g->sp.row_max_pct = t->row_max_pct;
     g->sp.blocks_pct = t->blocks_pct;
+    g->sp.gather = t->gather;
     g->tuned_kt[mode] = t->kt;
     g->tuned_persistent[mode] = t->persistent;
     g->tuned_fold[mode] = t->fold_direction;

@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["nvd_graph_create", "nvd_graph_destroy", "nvd_graph_info", "nvd_ge_distance",
                  "nvd_ge_distance_batched", "nvd_ge_grad", "nvd_status_string", "nvd_laplacian_apply",
-                 "nvd_effective_resistance"]:
+                 "nvd_effective_resistance", "nvd_graph_set_weights"]:
         assert must in names
 
 

@@ -90,17 +90,26 @@ def test_batched_uneven_pair_counts_and_multiple_tiles(nvd, small_batch):
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("kt", [1, 8, 32])
 def test_persistent_single_graph_bitwise_equals_host_loop(nvd, mode, kt, fold):
+    """The persistent kernel runs the per-slice register SpMM: with that gather engine
+    the host loop runs the same sums in the same order (bitwise equal); with the
+    stream engine (multi-column tiles) only the grouping of the inner products
+    differs."""
     wl = synth.workload_ba_small()
     g = wl.graph
     X, Y = wl.pairs(0, 12)
     G = nvd.Graph.from_csr(g)
     if mode == 0 and kt == 32:
         kt = 16
-    a, za = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, return_z=True, fold_direction=fold)
     b, zb = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, persistent=True, return_z=True,
                             fold_direction=fold)
+    G.set_tuning(mode=mode, gather=nvd.GATHER_SLICES)
+    a, za = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, return_z=True, fold_direction=fold)
     assert torch.equal(a, b)
     assert torch.equal(za, zb)
+    G.set_tuning(mode=mode, gather=nvd.GATHER_STREAM)
+    t, zt = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, return_z=True, fold_direction=fold)
+    tol = 1e-12 if mode == 0 else 1e-5
+    assert rel(t.cpu().numpy(), b.cpu().numpy()) < tol
 
 
 @pytest.mark.parametrize("mode,tol", [(0, 1e-11), (1, 1e-5)])
@@ -144,3 +153,32 @@ def test_batched_full_size_all_graphs(nvd, full_batch, mode, rtol, tol):
     assert np.all(np.isfinite(d2)) and np.all(d2 > 0)
     assert all(s["status"] == 0 for s in st)
     assert rel(d2, want) < tol
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode,rtol,tol", [(1, 1e-6, 1e-4), (0, 1e-12, 1e-9)])
+def test_batched_more_owner_columns_than_the_grid_has_threads(nvd, mode, rtol, tol):
+    """3,000 small random graphs (6..23 nodes, some disconnected) with 32 pairs each:
+    96,000 (graph, pair) columns, more than one co-resident wave of the persistent
+    kernel has threads, so the per-column results are collected in grid-stride
+    loops; every d^2 against the dense oracle."""
+    from oracle import dense
+    rng = np.random.default_rng(77)
+    graphs, xs, ys, want = [], [], [], []
+    for _ in range(3000):
+        n = int(rng.integers(6, 24))
+        eu, ev = synth.random_gnp_small(n, 0.35, rng)
+        if len(eu) == 0:
+            eu, ev = np.array([0]), np.array([1])
+        g = synth.csr_from_edges(n, eu, ev, rng.uniform(0.5, 2.0, len(eu)))
+        X, Y = rng.random((32, n)), rng.random((32, n))
+        graphs.append(g)
+        xs.append(X)
+        ys.append(Y)
+        want.append(dense.ge_d2_eig(g.n, g.rowptr, g.colidx, g.w, X, Y))
+    want = np.concatenate(want)
+    G = [nvd.Graph.from_csr(g) for g in graphs]
+    d2 = nvd.ge_distance_batched(G, [on(x) for x in xs], [on(y) for y in ys], mode=mode, rtol=rtol).numpy()
+    pos = want > 1e-12
+    assert rel(d2[pos], want[pos]) < tol
+    assert np.all(np.abs(d2[~pos]) < 1e-9)
