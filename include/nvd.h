@@ -59,6 +59,9 @@ typedef enum {
 
 #define NVD_GRAPH_DEVICE_PTRS 1u    /* rowptr/colidx/w are device pointers (else host) */
 #define NVD_GRAPH_SKIP_SYM_CHECK 2u /* trust the caller: skip the symmetry check */
+#define NVD_GRAPH_REORDER_DEGREE 4u /* store each component's nodes by degree, highest first (the rows the
+                                       SpMM gathers most form one contiguous run; results in the caller's
+                                       node order as always) */
 
 /*
  * nvd_graph_create -- build a graph handle from a CSR adjacency (Section 3.1:
@@ -198,7 +201,9 @@ typedef struct {
     int32_t gather;        /* multi-column SpMM: 0 register loads per slice (default), 1 register loads
                               over each warp's step stream, 2 TMA gathers over the stream (tiles whose
                               rows are 64 or 128 bytes; others use 1) */
-    int32_t reserved;
+    int32_t l2_hot;        /* 1: graphs made with NVD_GRAPH_REORDER_DEGREE keep the gathered vector's
+                              highest-degree rows persisting in L2 during multi-column SpMMs (this
+                              process's L2 set-aside is requested on first use) */
     double ms_per_iter;    /* device time of one PCG iteration of one tile, chosen setting */
     double ms_per_pair_iter; /* ms_per_iter / kt */
 } nvd_tune_result;
@@ -233,8 +238,8 @@ int nvd_graph_tune(nvd_graph_t g, int32_t mode, int32_t k, uint32_t flags, nvd_t
 /*
  * nvd_graph_set_tuning -- apply a setting (for example one nvd_graph_tune chose
  * earlier for the same graph) without timing anything.  Reads kt (0 = no
- * preference), row_max_pct and blocks_pct (10..1000), persistent and
- * fold_direction (0/1), gather (0..2); the other fields are ignored.  Host only; plans built
+ * preference), row_max_pct and blocks_pct (10..1000), persistent,
+ * fold_direction and l2_hot (0/1), gather (0..2); the other fields are ignored.  Host only; plans built
  * afterwards use it.
  * Errors: NVD_ERR_INVALID_ARG (NULL pointer, bad mode or field).
  */

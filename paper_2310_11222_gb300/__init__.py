@@ -44,6 +44,7 @@ SOLVE_D2_STOP = 128
 SOLVE_ELIMINATE = 256
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_SYM_CHECK = 2
+GRAPH_REORDER_DEGREE = 4
 TUNE_SINGLE_RHS = 1
 GATHER_SLICES, GATHER_STREAM, GATHER_TMA = 0, 1, 2   # nvd_tune_result.gather
 
@@ -82,7 +83,7 @@ class TuneResult(ctypes.Structure):
     """Mirror of ``nvd_tune_result``."""
     _fields_ = [("kt", ctypes.c_int32), ("row_max_pct", ctypes.c_int32), ("blocks_pct", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("candidates", ctypes.c_int32), ("fold_direction", ctypes.c_int32),
-                ("gather", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gather", ctypes.c_int32), ("l2_hot", ctypes.c_int32),
                 ("ms_per_iter", ctypes.c_double), ("ms_per_pair_iter", ctypes.c_double)]
 
 
@@ -217,12 +218,13 @@ class Graph:
     from the host; torch CUDA tensors are read on the device.
     """
 
-    def __init__(self, rowptr, colidx, w=None, *, skip_sym_check: bool = False, device=None):
+    def __init__(self, rowptr, colidx, w=None, *, skip_sym_check: bool = False, reorder: bool = False,
+                 device=None):
         torch = _torch()
         lib = load_library()
         self._lib = lib
         self.handle = ctypes.c_void_p(None)
-        flags = GRAPH_SKIP_SYM_CHECK if skip_sym_check else 0
+        flags = (GRAPH_SKIP_SYM_CHECK if skip_sym_check else 0) | (GRAPH_REORDER_DEGREE if reorder else 0)
         keep = []
         if isinstance(rowptr, np.ndarray):
             rp = np.ascontiguousarray(rowptr, dtype=np.int64)
@@ -323,12 +325,14 @@ class Graph:
         return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
     def set_tuning(self, *, mode: int = 0, kt: int = 0, row_max_pct: int = 100, blocks_pct: int = 100,
-                   persistent: bool = False, fold_direction: bool = False, gather: int = GATHER_SLICES):
+                   persistent: bool = False, fold_direction: bool = False, gather: int = GATHER_SLICES,
+                   l2_hot: bool = False):
         """Apply a work-decomposition setting without timing (``nvd_graph_set_tuning``).
-        ``gather``: GATHER_SLICES (default), GATHER_STREAM or GATHER_TMA."""
+        ``gather``: GATHER_SLICES (default), GATHER_STREAM or GATHER_TMA; ``l2_hot``: keep the
+        highest-degree rows of a degree-ordered graph persisting in L2."""
         r = TuneResult(kt=int(kt), row_max_pct=int(row_max_pct), blocks_pct=int(blocks_pct),
                        persistent=int(bool(persistent)), fold_direction=int(bool(fold_direction)),
-                       gather=int(gather))
+                       gather=int(gather), l2_hot=int(bool(l2_hot)))
         _check(self._lib.nvd_graph_set_tuning(self.handle, int(mode), ctypes.byref(r)), "nvd_graph_set_tuning")
 
     @property

@@ -46,6 +46,25 @@ std::atomic<int64_t> g_kernel_launches{0};
 
 void note_launch(int64_t n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
+size_t l2_persist_bytes() {
+    static std::mutex mu;
+    static std::vector<std::pair<int, size_t>> done;   // device, usable window bytes
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto &d : done)
+        if (d.first == dev) return d.second;
+    int persist = 0, window = 0;
+    size_t use = 0;
+    if (cudaDeviceGetAttribute(&persist, cudaDevAttrMaxPersistingL2CacheSize, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&window, cudaDevAttrMaxAccessPolicyWindowSize, dev) == cudaSuccess && persist > 0 &&
+        window > 0 && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist) == cudaSuccess)
+        use = std::min((size_t)persist, (size_t)window);
+    cudaGetLastError();
+    done.emplace_back(dev, use);
+    return use;
+}
+
 int allow_dynamic_smem(const void *kern, int bytes) {
     static std::mutex mu;
     static std::vector<std::tuple<const void *, int, int>> done;   // kernel, device, bytes

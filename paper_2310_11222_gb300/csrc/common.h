@@ -145,6 +145,9 @@ struct Ctx {
     int32_t sl_tma;                 // 1: a stream plan gathered by TMA (tma.cuh)
     const int32_t *sl_wsplit;       // [n_sblk][NWARP + 1] first slice of each warp, relative to the block's
     const longlong2 *sl_wrun;       // stream plans: [n_sblk][NWARP] {first entry, steps} of each warp
+    // ---- L2 residency of the gathered vector's hot rows (degree-ordered graphs)
+    int64_t hot_begin, hot_rows;    // rows [hot_begin, hot_begin + hot_rows) of the gathered vector
+    int32_t l2_hot;                 // 1: multi-column SpMMs keep those rows persisting in L2
     // ---- persistent-kernel grid barrier
     unsigned *bar_count, *bar_gen;
     int32_t bar_extra;              // arrivals awaited beyond the grid (0; 1 only to test the timeout)

@@ -885,6 +885,9 @@ void fill_graph_ctx(const nvd_graph_s *g, const Plan *pl, Ctx *c) {
     c->seg_end = g->seg_end.as<int64_t>();
     c->seg_owner = g->seg_owner.as<int32_t>();
     c->perm = g->perm.as<int32_t>();
+    c->hot_begin = g->hot_begin;
+    c->hot_rows = g->hot_rows;
+    c->l2_hot = g->sp.l2_hot;
     if (pl) {
         set_sp_plan(c, pl);
         c->vblk = pl->vblk.as<Block>();
@@ -939,7 +942,7 @@ static int graph_create_impl(nvd_graph_t *out, int64_t n, int64_t nnz, const int
                              cudaStream_t s) {
     if (n < 1 || n > INT32_MAX - 1 || nnz < 0 || !rowptr || (nnz > 0 && !colidx) ||
         (wdtype != NVD_F32 && wdtype != NVD_F64) ||
-        (flags & ~(NVD_GRAPH_DEVICE_PTRS | NVD_GRAPH_SKIP_SYM_CHECK))) {
+        (flags & ~(NVD_GRAPH_DEVICE_PTRS | NVD_GRAPH_SKIP_SYM_CHECK | NVD_GRAPH_REORDER_DEGREE))) {
         set_error("nvd_graph_create: invalid argument (n=%lld nnz=%lld wdtype=%d flags=%u)",
                   (long long)n, (long long)nnz, wdtype, flags);
         return NVD_ERR_INVALID_ARG;
@@ -1051,13 +1054,24 @@ static int graph_create_impl(nvd_graph_t *out, int64_t n, int64_t nnz, const int
         }
     g->ncomp = ncomp;
     std::vector<int32_t> perm;  // internal -> user
-    if (!contiguous) {
-        // stable counting sort of nodes by their component's smallest node
+    const bool reorder = flags & NVD_GRAPH_REORDER_DEGREE;
+    if (!contiguous || reorder) {
+        // stable counting sort of nodes by their component's smallest node; with
+        // NVD_GRAPH_REORDER_DEGREE each component's nodes then by stored entries,
+        // most first (ties by node), so its most gathered rows are one contiguous run
         std::vector<int64_t> start(n + 1, 0);
         for (int64_t r = 0; r < n; ++r) start[r + 1] = start[r] + cnt[r];
         perm.resize(n);
         std::vector<int64_t> fill(start.begin(), start.end() - 1);
         for (int64_t i = 0; i < n; ++i) perm[fill[root[i]]++] = (int32_t)i;
+        if (reorder) {
+            const std::vector<int64_t> &rp = g->h_rowptr;
+            for (int64_t r = 0; r < n; ++r)
+                if (cnt[r] > 1)
+                    std::stable_sort(perm.begin() + start[r], perm.begin() + start[r + 1], [&](int32_t a, int32_t b) {
+                        return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
+                    });
+        }
         std::vector<int32_t> iperm(n);
         for (int64_t i = 0; i < n; ++i) iperm[perm[i]] = (int32_t)i;
         std::vector<int32_t> col;
@@ -1122,6 +1136,14 @@ static int graph_create_impl(nvd_graph_t *out, int64_t n, int64_t nnz, const int
         }
     }
     g->nseg = (int32_t)g->h_seg_begin.size();
+    if (reorder && g->nseg > 0) {
+        g->reordered = true;
+        int32_t big = 0;
+        for (int32_t sg = 1; sg < g->nseg; ++sg)
+            if (g->h_seg_end[sg] - g->h_seg_begin[sg] > g->h_seg_end[big] - g->h_seg_begin[big]) big = sg;
+        g->hot_begin = g->h_seg_begin[big];
+        g->hot_rows = g->h_seg_end[big] - g->h_seg_begin[big];
+    }
     g->h_seg_of.assign(n, -1);
     for (int32_t sg = 0; sg < g->nseg; ++sg)
         for (int64_t i = g->h_seg_begin[sg]; i < g->h_seg_end[sg]; ++i)

@@ -73,6 +73,8 @@ struct SpParams {
     int32_t blocks_pct = 100;
     int32_t gather = 0;          // multi-column SpMM: 0 register slices, 1 register stream, 2 TMA stream
                                  // (2 only where tma_tile holds, else 1); the tuner tries the others
+    int32_t l2_hot = 0;          // 1: the multi-column SpMM keeps the gathered vector's hot rows (the
+                                 // degree-ordered head of the largest component) persisting in L2
 };
 
 // Work decomposition for one (KT, vector size, accumulator size, SpParams).
@@ -117,6 +119,8 @@ struct nvd_graph_s {
     // of internal entry e are ient_src[ient_ptr[e] .. ient_ptr[e+1]), increasing
     nvd::DevBuf ient_ptr, ient_src;
     int32_t ncomp = 0, nseg = 0;
+    bool reordered = false;      // NVD_GRAPH_REORDER_DEGREE: nodes by degree inside each component
+    int64_t hot_begin = 0, hot_rows = 0;   // reordered: the largest segment's rows (highest degree first)
     int64_t n_singleton = 0;
     std::vector<int64_t> h_rowptr, h_seg_begin, h_seg_end;
     std::vector<int32_t> h_seg_of;  // user node -> its segment (-1: isolated node)
@@ -157,6 +161,11 @@ void set_sp_plan(Ctx *c, const Plan *pl);
 // base) for TMA row gathers: one box = one whole row.  Encoded once per
 // (address, shape) and cached.
 int tma_map(const void *base, int64_t rows, int kt, int szv, CUtensorMap *out);
+
+// Bytes of L2 this process may keep persisting for one access-policy window on the
+// current device (the set-aside is requested once per device, on first use); 0 if
+// the device has none.
+size_t l2_persist_bytes();
 
 // Blocks per kernel launch the planner aims for (about two waves of 8 CTAs per SM).
 int target_blocks(const nvd_graph_s *g);

@@ -685,13 +685,28 @@ __device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, int seg
         TA acc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = 0;
-        for (int64_t e = it.e0 + warp * G + gi; e < it.e1; e += NWARP * G) {
-            const int ca = __ldcs(c.colidx + e);
-            const TA wa = (TA)__ldcs(w + e);
-            TV pa[VEC];
-            ldv<LD, TV, VEC>(src + (int64_t)ca * KT + col0, pa);
+        // entries e, e + S, e + 2S, ... of this lane group (S = NWARP * G), U of them
+        // gathered together before their products are added in entry order
+        constexpr int U = sizeof(TV) == 8 ? SPMM_UNROLL_F64 : SPMM_UNROLL_F32;
+        constexpr int64_t S = (int64_t)NWARP * G;
+        for (int64_t e = it.e0 + warp * G + gi; e < it.e1; e += U * S) {
+            int ca[U];
+            TA wa[U];
+            TV pa[U][VEC];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] += wa * (TA)pa[v];
+            for (int u = 0; u < U; ++u)
+                if (e + u * S < it.e1) {
+                    ca[u] = __ldcs(c.colidx + e + u * S);
+                    wa[u] = (TA)__ldcs(w + e + u * S);
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (e + u * S < it.e1) ldv<LD, TV, VEC>(src + (int64_t)ca[u] * KT + col0, pa[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (e + u * S < it.e1)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] += wa[u] * (TA)pa[u][v];
         }
 #pragma unroll
         for (int off = LPR; off < 32; off <<= 1)

@@ -103,24 +103,58 @@ __global__ void __launch_bounds__(NT, NVD_VEC_MINB(KT)) k_vec(Ctx c, Op op) {
 
 // Launch one of the kernels above on NT threads, with the programmatic-dependent-
 // launch attribute when enabled.
+// An L2 access-policy window for one launch (bytes = 0: none).
+struct L2Window {
+    const void *base = nullptr;
+    size_t bytes = 0;
+};
+
 template <class... KArgs, class... Args>
 inline cudaError_t launch_dependent_smem(void (*kern)(KArgs...), unsigned grid, size_t smem, cudaStream_t s,
-                                         Args &&...args) {
+                                         L2Window win, Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    if (NVD_USE_PDL) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    if (win.bytes) {
+        at[na].id = cudaLaunchAttributeAccessPolicyWindow;
+        at[na].val.accessPolicyWindow.base_ptr = const_cast<void *>(win.base);
+        at[na].val.accessPolicyWindow.num_bytes = win.bytes;
+        at[na].val.accessPolicyWindow.hitRatio = 1.0f;
+        at[na].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        at[na].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        ++na;
+    }
     cfg.attrs = at;
-    cfg.numAttrs = NVD_USE_PDL ? 1 : 0;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 template <class... KArgs, class... Args>
 inline cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args &&...args) {
-    return launch_dependent_smem(kern, grid, 0, s, std::forward<Args>(args)...);
+    return launch_dependent_smem(kern, grid, 0, s, L2Window(), std::forward<Args>(args)...);
+}
+
+// The window of a multi-column SpMM: the first rows of the gathered vector's hot run
+// (the degree-ordered head of the largest component), as many as the process's L2
+// set-aside holds.
+template <class TV, int KT>
+inline L2Window spmm_window(const Ctx &c, const TV *src) {
+    L2Window w;
+    if (KT == 1 || !c.l2_hot || c.hot_rows <= 0) return w;
+    const size_t cap = l2_persist_bytes();
+    const size_t row = (size_t)KT * sizeof(TV);
+    if (cap < row) return w;
+    w.base = src + c.hot_begin * KT;
+    w.bytes = std::min((size_t)c.hot_rows * row, cap);
+    return w;
 }
 
 // Per (owner, column): sum d^2 and residual norms over the owner's segments, the
@@ -231,8 +265,8 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
     if constexpr (KT > 1) {
         if (c.sl_stream && !c.sl_tma) {
             const bool prof = prof_enabled() && prof_begin(s, cls);
-            NVD_TRY_CUDA(launch_dependent(k_spmm_stream<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, s, c, epi, src,
-                                          dst));
+            NVD_TRY_CUDA(launch_dependent_smem(k_spmm_stream<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, 0, s,
+                                               spmm_window<TV, KT>(c, src), c, epi, src, dst));
             note_launch();
             if (prof) prof_end(s, bytes);
             return NVD_OK;
@@ -247,14 +281,16 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
             constexpr int SM = tma_kernel_smem<TV, TA, KT>();
             NVD_TRY(allow_dynamic_smem((const void *)kern, SM));
             const bool prof = prof_enabled() && prof_begin(s, cls);
-            NVD_TRY_CUDA(launch_dependent_smem(kern, (unsigned)c.n_sblk, (size_t)SM, s, c, epi, src, dst, tm));
+            NVD_TRY_CUDA(launch_dependent_smem(kern, (unsigned)c.n_sblk, (size_t)SM, s, spmm_window<TV, KT>(c, src),
+                                               c, epi, src, dst, tm));
             note_launch();
             if (prof) prof_end(s, bytes);
             return NVD_OK;
         }
     }
     const bool prof = prof_enabled() && prof_begin(s, cls);
-    NVD_TRY_CUDA(launch_dependent(k_spmm<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, s, c, epi, src, dst));
+    NVD_TRY_CUDA(launch_dependent_smem(k_spmm<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, 0, s,
+                                       spmm_window<TV, KT>(c, src), c, epi, src, dst));
     note_launch();
     if (prof) prof_end(s, bytes);
     return NVD_OK;
@@ -476,8 +512,11 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
         // The first inner solve goes to opts.rtol.  A later one solves for the
         // correction L c = r of the current z; its d^2 change r^T c is what decides
         // convergence and the variational d^2 error after it is quadratic in its
-        // residual, so a relative residual of 1e-2 (or opts.rtol if looser) suffices.
-        const double rtol_step = step == 0 ? o.rtol : std::max(o.rtol, 1e-2);
+        // residual, so a relative residual of 1e-1 (or opts.rtol if looser) suffices: it
+        // measures the remaining d^2 error to about 1% and leaves about 1% of it.  z
+        // itself is only linearly accurate in that residual, so when z is returned the
+        // corrections go to 1e-2.
+        const double rtol_step = step == 0 ? o.rtol : std::max(o.rtol, io.z ? 1e-2 : 1e-1);
         ci.rtol2 = rtol_step * rtol_step;
         NVD_TRY_CUDA(cudaMemsetAsync(c.n_active, 0, 4, s));
         dev::OpInit<float, KT> oi;

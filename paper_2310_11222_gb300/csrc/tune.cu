@@ -188,7 +188,11 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
     //    back, twice each, and the candidate must win by 2%: single timings differ
     //    by a few percent from run to run)
     for (int pass = 0; pass < 2; ++pass) {
-        for (int pct : {50, 200}) {
+        // fewer, larger blocks (25%) balance the fixed warp runs of multi-column
+        // tiles better, and at four CTAs per SM fill one wave of 608 blocks
+        std::vector<int> pcts = {50, 200};
+        if (pass == 1 && best_kt > 1) pcts.insert(pcts.begin(), 25);
+        for (int pct : pcts) {
             SpParams cand = g->sp;
             (pass == 0 ? cand.row_max_pct : cand.blocks_pct) = pct;
             const SpParams keep = g->sp;
@@ -317,7 +321,7 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
         out->candidates = ntried;
         out->fold_direction = fold;
         out->gather = g->sp.gather;
-        out->reserved = 0;
+        out->l2_hot = g->sp.l2_hot;
         out->ms_per_iter = best_iter;
         out->ms_per_pair_iter = best_iter / best_kt;
     }
@@ -332,13 +336,14 @@ extern "C" int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_
         !(t->kt == 0 || t->kt == 1 || t->kt == 4 || t->kt == 8 || t->kt == 16 || t->kt == 32) ||
         t->row_max_pct < 10 || t->row_max_pct > 1000 || t->blocks_pct < 10 || t->blocks_pct > 1000 ||
         (t->persistent != 0 && t->persistent != 1) || (t->fold_direction != 0 && t->fold_direction != 1) ||
-        t->gather < 0 || t->gather > 2) {
+        t->gather < 0 || t->gather > 2 || (t->l2_hot != 0 && t->l2_hot != 1)) {
         set_error("nvd_graph_set_tuning: invalid argument");
         return NVD_ERR_INVALID_ARG;
     }
     g->sp.row_max_pct = t->row_max_pct;
     g->sp.blocks_pct = t->blocks_pct;
     g->sp.gather = t->gather;
+    g->sp.l2_hot = t->l2_hot;
     g->tuned_kt[mode] = t->kt;
     g->tuned_persistent[mode] = t->persistent;
     g->tuned_fold[mode] = t->fold_direction;

@@ -94,3 +94,30 @@ def test_stream_under_other_work_decompositions(nvd, case, gather, row_max_pct, 
     G.set_tuning(mode=1, row_max_pct=row_max_pct, blocks_pct=blocks_pct, gather=gather)
     d2 = nvd.ge_distance(G, on(X), on(Y), mode=1, kt=32, rtol=1e-7)
     assert rel(d2.cpu().numpy(), want) < 1e-4
+
+
+def test_degree_order_and_l2_window(nvd, case):
+    """NVD_GRAPH_REORDER_DEGREE stores each component's nodes by degree (the hub rows
+    first): d^2, z in the caller's node order and the weight gradient on the caller's
+    entries match the graph in its own order; keeping the hot rows persisting in L2
+    changes no result bit."""
+    g, X, Y, want = case
+    G = nvd.Graph.from_csr(g)
+    R = nvd.Graph.from_csr(g, reorder=True)
+    for mode, kt, kw, tol in ((0, 16, dict(rtol=1e-12), 1e-9), (1, 32, dict(rtol=1e-7), 1e-4),
+                              (2, 32, dict(rtol=1e-5, d2_rtol=1e-11), 1e-9)):
+        a, za = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, return_z=True, **kw)
+        outs = []
+        for hot in (False, True):
+            R.set_tuning(mode=mode, l2_hot=hot)
+            b, zb = nvd.ge_distance(R, on(X), on(Y), mode=mode, kt=kt, return_z=True, **kw)
+            assert rel(b.cpu().numpy(), want) < tol, (mode, hot)
+            assert rel(b.cpu().numpy(), a.cpu().numpy()) < tol
+            zs = float(za.abs().max())
+            assert float((zb - za).abs().max()) <= (1e-8 if mode != 1 else 1e-3) * zs
+            outs.append((b, zb))
+        assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    z = nvd.ge_distance(G, on(X), on(Y), rtol=1e-12, return_z=True)[1]
+    gw, _, _ = nvd.ge_grad(G, z, on(np.ones(X.shape[0])))
+    gr, _, _ = nvd.ge_grad(R, z, on(np.ones(X.shape[0])))
+    assert torch.equal(gw, gr)                       # the same sums per caller entry, mapped back

@@ -71,7 +71,7 @@ def test_tune_then_solve(nvd, hub_graph, mode):
     G = nvd.Graph.from_csr(g)
     r = G.tune(mode=mode, k=12)
     assert r["kt"] in (1, 4, 8, 16, 32) and (mode != 0 or r["kt"] <= 16)
-    assert r["row_max_pct"] in (50, 100, 200) and r["blocks_pct"] in (50, 100, 200)
+    assert r["row_max_pct"] in (50, 100, 200) and r["blocks_pct"] in (25, 50, 100, 200)
     assert r["persistent"] in (0, 1) and (mode != 2 or r["persistent"] == 0)
     assert r["fold_direction"] in (0, 1)
     assert r["candidates"] >= 5 and r["ms_per_iter"] > 0
