@@ -199,7 +199,8 @@ typedef struct {
     int32_t candidates;    /* configurations timed */
     int32_t fold_direction; /* 1: two kernels per iteration (NVD_SOLVE_FOLD_DIRECTION) were faster */
     int32_t gather;        /* multi-column SpMM: 0 register loads per slice (default), 1 register loads
-                              over each warp's step stream, 2 TMA gathers over the stream (tiles whose
+                              over each warp's step stream, 2 TMA gathers over the stream, 3 per-lane
+                              asynchronous copies (cp.async) over the stream (2 and 3: tiles whose
                               rows are 64 or 128 bytes; others use 1) */
     int32_t l2_hot;        /* 1: graphs made with NVD_GRAPH_REORDER_DEGREE keep the gathered vector's
                               highest-degree rows persisting in L2 during multi-column SpMMs (this
@@ -213,7 +214,8 @@ typedef struct {
  * this graph by timing it: tile width (k-blocking) for k pairs, the row-split
  * limit (longer rows become split sub-items), the number of SpMV blocks, the
  * gather engine of multi-column SpMMs (register loads per slice, register loads
- * over a warp's step stream, TMA row gathers into shared memory), host-driven
+ * over a warp's step stream, TMA row gathers or per-lane asynchronous copies
+ * into shared memory), host-driven
  * versus persistent iterations, and two versus three kernels per iteration
  * (NVD_SOLVE_FOLD_DIRECTION).  Candidates run real solves with
  * seeded synthetic right-hand sides for a fixed number of iterations on
@@ -239,7 +241,7 @@ int nvd_graph_tune(nvd_graph_t g, int32_t mode, int32_t k, uint32_t flags, nvd_t
  * nvd_graph_set_tuning -- apply a setting (for example one nvd_graph_tune chose
  * earlier for the same graph) without timing anything.  Reads kt (0 = no
  * preference), row_max_pct and blocks_pct (10..1000), persistent,
- * fold_direction and l2_hot (0/1), gather (0..2); the other fields are ignored.  Host only; plans built
+ * fold_direction and l2_hot (0/1), gather (0..3); the other fields are ignored.  Host only; plans built
  * afterwards use it.
  * Errors: NVD_ERR_INVALID_ARG (NULL pointer, bad mode or field).
  */

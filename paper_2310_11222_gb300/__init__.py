@@ -46,7 +46,7 @@ GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_SYM_CHECK = 2
 GRAPH_REORDER_DEGREE = 4
 TUNE_SINGLE_RHS = 1
-GATHER_SLICES, GATHER_STREAM, GATHER_TMA = 0, 1, 2   # nvd_tune_result.gather
+GATHER_SLICES, GATHER_STREAM, GATHER_TMA, GATHER_ACOPY = 0, 1, 2, 3   # nvd_tune_result.gather
 
 STATUS = {0: "NVD_OK", 1: "NVD_ERR_INVALID_ARG", 2: "NVD_ERR_NOT_SYMMETRIC", 3: "NVD_ERR_BAD_WEIGHT",
           4: "NVD_ERR_OOM", 5: "NVD_ERR_CUDA", 6: "NVD_ERR_NOT_CONVERGED", 7: "NVD_ERR_NUMERIC",
@@ -328,7 +328,7 @@ class Graph:
                    persistent: bool = False, fold_direction: bool = False, gather: int = GATHER_SLICES,
                    l2_hot: bool = False):
         """Apply a work-decomposition setting without timing (``nvd_graph_set_tuning``).
-        ``gather``: GATHER_SLICES (default), GATHER_STREAM or GATHER_TMA; ``l2_hot``: keep the
+        ``gather``: GATHER_SLICES (default), GATHER_STREAM, GATHER_TMA or GATHER_ACOPY; ``l2_hot``: keep the
         highest-degree rows of a degree-ordered graph persisting in L2."""
         r = TuneResult(kt=int(kt), row_max_pct=int(row_max_pct), blocks_pct=int(blocks_pct),
                        persistent=int(bool(persistent)), fold_direction=int(bool(fold_direction)),

@@ -288,7 +288,7 @@ int batched_impl(const nvd_graph_t *gs, int32_t G, const int32_t *k_per, const v
         memcpy(&rbits, &o.rtol, 8);
         key.push_back(rbits);
         // the captured launch holds workspace addresses: a regrown workspace is a new key
-        for (const void *ptr : {(const void *)w.part, (const void *)w.x, (const void *)w.r, (const void *)w.p,
+        for (const void *ptr : {(const void *)w.part, (const void *)w.gpart, (const void *)w.gcount, (const void *)w.x, (const void *)w.r, (const void *)w.p,
                                 (const void *)w.q, (const void *)a.u, (const void *)w.delta, (const void *)w.res,
                                 (const void *)c.active,
                                 (const void *)w.hsum, (const void *)c.rho, (const void *)bar, (const void *)d_own})

@@ -118,6 +118,8 @@ struct Ctx {
     double *part;                   // [ND][part_stride][KT]
     int64_t part_stride;            // >= max(n_sblk + n_heavy, n_vblk)
     unsigned *counter;              // [nseg] arrival counters (self-resetting)
+    double *gpart;                  // [ND][part_stride][KT] sums of slot groups, at each group's first slot
+    unsigned *gcount;               // [part_stride] group arrival counters, at each group's first slot (self-resetting)
     // ---- per (segment, column) scalar state, [nseg][KT]
     double *rho, *rr, *rr0, *alpha, *beta, *mean, *meanx, *d2, *dz, *zr;
     double *hs_sum, *hs_hist;       // d^2 stop: sum of alpha_k rho_k; [nseg*KT][d2_window] last terms
@@ -142,7 +144,7 @@ struct Ctx {
     const void *sl_w;
     int32_t sl_h;                   // H of the plan the pointers above belong to
     int32_t sl_stream;              // 1: stream plan (stream.cuh): sl_* hold every warp's steps
-    int32_t sl_tma;                 // 1: a stream plan gathered by TMA (tma.cuh)
+    int32_t sl_tma;                 // stream plan engine: 1 TMA gathers, 2 per-lane asynchronous copies (tma.cuh)
     const int32_t *sl_wsplit;       // [n_sblk][NWARP + 1] first slice of each warp, relative to the block's
     const longlong2 *sl_wrun;       // stream plans: [n_sblk][NWARP] {first entry, steps} of each warp
     // ---- L2 residency of the gathered vector's hot rows (degree-ordered graphs)

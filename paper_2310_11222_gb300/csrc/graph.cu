@@ -595,9 +595,10 @@ static int fill_plan_slices(nvd_graph_s *g, Plan *pl, cudaStream_t s) {
 }
 
 int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out, bool allow_stream) {
-    // gather mode of this plan: 0 register slices, 1 register stream, 2 TMA stream
+    // gather mode of this plan: 0 register slices, 1 register stream, 2 TMA stream,
+    // 3 asynchronous-copy stream (2 and 3 for rows of 64 or 128 bytes)
     const int gm = (!allow_stream || KT == 1 || g->sp.gather <= 0) ? 0
-                   : (g->sp.gather >= 2 && tma_tile(KT, szv)) ? 2 : 1;
+                   : (g->sp.gather >= 2 && tma_tile(KT, szv)) ? std::min(g->sp.gather, 3) : 1;
     const bool tma = gm != 0;   // stream layout (the name of the TMA plans it began with)
     const int64_t key = ((int64_t)(KT * 256 + szv * 16 + sza) << 32) | ((int64_t)gm << 30) |
                         ((int64_t)g->sp.row_max_pct << 16) | (int64_t)g->sp.blocks_pct;
@@ -798,6 +799,7 @@ int get_plan(nvd_graph_s *g, int KT, int szv, int sza, Plan **out, bool allow_st
     }
     pl->stream = tma;
     pl->tma = gm == 2;
+    pl->acopy = gm == 3;
     pl->n_light_slices = n_light_slices;
     pl->n_items = (int64_t)items.size();
     pl->n_sblk = (int64_t)sblk.size();
@@ -866,7 +868,7 @@ void set_sp_plan(Ctx *c, const Plan *pl) {
     c->sl_w = pl->sl_w.p;
     c->sl_h = sp_slice_rows(pl->KT, pl->szv);
     c->sl_stream = pl->stream ? 1 : 0;
-    c->sl_tma = pl->tma ? 1 : 0;
+    c->sl_tma = pl->tma ? 1 : pl->acopy ? 2 : 0;
     c->sl_wsplit = pl->sl_wsplit.as<int32_t>();
     c->sl_wrun = pl->sl_wrun.as<longlong2>();
 }

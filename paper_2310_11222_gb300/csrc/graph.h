@@ -71,7 +71,8 @@ struct DevBuf {
 struct SpParams {
     int32_t row_max_pct = 100;
     int32_t blocks_pct = 100;
-    int32_t gather = 0;          // multi-column SpMM: 0 register slices, 1 register stream, 2 TMA stream
+    int32_t gather = 0;          // multi-column SpMM: 0 register slices, 1 register stream, 2 TMA stream,
+                                 // 3 asynchronous-copy stream
                                  // (2 only where tma_tile holds, else 1); the tuner tries the others
     int32_t l2_hot = 0;          // 1: the multi-column SpMM keeps the gathered vector's hot rows (the
                                  // degree-ordered head of the largest component) persisting in L2
@@ -89,6 +90,7 @@ struct Plan {
     DevBuf sl_wrun;                         // stream plans: per (block, warp) {first entry, steps}
     bool stream = false;                    // stream layout (stream.cuh)
     bool tma = false;                       // stream plan gathered by TMA
+    bool acopy = false;                     // stream plan gathered by per-lane asynchronous copies
     int64_t n_light_slices = 0;             // stream plans: heavy-chunk slices follow the light ones
     int64_t part_slots() const {
         int64_t a = n_sblk + n_heavy;

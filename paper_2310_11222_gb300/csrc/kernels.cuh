@@ -12,9 +12,10 @@
 // plus a sliced copy of its light rows (see Ctx::sl_*).  Each CTA block covers
 // work of one segment (slices, heavy sub-items or a row range) and owns one
 // partial-sum slot per inner product; the last block of a segment to finish
-// (atomic arrival counter) sums the segment's slots in slot order and updates
-// the per-(segment, column) CG scalars -- so every reduction is deterministic
-// and needs no extra launch.
+// (atomic arrival counters) adds the segment's slots -- directly in slot order,
+// or, for many slots, the sums of groups of consecutive slots that each group's
+// last writer formed -- and updates the per-(segment, column) CG scalars, so
+// every reduction is deterministic and needs no extra launch.
 #pragma once
 
 #include <math.h>
@@ -250,44 +251,64 @@ __device__ __forceinline__ void block_reduce_cols(double (&acc)[ND > 0 ? ND : 1]
 constexpr int pow2floor(int x) { return x >= 256 ? 256 : x >= 128 ? 128 : x >= 64 ? 64 : x >= 32 ? 32
                                        : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1; }
 
-// Publish this block's partials into `slot`, count the arrival on the segment
-// and, in the last block of the segment, sum the segment's slots -- blocks
-// [s0, s0 + cnt) then split-row slots [h0, h0 + hcnt) -- in slot order and call
-// fin(c, seg, j, sums) for each column j (one thread per column).
-// `red` needs NT doubles of shared scratch.
-template <int ND, int KT, class Fin>
-__device__ void seg_arrive(const Ctx &c, const Fin &fin, int seg, int64_t slot, const double *tot,
-                           int64_t s0, int32_t cnt, int64_t h0, int32_t hcnt, double *red) {
-    static_assert(ND > 0, "arrival needs a reduction");
-    __shared__ int s_last;
-    if (threadIdx.x < ND * KT) {
-        const int d = threadIdx.x / KT, j = threadIdx.x % KT;
-        c.part[((int64_t)d * c.part_stride + slot) * KT + j] = tot[threadIdx.x];
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&c.counter[seg], 1u) == (unsigned)(cnt - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+// Cross-block sums.  Every block of a pass owns one partial-sum slot per inner
+// product; a split row's finishing chunk owns one more ("heavy" slot).  The sum
+// over a segment's slots is taken in a fixed order, so it does not depend on
+// which block finishes last:
+//   few slots: the segment's last block to arrive adds all slots in slot order;
+//   many slots: the slots form arrival groups of SLOT_GROUP consecutive slots; the
+//     last writer of a group adds that group in slot order into the group's sum
+//     (gpart, at the group's first slot) and arrives on the segment; the last
+//     group to arrive adds the group sums in group order.  The tail of a pass (the
+//     work left once every other block is done) then reads a few hundred group
+//     sums instead of every slot -- one SM reading tens of thousands of slots took
+//     a large part of a multi-column SpMM.
+constexpr int SLOT_GROUP = 32;
+// Slots x sums up to which one block adds the segment's slots itself.
+constexpr int FLAT_SUMS_MAX = 16384;
+
+// Block-wide, fixed order: for each sum p = d * KT + j (P = ND * KT of them),
+//   sums[p] = sum_k a[(d * stride + a0 + k * as) * KT + j], k < an
+//           + sum_k b[(d * stride + b0 + k * bs) * KT + j], k < bn
+// (thread `sub` of the TPP threads of sum p takes k = sub, sub + TPP, ... of each
+// range in order; the TPP partials are then added by a fixed butterfly).
+// `sums` holds P doubles and `red` at least 128 + NWARP doubles of shared scratch
+// (sums may alias red).
+template <int ND, int KT>
+__device__ __forceinline__ void block_sum_slots(const double *a, int64_t a0, int32_t an, int32_t as,
+                                                const double *b, int64_t b0, int32_t bn, int32_t bs,
+                                                int64_t stride, double *red) {
     constexpr int P = ND * KT;
     constexpr int TPP = pow2floor(NT / P);
     const int pair = threadIdx.x / TPP, sub = threadIdx.x % TPP;
     double s = 0.0;
     if (pair < P) {
         const int d = pair / KT, j = pair % KT;
-        const double *base = c.part + (int64_t)d * c.part_stride * KT + j;
+        const double *pa = a + (d * stride + a0) * KT + j;
+        const int64_t sa = (int64_t)as * KT;
         // eight independent loads in flight, added in slot order
         int i = sub;
-        for (; i + 7 * TPP < cnt; i += 8 * TPP) {
+        for (; i + 7 * TPP < an; i += 8 * TPP) {
             double v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcg(base + (s0 + i + u * TPP) * KT);
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(pa + (int64_t)(i + u * TPP) * sa);
 #pragma unroll
             for (int u = 0; u < 8; ++u) s += v[u];
         }
-        for (; i < cnt; i += TPP) s += __ldcg(base + (s0 + i) * KT);
-        for (int h = sub; h < hcnt; h += TPP) s += __ldcg(base + (h0 + h) * KT);
+        for (; i < an; i += TPP) s += __ldcg(pa + (int64_t)i * sa);
+        if (bn > 0) {
+            const double *pb = b + (d * stride + b0) * KT + j;
+            const int64_t sb = (int64_t)bs * KT;
+            i = sub;
+            for (; i + 7 * TPP < bn; i += 8 * TPP) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldcg(pb + (int64_t)(i + u * TPP) * sb);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s += v[u];
+            }
+            for (; i < bn; i += TPP) s += __ldcg(pb + (int64_t)i * sb);
+        }
     }
     constexpr int WOFF = TPP < 32 ? TPP : 32;
 #pragma unroll
@@ -303,17 +324,121 @@ __device__ void seg_arrive(const Ctx &c, const Fin &fin, int seg, int64_t slot, 
             sums[pair] = t;
         }
     } else {
+        __syncthreads();         // the caller may have read red just before
         if (sub == 0 && pair < P) sums[pair] = s;
     }
     __syncthreads();
+}
+
+// After this block's writes to a slot of group [f, f + m): count the arrival; the
+// group's last writer adds the group into gpart at f.  Returns (block-uniformly)
+// whether this block did.
+template <int ND, int KT>
+__device__ __forceinline__ bool group_arrive(const Ctx &c, int64_t f, int32_t m, double *red) {
+    __shared__ int s_glast;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_glast = (atomicAdd(&c.gcount[f], 1u) == (unsigned)(m - 1));
+    __syncthreads();
+    if (!s_glast) return false;
+    __threadfence();
+    block_sum_slots<ND, KT>(c.part, f, m, 1, nullptr, 0, 0, 0, c.part_stride, red);
+    if (threadIdx.x < ND * KT) {
+        const int d = threadIdx.x / KT, j = threadIdx.x % KT;
+        c.gpart[((int64_t)d * c.part_stride + f) * KT + j] = red[threadIdx.x];
+    }
+    if (threadIdx.x == 0) atomicExch(&c.gcount[f], 0u);
+    return true;
+}
+
+__device__ __forceinline__ int32_t n_groups(int32_t cnt) { return (cnt + SLOT_GROUP - 1) / SLOT_GROUP; }
+
+// The segment adds its slots itself (one level) when they are few, unless split
+// rows arrive in groups of their own (hgroup) and the segment has some.
+template <int ND, int KT>
+__device__ __forceinline__ bool seg_flat(int32_t cnt, int32_t hcnt, bool hgroup) {
+    return (int64_t)(cnt + hcnt) * ND * KT <= FLAT_SUMS_MAX && (!hgroup || hcnt == 0);
+}
+
+// Arrival of a group sum on its segment; the last group adds the block groups then
+// the heavy groups (hgroup; else the heavy slots themselves) and calls
+// fin(c, seg, j, sums) for each column j.
+template <int ND, int KT, class Fin>
+__device__ void seg_group_arrive(const Ctx &c, const Fin &fin, int seg, int64_t s0, int32_t cnt, int64_t h0,
+                                 int32_t hcnt, bool hgroup, double *red) {
+    __shared__ int s_last;
+    const int32_t ng = n_groups(cnt) + (hgroup ? n_groups(hcnt) : 0);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&c.counter[seg], 1u) == (unsigned)(ng - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (hgroup)
+        block_sum_slots<ND, KT>(c.gpart, s0, n_groups(cnt), SLOT_GROUP, c.gpart, h0, n_groups(hcnt), SLOT_GROUP,
+                                c.part_stride, red);
+    else
+        block_sum_slots<ND, KT>(c.gpart, s0, n_groups(cnt), SLOT_GROUP, c.part, h0, hcnt, 1, c.part_stride, red);
     if (threadIdx.x < KT) {
         double v[ND];
 #pragma unroll
-        for (int d = 0; d < ND; ++d) v[d] = sums[d * KT + threadIdx.x];
+        for (int d = 0; d < ND; ++d) v[d] = red[d * KT + threadIdx.x];
         fin(c, seg, threadIdx.x, v);
     }
     if (threadIdx.x == 0) atomicExch(&c.counter[seg], 0u);
     __syncthreads();
+}
+
+// Publish this block's partials (tot, shared) into `slot` and arrive: the segment's
+// blocks are slots [s0, s0 + cnt), its split-row slots [h0, h0 + hcnt).  The block
+// that completes the segment calls fin(c, seg, j, sums) for each column j (one
+// thread per column).  `red` needs NT doubles of shared scratch.  hgroup: the
+// split rows' slots arrive themselves (heavy_arrive), in groups; every block of the
+// pass must pass the same value, and it may be true only if every split row of the
+// segment is finished in this pass.
+template <int ND, int KT, class Fin>
+__device__ void seg_arrive(const Ctx &c, const Fin &fin, int seg, int64_t slot, const double *tot,
+                           int64_t s0, int32_t cnt, int64_t h0, int32_t hcnt, double *red, bool hgroup = false) {
+    static_assert(ND > 0, "arrival needs a reduction");
+    __shared__ int s_last;
+    if (threadIdx.x < ND * KT) {
+        const int d = threadIdx.x / KT, j = threadIdx.x % KT;
+        c.part[((int64_t)d * c.part_stride + slot) * KT + j] = tot[threadIdx.x];
+    }
+    if (!seg_flat<ND, KT>(cnt, hcnt, hgroup)) {
+        const int64_t f = s0 + (slot - s0) / SLOT_GROUP * SLOT_GROUP;
+        const int32_t m = (int32_t)(s0 + cnt - f < SLOT_GROUP ? s0 + cnt - f : SLOT_GROUP);
+        if (group_arrive<ND, KT>(c, f, m, red)) seg_group_arrive<ND, KT>(c, fin, seg, s0, cnt, h0, hcnt, hgroup, red);
+        return;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&c.counter[seg], 1u) == (unsigned)(cnt - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    block_sum_slots<ND, KT>(c.part, s0, cnt, 1, c.part, h0, hcnt, 1, c.part_stride, red);
+    if (threadIdx.x < KT) {
+        double v[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) v[d] = red[d * KT + threadIdx.x];
+        fin(c, seg, threadIdx.x, v);
+    }
+    if (threadIdx.x == 0) atomicExch(&c.counter[seg], 0u);
+    __syncthreads();
+}
+
+// A split row's finishing chunk (a whole block) has written the row's slot hs:
+// arrive on the row's heavy group and, if that completes it, on the segment.
+template <int ND, int KT, class Fin>
+__device__ void heavy_arrive(const Ctx &c, const Fin &fin, int seg, int64_t hs, double *red) {
+    const int64_t s0 = c.seg_sblk_off[seg];
+    const int32_t cnt = c.seg_sblk_off[seg + 1] - (int32_t)s0;
+    const int64_t h0 = c.n_sblk + c.seg_heavy_off[seg];
+    const int32_t hcnt = c.seg_heavy_off[seg + 1] - c.seg_heavy_off[seg];
+    const int64_t f = h0 + (hs - h0) / SLOT_GROUP * SLOT_GROUP;
+    const int32_t m = (int32_t)(h0 + hcnt - f < SLOT_GROUP ? h0 + hcnt - f : SLOT_GROUP);
+    if (group_arrive<ND, KT>(c, f, m, red)) seg_group_arrive<ND, KT>(c, fin, seg, s0, cnt, h0, hcnt, true, red);
 }
 
 // Is any column of the segment still iterating?  (Constant during one phase:
@@ -757,6 +882,7 @@ __device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, int seg
                     for (int v = 0; v < VEC; ++v)
                         c.part[((int64_t)d * c.part_stride + hs) * KT + threadIdx.x * VEC + v] = dot_get(hdot[d][v]);
             }
+            heavy_arrive<ND, KT>(c, epi.fin, seg, c.n_sblk + it.hrow, red);
         }
     }
     __syncthreads();
@@ -952,6 +1078,110 @@ __device__ void spmv1_block(const Ctx &c, const Epi &epi, const TV *__restrict__
     }
 }
 
+// A warp's fixed run of light slices [s_lo, s_hi) of a multi-column SpMM (tiles
+// where U steps of G rows span at most 16 entries: 128-byte FP32 rows and the FP64
+// tiles; with 8 rows per slice the per-step loop of spmm_block measured 1.6% faster,
+// with 4 this form 2% faster).  Products are added in entry
+// order exactly as in the per-step loop; what changes is how the slices' columns
+// and weights reach the lanes: the run's entries are one contiguous stream, read
+// 32 at a time by the whole warp (one coalesced load each of columns and weights)
+// into a window of two such chunks, and handed to the lanes by shuffles; the
+// chunk after the window and the next slice's bounds and row id are loaded while
+// the current gathers are in flight.  The chain per U steps is then one gather
+// latency instead of a column load followed by a gather.
+template <class LD, class TV, class TW, class TA, int KT, class Epi>
+__device__ __forceinline__ void spmm_light_run(const Ctx &c, Epi &e, const TV *__restrict__ src,
+                                               TV *__restrict__ dst, int64_t s_lo, int64_t s_hi,
+                                               typename Epi::template D<TV> (&dot)[Epi::ND > 0 ? Epi::ND : 1]
+                                                                                  [SpCfg<TV, TA, KT>::VEC]) {
+    typedef SpCfg<TV, TA, KT> C;
+    constexpr int VEC = C::VEC, LPR = C::LPR, G = C::G;
+    constexpr int U = sizeof(TV) == 8 ? SPMM_UNROLL_F64 : SPMM_UNROLL_F32;
+    static_assert(U * G <= 32 && 32 % G == 0, "U steps of a slice fit one 32-entry chunk");
+    if (s_lo >= s_hi) return;
+    const int lane = threadIdx.x & 31;
+    const int gid = lane / LPR, col0 = (lane % LPR) * VEC;
+    const TA *__restrict__ deg = deg_of<TA>(c);
+    // entries of the run relative to its first (a run holds far fewer than 2^31)
+    const int64_t e_lo = __ldg(c.sl_base + s_lo);
+    const int32_t *__restrict__ slc = c.sl_col + e_lo;
+    const TW *__restrict__ slw = reinterpret_cast<const TW *>(c.sl_w) + e_lo;
+    const int n_e = (int)(__ldg(c.sl_base + s_hi) - e_lo);
+    int base = 0;
+    int nb = (int)(__ldg(c.sl_base + s_lo + 1) - e_lo);
+    int32_t i = __ldg(c.sl_row + s_lo * G + gid);
+    // window [wb, wb + 64): chunk (mc, mw) then chunk (nc, nw)
+    int wb = 0;
+    int mc = 0, nc = 0;
+    TW mw = 0, nw = 0;
+    if (lane < n_e) {
+        mc = __ldcs(slc + lane);
+        mw = __ldcs(slw + lane);
+    }
+    if (32 + lane < n_e) {
+        nc = __ldcs(slc + 32 + lane);
+        nw = __ldcs(slw + 32 + lane);
+    }
+    for (int64_t sl = s_lo; sl < s_hi; ++sl) {
+        const int L = (nb - base) / G;
+        // the next slice's end and row id, in flight during this slice
+        int nb2 = nb;
+        int32_t i2 = -1;
+        if (sl + 1 < s_hi) {
+            nb2 = (int)(__ldg(c.sl_base + sl + 2) - e_lo);
+            i2 = __ldg(c.sl_row + (sl + 1) * G + gid);
+        }
+        TV own[VEC];
+        TA dg = 0;
+        if (i >= 0) {
+            ldv<LD, TV, VEC>(src + (int64_t)i * KT + col0, own);
+            dg = __ldg(deg + i);
+        }
+        TA acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = 0;
+        for (int j = 0; j < L; j += U) {
+            const int pos = base + j * G;
+            if (pos >= wb + 32) {   // slide the window by one chunk
+                mc = nc;
+                mw = nw;
+                wb += 32;
+                nc = 0;
+                nw = 0;
+                if (wb + 32 + lane < n_e) {
+                    nc = __ldcs(slc + wb + 32 + lane);
+                    nw = __ldcs(slw + wb + 32 + lane);
+                }
+            }
+            const int ob = pos - wb;   // < 32, a multiple of G
+            int cu[U];
+            TA wu[U];
+            TV pv[U][VEC];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                // step j + u is entries ob + u*G .. + G - 1 of the window: all in the
+                // first chunk or all in the second (G divides 32), the same for every lane
+                const bool lo = ob + u * G < 32;
+                const int sl_lane = (ob + u * G + gid) & 31;
+                cu[u] = __shfl_sync(NVD_FULLMASK, lo ? mc : nc, sl_lane);
+                wu[u] = (TA)__shfl_sync(NVD_FULLMASK, lo ? mw : nw, sl_lane);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j + u < L) ldv<LD, TV, VEC>(src + (int64_t)cu[u] * KT + col0, pv[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j + u < L)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] += wu[u] * (TA)pv[u][v];
+        }
+        if (i >= 0) e.template elem<TV, TA, VEC>(c, i, col0, KT, own, acc, dg, dst, dot);
+        base = nb;
+        nb = nb2;
+        i = i2;
+    }
+}
+
 // One SpMV/SpMM block b: its slices or heavy sub-items, then the segment arrival.
 template <class LD, class TV, class TW, class TA, int KT, class Epi>
 __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ src, TV *__restrict__ dst,
@@ -994,6 +1224,10 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
             const int32_t *split = c.sl_wsplit + b * (NWARP + 1);
             const int warp = threadIdx.x >> 5;
             const int64_t s_hi = blk.i0 + __ldg(split + warp + 1);
+            constexpr int U = sizeof(TV) == 8 ? SPMM_UNROLL_F64 : SPMM_UNROLL_F32;
+            if constexpr (U * G <= 16) {
+                spmm_light_run<LD, TV, TW, TA, KT, Epi>(c, e, src, dst, blk.i0 + __ldg(split + warp), s_hi, dot);
+            } else
             for (int64_t sl = blk.i0 + __ldg(split + warp); sl < s_hi; ++sl) {
                 const int64_t base = __ldg(c.sl_base + sl);
                 const int L = (int)((__ldg(c.sl_base + sl + 1) - base) / G);
@@ -1006,7 +1240,6 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
                 }
                 const int32_t *__restrict__ cp = c.sl_col + base + gid;
                 const TW *__restrict__ wp = slw + base + gid;
-                constexpr int U = sizeof(TV) == 8 ? SPMM_UNROLL_F64 : SPMM_UNROLL_F32;
                 TA acc[VEC];
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) acc[v] = 0;
@@ -1047,7 +1280,10 @@ __device__ void spmm_block(const Ctx &c, const Epi &epi, const TV *__restrict__ 
         const int32_t cnt = c.seg_sblk_off[seg + 1] - (int32_t)s0;
         const int64_t h0 = c.n_sblk + c.seg_heavy_off[seg];
         const int32_t hcnt = c.seg_heavy_off[seg + 1] - c.seg_heavy_off[seg];
-        seg_arrive<ND, KT>(c, epi.fin, seg, b, tot, s0, cnt, h0, hcnt, red);
+        // split rows arrive by themselves only in a pass that runs them (a segment
+        // whose columns have all stopped skips its rows; `live` is the same in
+        // every block of the pass)
+        seg_arrive<ND, KT>(c, epi.fin, seg, b, tot, s0, cnt, h0, hcnt, red, live);
     }
 }
 

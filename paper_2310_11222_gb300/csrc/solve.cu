@@ -125,13 +125,12 @@ int distance_impl(nvd_graph_t g, int32_t k, const void *x, const void *y, int32_
     fill_graph_ctx(g, pl, &c);
     SolveWs w;
     NVD_TRY(setup_ws(g, pl, KT, szv, mixed, 1, &c, &w, s));
-    if (mixed) c.part_stride = std::max(pl->part_slots(), pl64->part_slots());
     if (mixed) {
+        // the FP32 and FP64 plans share the slots and split-row sums
+        NVD_TRY(setup_part(g, std::max(pl->part_slots(), pl64->part_slots()), KT, &c, &w, s));
         int st = NVD_OK;
-        w.part = (double *)g->wsp("part", (size_t)4 * c.part_stride * KT * 8 + 64, &st);
         w.hsum = (double *)g->wsp("hsum", (size_t)std::max<int64_t>({pl->n_chunks, pl64->n_chunks, 1}) * KT * 8, &st);
         if (st) return st;
-        c.part = w.part;
         c.hsum = w.hsum;
     }
     const int64_t sk = (int64_t)std::max(g->nseg, 1) * KT;

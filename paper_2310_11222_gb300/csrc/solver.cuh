@@ -70,7 +70,7 @@ template <class TV, class TW, class TA, int KT, class Epi>
 __global__ void __launch_bounds__(NT, NVD_STREAM_MINB) k_spmm_stream(Ctx c, Epi epi, const TV *src, TV *dst) {
     __shared__ __align__(16) char smem[dev::SpCfg<TV, TA, KT>::SMEM];
     pdl_trigger_and_wait();
-    dev::spmm_block_stream<false, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, nullptr, smem, nullptr);
+    dev::spmm_block_stream<0, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, nullptr, smem, nullptr);
 }
 
 template <class TV, class TA, int KT>
@@ -82,8 +82,18 @@ __global__ void __launch_bounds__(NT, 2)
     extern __shared__ __align__(128) char dsm[];
     pdl_trigger_and_wait();
     char *ring = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(dsm) + 127) & ~(uintptr_t)127);
-    dev::spmm_block_stream<true, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, ring, dsm + tma_ring_bytes(),
+    dev::spmm_block_stream<1, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, ring, dsm + tma_ring_bytes(),
                                                       &tm);
+}
+
+// The same stream plan and ring with per-lane asynchronous copies (no tensor map).
+template <class TV, class TW, class TA, int KT, class Epi>
+__global__ void __launch_bounds__(NT, 2) k_spmm_acopy(Ctx c, Epi epi, const TV *src, TV *dst) {
+    extern __shared__ __align__(128) char dsm[];
+    pdl_trigger_and_wait();
+    char *ring = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(dsm) + 127) & ~(uintptr_t)127);
+    dev::spmm_block_stream<2, TV, TW, TA, KT, Epi>(c, epi, src, dst, blockIdx.x, ring, dsm + tma_ring_bytes(),
+                                                   nullptr);
 }
 
 // lane vectors per thread per trip of the vector passes (one column / several)
@@ -195,8 +205,8 @@ void note_launch(int64_t n = 1);
 // ------------------------------------------------------------------ workspace
 
 struct SolveWs {
-    double *part = nullptr;
-    unsigned *counter = nullptr;
+    double *part = nullptr, *gpart = nullptr;
+    unsigned *counter = nullptr, *gcount = nullptr;
     double *st_d = nullptr;   // (11 + d2_window) x [nseg][KT]
     int32_t *st_i = nullptr;  // 3 x [nseg][KT] + n_active + err
     ColResult *res = nullptr;
@@ -206,6 +216,22 @@ struct SolveWs {
     void *u = nullptr;   // D^-1 r, the vector the SpMV runs on (direction folded into the SpMV)
 };
 
+// Partial-sum slots of `stride` blocks (ND <= 4 sums of KT columns each), their
+// group sums and the zeroed group arrival counters.
+inline int setup_part(nvd_graph_s *g, int64_t stride, int KT, Ctx *c, SolveWs *w, cudaStream_t s) {
+    int st = NVD_OK;
+    w->part = (double *)g->wsp("part", (size_t)4 * stride * KT * 8 + 64, &st);
+    w->gpart = (double *)g->wsp("gpart", (size_t)4 * stride * KT * 8 + 64, &st);
+    w->gcount = (unsigned *)g->wsp("gcount", (size_t)stride * 4 + 64, &st);
+    if (st != NVD_OK) return st;
+    NVD_TRY_CUDA(cudaMemsetAsync(w->gcount, 0, (size_t)stride * 4, s));
+    c->part = w->part;
+    c->gpart = w->gpart;
+    c->gcount = w->gcount;
+    c->part_stride = stride;
+    return NVD_OK;
+}
+
 // Allocate (or reuse) the workspace of a solve and point the Ctx state at it.
 inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixed, int n_owner,
                     Ctx *c, SolveWs *w, cudaStream_t s) {
@@ -213,7 +239,6 @@ inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixe
     const int64_t nseg = std::max(g->nseg, 1);
     const int64_t sk = nseg * KT;
     const int64_t nk = g->n * KT;
-    w->part = (double *)g->wsp("part", (size_t)4 * pl->part_slots() * KT * 8 + 64, &st);
     w->counter = (unsigned *)g->wsp("counter", (size_t)nseg * 4, &st);
     w->st_d = (double *)g->wsp("st_d", (size_t)(11 + d2_window()) * sk * 8, &st);
     w->st_i = (int32_t *)g->wsp("st_i", (size_t)(3 * sk + 8) * 4, &st);
@@ -239,8 +264,7 @@ inline int setup_ws(nvd_graph_s *g, const Plan *pl, int KT, size_t tv, bool mixe
     c->active = w->st_i; c->iters = w->st_i + sk; c->status = w->st_i + 2 * sk;
     c->n_active = w->st_i + 3 * sk;
     c->err = w->st_i + 3 * sk + 1;
-    c->part = w->part;
-    c->part_stride = pl->part_slots();
+    NVD_TRY(setup_part(g, pl->part_slots(), KT, c, w, s));
     c->counter = w->counter;
     c->hsum = w->hsum;
     return NVD_OK;
@@ -263,7 +287,7 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
         return NVD_ERR_UNSUPPORTED;
     }
     if constexpr (KT > 1) {
-        if (c.sl_stream && !c.sl_tma) {
+        if (c.sl_stream && c.sl_tma == 0) {
             const bool prof = prof_enabled() && prof_begin(s, cls);
             NVD_TRY_CUDA(launch_dependent_smem(k_spmm_stream<TV, TW, TA, KT, Epi>, (unsigned)c.n_sblk, 0, s,
                                                spmm_window<TV, KT>(c, src), c, epi, src, dst));
@@ -273,7 +297,19 @@ inline int launch_spmm(const Ctx &c, const Epi &epi, const TV *src, TV *dst, cud
         }
     }
     if constexpr (tma_tile(KT, (int)sizeof(TV))) {
-        if (c.sl_stream && c.sl_tma) {
+        if (c.sl_stream && c.sl_tma == 2) {
+            // neighbour rows copied by each lane into the TMA engine's ring
+            auto kern = k_spmm_acopy<TV, TW, TA, KT, Epi>;
+            constexpr int SM = tma_kernel_smem<TV, TA, KT>();
+            NVD_TRY(allow_dynamic_smem((const void *)kern, SM));
+            const bool prof = prof_enabled() && prof_begin(s, cls);
+            NVD_TRY_CUDA(launch_dependent_smem(kern, (unsigned)c.n_sblk, (size_t)SM, s, spmm_window<TV, KT>(c, src),
+                                               c, epi, src, dst));
+            note_launch();
+            if (prof) prof_end(s, bytes);
+            return NVD_OK;
+        }
+        if (c.sl_stream && c.sl_tma == 1) {
             // neighbour rows gathered by TMA; the tensor map describes src as [n][KT]
             CUtensorMap tm;
             NVD_TRY(tma_map(src, c.n, KT, (int)sizeof(TV), &tm));

@@ -201,12 +201,12 @@ __device__ __forceinline__ void reg_stream(const Ctx &c, int64_t E0, int64_t T, 
     }
 }
 
-// One CTA block b of a stream plan (see the top of this file); USE_TMA selects the
-// TMA engine (`ring`: this CTA's 128-byte aligned ring area, `tm`: the tensor map of
-// src), otherwise the register engine.  Then the block's inner-product partials and
-// the segment arrival, as in the register path.  `smem` is the register path's
-// layout (reduction scratch and totals).
-template <bool USE_TMA, class TV, class TW, class TA, int KT, class Epi>
+// One CTA block b of a stream plan (see the top of this file); ENGINE 0 registers,
+// 1 TMA (`ring`: this CTA's 128-byte aligned ring area, `tm`: the tensor map of src),
+// 2 per-lane asynchronous copies into the same ring.  Then the block's inner-product
+// partials and the segment arrival, as in the register path.  `smem` is the register
+// path's layout (reduction scratch and totals).
+template <int ENGINE, class TV, class TW, class TA, int KT, class Epi>
 __device__ void spmm_block_stream(const Ctx &c, const Epi &epi, const TV *__restrict__ src, TV *__restrict__ dst,
                                   int64_t b, char *ring, char *smem, const CUtensorMap *tm) {
     typedef SpCfg<TV, TA, KT> C;
@@ -229,7 +229,36 @@ __device__ void spmm_block_stream(const Ctx &c, const Epi &epi, const TV *__rest
     if (T > 0) {
         StreamRows<TV, TA, KT, Epi> rows(c, epi, seg, col0, dst, dot);
         bool ok = true;
-        if constexpr (USE_TMA) {
+        if constexpr (ENGINE == 2) {
+            static_assert(H * RB == TMA_STEP_BYTES && (H == 4 || H == 8), "one step is 512 bytes of 4 or 8 rows");
+            static_assert(TMA_STEP_BYTES + H * (int)sizeof(TA) <= TMA_IDS_OFFSET, "weights fit the slot");
+            static_assert(VEC * (int)sizeof(TV) == 16, "16-byte lane vectors");
+            char *wring = ring + warp * TMA_SLOTS * TMA_SLOT_BYTES;
+            auto slot_values = [&](const char *slot, TV (&pv)[VEC], TA &w, int32_t &col) {
+                SmemVec<TV, VEC>::ld(slot + lane * 16, pv);
+                w = *reinterpret_cast<const TA *>(slot + TMA_STEP_BYTES + gid * (int)sizeof(TA));
+                col = reinterpret_cast<const int32_t *>(slot + TMA_IDS_OFFSET)[gid];
+            };
+            if (blk.pad == 0) {
+                acopy_stream<H, RB, TV, TA, KT>(c, E0, T, src, wring, [&](int64_t, const char *slot) {
+                    TV pv[VEC];
+                    TA w;
+                    int32_t col;
+                    slot_values(slot, pv, w, col);
+                    rows.light(pv, w, col);
+                    return true;
+                });
+            } else {
+                acopy_stream<H, RB, TV, TA, KT>(c, E0, T, src, wring, [&](int64_t, const char *slot) {
+                    TV pv[VEC];
+                    TA w;
+                    int32_t col;
+                    slot_values(slot, pv, w, col);
+                    rows.heavy(pv, w);
+                    return true;
+                });
+            }
+        } else if constexpr (ENGINE == 1) {
             static_assert(H * RB == TMA_STEP_BYTES && (H == 4 || H == 8), "one step is 512 bytes of 4 or 8 rows");
             static_assert(TMA_STEP_BYTES + H * (int)sizeof(TA) <= TMA_IDS_OFFSET, "weights fit the slot");
             static_assert(VEC * (int)sizeof(TV) == 16, "16-byte lane vectors");

@@ -192,5 +192,107 @@ __device__ __forceinline__ bool tma_stream(const Ctx &c, int64_t E0, int64_t T, 
     return true;
 }
 
+// ------------------------------------------------------------------ per-lane asynchronous copies
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Steps per round and rounds in flight of the asynchronous-copy engine (the ring is
+// the TMA engine's: TMA_SLOTS slots of TMA_SLOT_BYTES per warp).
+constexpr int ACOPY_ROUND = 4;
+constexpr int ACOPY_DEPTH = TMA_SLOTS / ACOPY_ROUND;
+
+// The step stream of one warp as in tma_stream, with the rows fetched by ordinary
+// per-lane asynchronous copies (cp.async) instead of the TMA unit: lane (g, sub)
+// copies its own 16 bytes of row g of every step -- the bytes it reads back when the
+// step is consumed -- so a lane only waits for its own copies (cp.async.wait_group),
+// and the copies go through the load path like register gathers, without holding
+// registers while in flight.  Rounds of ACOPY_ROUND steps, ACOPY_DEPTH rounds in
+// flight; at the start of round k (its copies waited for), round k + DEPTH - 1 is
+// issued into the slots of round k - 1, which every lane has read.  The lanes that
+// loaded a round's columns and weights (entry s*H + g of the round in lane s*H + g)
+// store them into the step's slot; the copy of step s row g takes its column by a
+// shuffle.  consume(t, slot) as for tma_stream.  No wait can hang: wait_group waits
+// for this lane's own copies, which always complete.
+template <int H, int RB, class TV, class TA, int KT, class Consume>
+__device__ __forceinline__ void acopy_stream(const Ctx &c, int64_t E0, int64_t T, const TV *__restrict__ src,
+                                             char *wring, Consume &&consume) {
+    constexpr int R = ACOPY_ROUND, DEPTH = ACOPY_DEPTH, LPR = RB / 16, VEC = 16 / (int)sizeof(TV);
+    static_assert(R * H <= 32 && DEPTH >= 2 && LPR * H == 32, "one round's entries fit the warp's lanes");
+    const int lane = threadIdx.x & 31, gid = lane / LPR, sub = lane % LPR;
+    const int32_t *__restrict__ cols = c.sl_col + E0;
+    const TA *__restrict__ ws = reinterpret_cast<const TA *>(c.sl_w) + E0;
+    const int64_t NE = T * H;
+    const int64_t NR = (T + R - 1) / R;   // rounds
+    // meta of a round: lane l < R*H holds entry l (step l / H, row l % H)
+    auto load_meta = [&](int64_t k, int &oc, TA &ow) {
+        const int64_t e = k * (R * H) + lane;
+        oc = 0;
+        ow = 0;
+        if (lane < R * H && e < NE) {
+            oc = __ldcs(cols + e);
+            ow = __ldcs(ws + e);
+        }
+    };
+    auto issue = [&](int64_t k, int mc, TA mw) {
+        if (k < NR) {
+            if (lane < R * H) {
+                const int64_t t = k * R + lane / H;
+                if (t < T) {
+                    char *slot = wring + (int)(t % TMA_SLOTS) * TMA_SLOT_BYTES;
+                    reinterpret_cast<TA *>(slot + TMA_STEP_BYTES)[lane % H] = mw;
+                    reinterpret_cast<int32_t *>(slot + TMA_IDS_OFFSET)[lane % H] = mc;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < R; ++s) {
+                const int col = __shfl_sync(NVD_FULLMASK, mc, s * H + gid);
+                const int64_t t = k * R + s;
+                if (t < T)
+                    cp_async16(wring + (int)(t % TMA_SLOTS) * TMA_SLOT_BYTES + gid * RB + sub * 16,
+                               src + (int64_t)col * KT + sub * VEC);
+            }
+        }
+        cp_async_commit();   // an empty group past the end keeps the group count
+    };
+    // meta two rounds ahead of its issue
+    int c0, c1;
+    TA w0, w1;
+    {
+        int mc;
+        TA mw;
+#pragma unroll
+        for (int k = 0; k < DEPTH - 1; ++k) {
+            load_meta(k, mc, mw);
+            issue(k, mc, mw);
+        }
+        load_meta(DEPTH - 1, c0, w0);
+        load_meta(DEPTH, c1, w1);
+    }
+    int64_t t = 0;
+    for (int64_t k = 0; k < NR; ++k) {
+        __syncwarp();                       // round k - 1 has been read by every lane
+        issue(k + DEPTH - 1, c0, w0);
+        c0 = c1;
+        w0 = w1;
+        load_meta(k + DEPTH + 1, c1, w1);
+        cp_async_wait<DEPTH - 1>();         // this lane's copies of round k have landed
+        __syncwarp();                       // and every lane's slot stores of round k are visible
+        bool go = true;
+        for (int s = 0; s < R && t < T; ++s, ++t) {
+            go = consume(t, (const char *)(wring + (int)(t % TMA_SLOTS) * TMA_SLOT_BYTES));
+            if (!go) break;
+        }
+        if (!go) break;
+    }
+    cp_async_wait_all();
+    __syncwarp();
+}
+
 }  // namespace dev
 }  // namespace nvd

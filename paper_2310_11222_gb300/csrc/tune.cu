@@ -9,7 +9,7 @@
 //     stored in the sliced layout, where it would make its whole slice as long;
 //   * the number of light CTA blocks per SpMV launch;
 //   * the gather engine of the multi-column SpMM (register slices, register stream,
-//     TMA stream);
+//     TMA stream, asynchronous-copy stream);
 //   * host-driven iterations versus one persistent cooperative launch per tile;
 //   * two kernels per iteration (direction update folded into the SpMV) or three.
 // Each candidate runs real solves on this graph with seeded synthetic
@@ -218,10 +218,13 @@ int tune_impl(nvd_graph_s *g, int32_t mode, int32_t k, uint32_t flags, nvd_tune_
         }
     }
     // 3b. gathers of the multi-column SpMM: register slices (default), register stream
-    //     and, where the tile width allows it, TMA stream
+    //     and, where the tile width allows it, TMA and asynchronous-copy streams
     if (best_kt > 1) {
         std::vector<int> modes = {0, 1};
-        if (tma_tile(best_kt, b.mode == NVD_MODE_FP64 ? 8 : 4)) modes.push_back(2);
+        if (tma_tile(best_kt, b.mode == NVD_MODE_FP64 ? 8 : 4)) {
+            modes.push_back(2);
+            modes.push_back(3);
+        }
         for (int gmode : modes) {
             if (gmode == g->sp.gather) continue;
             SpParams cand = g->sp;
@@ -336,7 +339,7 @@ extern "C" int nvd_graph_set_tuning(nvd_graph_t g, int32_t mode, const nvd_tune_
         !(t->kt == 0 || t->kt == 1 || t->kt == 4 || t->kt == 8 || t->kt == 16 || t->kt == 32) ||
         t->row_max_pct < 10 || t->row_max_pct > 1000 || t->blocks_pct < 10 || t->blocks_pct > 1000 ||
         (t->persistent != 0 && t->persistent != 1) || (t->fold_direction != 0 && t->fold_direction != 1) ||
-        t->gather < 0 || t->gather > 2 || (t->l2_hot != 0 && t->l2_hot != 1)) {
+        t->gather < 0 || t->gather > 3 || (t->l2_hot != 0 && t->l2_hot != 1)) {
         set_error("nvd_graph_set_tuning: invalid argument");
         return NVD_ERR_INVALID_ARG;
     }

@@ -1,9 +1,10 @@
-"""The multi-column SpMM's three gather engines -- register loads per slice
-(GATHER_SLICES), register loads over each warp's step stream (GATHER_STREAM) and TMA
-tile::gather4 over the stream (GATHER_TMA, tiles whose rows are 64 or 128 bytes) --
+"""The multi-column SpMM's four gather engines -- register loads per slice
+(GATHER_SLICES), register loads over each warp's step stream (GATHER_STREAM), TMA
+tile::gather4 over the stream (GATHER_TMA) and per-lane asynchronous copies over the
+stream (GATHER_ACOPY; the last two for tiles whose rows are 64 or 128 bytes) --
 against each other and against the oracle: a graph with split heavy rows (degrees up
 to 3000), rows on both sides of the light-row limits, several components in a
-shuffled node order and isolated nodes, with a ragged last tile.  The two stream
+shuffled node order and isolated nodes, with a ragged last tile.  The three stream
 engines run the same plan in the same order (bitwise equal results); every engine
 gives each warp a fixed run of work, so its results are bitwise repeatable."""
 import numpy as np
@@ -65,7 +66,7 @@ def test_gather_engines_match_each_other_and_the_oracle(nvd, case, mode, kt):
     tol = {0: 1e-9, 1: 1e-4, 2: 1e-9}[mode]
     tma_ok = kt * (8 if mode == 0 else 4) in (64, 128)
     out = {}
-    for gather in (nvd.GATHER_SLICES, nvd.GATHER_STREAM, nvd.GATHER_TMA):
+    for gather in (nvd.GATHER_SLICES, nvd.GATHER_STREAM, nvd.GATHER_TMA, nvd.GATHER_ACOPY):
         G = nvd.Graph.from_csr(g)
         G.set_tuning(mode=mode, gather=gather)
         a = nvd.ge_distance(G, on(X), on(Y), mode=mode, kt=kt, **kw)
@@ -76,12 +77,13 @@ def test_gather_engines_match_each_other_and_the_oracle(nvd, case, mode, kt):
     # TMA (where the tile allows it, else the register stream again): the same plan,
     # the same sums in the same order
     assert torch.equal(out[nvd.GATHER_STREAM], out[nvd.GATHER_TMA]), tma_ok
+    assert torch.equal(out[nvd.GATHER_STREAM], out[nvd.GATHER_ACOPY]), tma_ok
     # per-slice plan: the same CG, rows added in another grouping of the inner products
     assert rel(out[nvd.GATHER_SLICES].cpu().numpy(), out[nvd.GATHER_STREAM].cpu().numpy()) < \
         {0: 1e-10, 1: 1e-5, 2: 1e-10}[mode]
 
 
-@pytest.mark.parametrize("gather", [1, 2])
+@pytest.mark.parametrize("gather", [1, 2, 3])
 @pytest.mark.parametrize("row_max_pct,blocks_pct", [(10, 100), (100, 10), (100, 400), (1000, 100)])
 def test_stream_under_other_work_decompositions(nvd, case, gather, row_max_pct, blocks_pct):
     """Few rows per block, very many blocks, and the light-row limit moved so that the
