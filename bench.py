@@ -44,7 +44,7 @@ if ROOT not in sys.path:
 METRIC = "GE distances/s on 1 GB300 at d² rel.err≤1e-6; SpMV HBM GB/s vs peak"
 UNIT = "distances/s"
 PL_PAIRS = 128         # power-law workload: pairs per step (per rank)
-PL_RTOL_IN = 1e-5      # its inner FP32 solve tolerance
+PL_RTOL_IN = 3e-5      # its inner FP32 solve tolerance
 PL_D2_RTOL = 1e-8      # its refinement stop (relative change of d^2)
 PL_ORACLE_PAIRS = 2    # pairs the oracle solves for the CPU baseline and the error check
 PAIRS_PER_STEP = 8
@@ -244,8 +244,10 @@ def run_other_workload(args, nvd, synth, torch, np, local):
         xhs = [torch.from_numpy(x).pin_memory() for x in X]
         yhs = [torch.from_numpy(y).pin_memory() for y in Y]
         k = 32 * len(graphs)
-        kw = dict(mode=nvd.MODE_FP32, rtol=1e-6)
-        prof = False   # one persistent launch: no separate SpMV launches to time
+        # the workload as stated: one persistent, graph-captured launch; the library's
+        # default host-driven form is timed beside it (batched_host_loop)
+        kw = dict(mode=nvd.MODE_FP32, rtol=1e-6, persistent=True)
+        prof = False   # one persistent launch per step: no separate SpMM launches to time
 
         def step():
             return nvd.ge_distance_batched(Gs, xs, ys, **kw)
@@ -259,7 +261,8 @@ def run_other_workload(args, nvd, synth, torch, np, local):
         h2d, d2h = sum(2 * x.nbytes for x in X), 8 * k
         cfg = {"workload": "batched: 64 graphs, n log-uniform in [1e3, 2e5], 32 BA (m in 2..6) + 32 WS "
                            "(k=10, p=0.1), unit weights, 32 pairs each (16 e_i - e_j, 16 diffuse); FP32 "
-                           "block-PCG with FP64 reductions to rtol 1e-6 in one persistent graph-captured launch",
+                           "block-PCG with FP64 reductions to rtol 1e-6, the 64 graphs as one block-diagonal "
+                           "Laplacian in one persistent graph-captured launch",
                "graphs": len(graphs), "n_total": int(sum(gi.n for gi in graphs)),
                "nnz_total": int(sum(int(gi.rowptr[-1]) for gi in graphs)), "pairs_per_step": k}
         unit = UNIT
@@ -408,13 +411,12 @@ def run_other_workload(args, nvd, synth, torch, np, local):
     peak = float(peaks["hbm_gbs"])
     achieved = (spmv_bytes / n_spmv) / (spmv_ms / n_spmv / 1e3) / 1e9 if n_spmv else None
     value = k * args.steps / (total_ms / 1e3)
-    roof = None
+    step_roof = None
     if name == "batched":
-        # one persistent launch runs every graph's whole tile solve: its algorithmic
-        # bytes are, per graph, the iterations its slowest column ran times one PCG
-        # iteration's bytes (SpMM: CSR entries, row pointers, degrees, p read, q written;
-        # residual pass: r, q read, r written, D^-1; direction pass: x, r, p read, x, p
-        # written, D^-1), FP32 values, 32 columns
+        # the whole step against the copy bandwidth: per graph, the iterations its
+        # slowest column ran times one PCG iteration's bytes (SpMM: CSR entries, row
+        # pointers, degrees, p read, q written; residual pass: r, q read, r written,
+        # D^-1; direction pass: x, r, p read, x, p written, D^-1), FP32 values, 32 columns
         _, st = nvd.ge_distance_batched(Gs, xs, ys, return_stats=True, **kw)
         kt, sv = 32, 4
         tot_bytes, off = 0.0, 0
@@ -425,12 +427,39 @@ def run_other_workload(args, nvd, synth, torch, np, local):
             per_it = (nnz_ * (4 + sv) + 8 * (n_ + 1) + n_ * sv + 2 * n_ * kt * sv) + 8 * n_ * kt * sv + 2 * n_ * sv
             tot_bytes += its * per_it
         ach = tot_bytes / (total_ms / args.steps / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
-                "kernel": "k_persistent<float,float,float,32,float> (the whole batch: SpMM and vector passes of every "
-                          "graph's PCG iterations in one launch per step; duration = the step's event time)",
-                "launches": args.steps, "avg_launch_us": 1e3 * total_ms / args.steps,
-                "algorithmic_bytes_per_launch": tot_bytes,
-                "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy) of MEASURED_PEAKS.json"}
+        step_roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None,
+                     "kernel": "k_persistent<float,float,float,32,float> (the whole batch: SpMM and vector passes "
+                               "of every graph's PCG iterations in one launch per step; duration = the step's "
+                               "event time)",
+                     "launches": args.steps, "avg_launch_us": 1e3 * total_ms / args.steps,
+                     "algorithmic_bytes_per_launch": tot_bytes,
+                     "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy) of MEASURED_PEAKS.json"}
+        # the library's default form (host-driven launches over all graphs), same
+        # pairs, same process: its rate and its SpMM launches' roofline
+        kh = dict(kw, persistent=False)
+        for _ in range(args.warmup):
+            nvd.ge_distance_batched(Gs, xs, ys, **kh)
+        torch.cuda.synchronize()
+        nvd.profile_enable(True)
+        nvd.profile_read(0)
+        evh = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for a_, b_ in evh:
+            flush.zero_()
+            a_.record()
+            nvd.ge_distance_batched(Gs, xs, ys, **kh)
+            b_.record()
+        torch.cuda.synchronize()
+        nh, hms, hbytes = nvd.profile_read(0)
+        nvd.profile_enable(False)
+        tot_h = sum(a_.elapsed_time(b_) for a_, b_ in evh)
+        host_line = {"distances_per_s": k * args.steps / (tot_h / 1e3), "ms_per_step": tot_h / args.steps,
+                     "vs_persistent": total_ms / tot_h,
+                     "spmm_roofline": {"frac": ((hbytes / nh) / (hms / nh / 1e3) / 1e9) / peak if nh else None,
+                                       "avg_launch_us": 1e3 * hms / nh if nh else None, "launches": nh},
+                     "what": "nvd_ge_distance_batched default: one launch per phase over all graphs, the host "
+                             "polling convergence"}
     line = {
         "metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -438,13 +467,15 @@ def run_other_workload(args, nvd, synth, torch, np, local):
         "e2e": {"value": k * args.steps / te, "unit": unit, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches), "clocks": clk,
-        "roofline": roof if roof is not None else None if not n_spmv else {
+        "roofline": step_roof if step_roof is not None else None if not n_spmv else {
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "kernel": "k_spmm (every SpMV/SpMM launch of the step, algorithmic bytes)",
             "launches": n_spmv, "avg_launch_us": 1e3 * spmv_ms / n_spmv,
             "algorithmic_bytes_per_launch": spmv_bytes / n_spmv,
             "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy) of MEASURED_PEAKS.json"},
     }
+    if step_roof is not None:
+        line["batched_host_loop"] = host_line
     if not args.no_cpu_baseline:
         v, what = oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": unit, "cores": ocg.default_threads(), "kind": "oracle",

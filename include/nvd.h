@@ -412,9 +412,15 @@ int nvd_network_variance(nvd_graph_t g, int32_t s, const int32_t *nodes, const d
  * nvd_ge_distance_batched -- many graphs in one solve: the G graphs are treated as
  * the diagonal blocks of one block-diagonal Laplacian and every (graph, pair)
  * keeps its own CG scalars and convergence test, so the result equals G
- * independent nvd_ge_distance calls.  The PCG loop runs inside one persistent
- * cooperative kernel captured in a CUDA graph (replayed when the same arguments
- * come again).
+ * independent nvd_ge_distance calls.  The PCG iterations are driven from the
+ * host, one launch per phase over all graphs (the kernels of nvd_ge_distance at
+ * full occupancy; convergence polled one batch behind), or, with
+ * NVD_SOLVE_PERSISTENT, run inside one persistent cooperative kernel captured in
+ * a CUDA graph (replayed when the same arguments come again).  Measured on the
+ * 64-graph workload (1.7e6 nodes) the host-driven form takes 23 ms per FP32 step
+ * against 45 ms; the persistent kernel (two CTAs per SM at its register count,
+ * three grid barriers per iteration) is ahead by at most ~10% on batches of a few
+ * graphs or a few tens of thousands of nodes.
  *
  *   graphs  [G] handles (same device).
  *   k_per   [G] pairs per graph.

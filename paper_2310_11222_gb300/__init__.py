@@ -520,8 +520,9 @@ def network_variance(graph: Graph, nodes, p, *, mode: int = MODE_FP64, rtol: Opt
 
 def ge_distance_batched(graphs: Sequence[Graph], xs, ys, *, mode: int = MODE_FP32,
                         rtol: Optional[float] = None, max_iter: int = 10000, return_stats: bool = False,
-                        fold_direction: bool = False):
-    """d^2 for many graphs in one persistent launch; xs[g], ys[g] are CUDA [k_g, n_g]."""
+                        fold_direction: bool = False, persistent: bool = False):
+    """d^2 for many graphs in one solve; xs[g], ys[g] are CUDA [k_g, n_g].  One launch per
+    phase over all graphs, or with ``persistent`` one persistent launch per tile."""
     torch = _torch()
     lib = load_library()
     G = len(graphs)
@@ -537,6 +538,8 @@ def ge_distance_batched(graphs: Sequence[Graph], xs, ys, *, mode: int = MODE_FP3
         o.rtol = rtol
     if fold_direction:
         o.flags |= SOLVE_FOLD_DIRECTION
+    if persistent:
+        o.flags |= SOLVE_PERSISTENT
     d2 = torch.empty(total, dtype=torch.float64)
     stats = (SolveStats * max(total, 1))()
     dev = xs[0].device

@@ -1,13 +1,15 @@
-// C ABI: nvd_ge_distance_batched -- many graphs in one persistent launch.
+// C ABI: nvd_ge_distance_batched -- many graphs in one solve.
 //
 // The G graphs are concatenated once into an internal union graph: the diagonal
 // blocks of one block-diagonal Laplacian, graph g owning node range
 // [off_g, off_g + n_g) and its own segments (connected components).  Every
 // (graph, pair) keeps its own CG scalars and convergence test, so the result
-// equals G separate solves.  One tile of pairs is solved by one cooperative
-// persistent kernel (persistent.cuh), captured in a CUDA graph together with
-// its state resets and the copy of the results; repeated calls with the same
-// arguments replay the captured graph.
+// equals G separate solves.  One tile of pairs is solved by the host-driven
+// loop of nvd_ge_distance over the union graph (every graph's rows in each
+// launch, owners table for the inputs and results), or, with
+// NVD_SOLVE_PERSISTENT, by one cooperative persistent kernel (persistent.cuh),
+// captured in a CUDA graph together with its state resets and the copy of the
+// results; repeated calls with the same arguments replay the captured graph.
 #include <algorithm>
 #include <cstring>
 #include <list>
@@ -303,6 +305,22 @@ int batched_impl(const nvd_graph_t *gs, int32_t G, const int32_t *k_per, const v
             key.push_back((uint64_t)(uintptr_t)own[i].y);
             key.push_back((uint64_t)kc);
         }
+        if (!(o.flags & NVD_SOLVE_PERSISTENT)) {
+            // the same phases as separate launches over the union graph, on the
+            // caller's stream, every graph's rows in each launch
+            NVD_TRY_CUDA(cudaMemcpyAsync(d_own, own.data(), G * sizeof(Owner), cudaMemcpyHostToDevice, s));
+            NVD_TRY_CUDA(cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 8) * 4, s));
+            TileIO io{};
+            io.owners = true;
+            io.kc = KT;
+            const int rc = o.mode == NVD_MODE_FP64 ? run_tile_fp64(U, c, w, o, io, s, KT, xdt)
+                                                   : run_tile_fp32(U, c, w, o, io, s, KT, xdt);
+            if (rc != NVD_OK && rc != NVD_ERR_NOT_CONVERGED) return rc;
+            NVD_TRY(run_collect(c, KT, w.res, nullptr, 0, G, s));
+            NVD_TRY_CUDA(cudaMemcpyAsync(u->h_res, w.res, (size_t)G * KT * sizeof(ColResult), cudaMemcpyDeviceToHost,
+                                         s));
+            NVD_TRY_CUDA(cudaStreamSynchronize(s));
+        } else {
         auto &cap = u->graphs[key];
         // order the library stream after the caller's work
         NVD_TRY_CUDA(cudaEventRecord(u->ev_in, s));
@@ -349,6 +367,7 @@ int batched_impl(const nvd_graph_t *gs, int32_t G, const int32_t *k_per, const v
         NVD_TRY_CUDA(cudaEventRecord(u->ev_out, cs));
         NVD_TRY_CUDA(cudaStreamWaitEvent(s, u->ev_out, 0));
         NVD_TRY_CUDA(cudaStreamSynchronize(cs));
+        }
         int err = 0;
         NVD_TRY_CUDA(cudaMemcpy(&err, c.err, 4, cudaMemcpyDeviceToHost));
         if (err) {

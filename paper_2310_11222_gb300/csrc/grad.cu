@@ -101,15 +101,21 @@ __global__ void k_grad_scatter(const double *__restrict__ gint, const int64_t *_
     }
 }
 
-// grad_x = 2 gbar_j z, grad_y = -grad_x.
+// grad_x = 2 gbar_j z, grad_y = -grad_x.  Column j of [k][n] on blockIdx.y (and its
+// grid stride): the factor 2 gbar_j is one value per column, so an element costs one
+// multiply and no index division (the FP64 unit, 1/64 of the FP32 rate, had bounded
+// the per-element form).
 template <class TZ>
-__global__ void k_grad_xy(const TZ *__restrict__ z, int64_t n, int64_t total, const double *__restrict__ gbar,
+__global__ void k_grad_xy(const TZ *__restrict__ z, int64_t n, int k, const double *__restrict__ gbar,
                           TZ *gx, TZ *gy) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const double v = 2.0 * gbar[t / n] * (double)z[t];
-        if (gx) gx[t] = (TZ)v;
-        if (gy) gy[t] = (TZ)(-v);
+    for (int j = blockIdx.y; j < k; j += gridDim.y) {
+        const double cj = 2.0 * gbar[j];
+        const TZ *zj = z + (int64_t)j * n;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            const double v = cj * (double)zj[i];
+            if (gx) gx[(int64_t)j * n + i] = (TZ)v;
+            if (gy) gy[(int64_t)j * n + i] = (TZ)(-v);
+        }
     }
 }
 
@@ -178,13 +184,17 @@ int grad_impl(nvd_graph_t g, int32_t k, const void *z, int32_t zdt, const double
     if (prev != g->device) cudaSetDevice(g->device);
     int rc = NVD_OK;
     if (grad_x || grad_y) {
-        const int64_t total = (int64_t)k * g->n;
+        // about 32 CTAs per SM in all, spread over the columns
+        const int gy = std::min(k, 65535);
+        const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256,
+                                                                   ((int64_t)g->num_sms * 32 + gy - 1) / gy));
+        const dim3 grid((unsigned)gx, (unsigned)gy);
         if (zdt == NVD_F64)
-            k_grad_xy<double><<<grid_cap(total, g->num_sms), 256, 0, s>>>((const double *)z, g->n, total, gbar,
-                                                                         (double *)grad_x, (double *)grad_y);
+            k_grad_xy<double><<<grid, 256, 0, s>>>((const double *)z, g->n, k, gbar, (double *)grad_x,
+                                                   (double *)grad_y);
         else
-            k_grad_xy<float><<<grid_cap(total, g->num_sms), 256, 0, s>>>((const float *)z, g->n, total, gbar,
-                                                                        (float *)grad_x, (float *)grad_y);
+            k_grad_xy<float><<<grid, 256, 0, s>>>((const float *)z, g->n, k, gbar, (float *)grad_x,
+                                                  (float *)grad_y);
         if (cudaGetLastError() != cudaSuccess) rc = NVD_ERR_CUDA;
     }
     if (rc == NVD_OK && grad_w && g->nnz_user > 0) {

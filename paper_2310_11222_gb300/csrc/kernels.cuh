@@ -21,6 +21,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "common.h"
 
 namespace nvd {
@@ -811,8 +813,10 @@ __device__ __forceinline__ void spmm_chunk(const Ctx &c, const Epi &epi, int seg
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = 0;
         // entries e, e + S, e + 2S, ... of this lane group (S = NWARP * G), U of them
-        // gathered together before their products are added in entry order
-        constexpr int U = sizeof(TV) == 8 ? SPMM_UNROLL_F64 : SPMM_UNROLL_F32;
+        // gathered together before their products are added in entry order (one in the
+        // persistent kernel, LdCoh, whose registers are already at its cap: the unrolled
+        // form made its batched solve 43% slower; the sums are the same either way)
+        constexpr int U = std::is_same<LD, LdCoh>::value ? 1 : sizeof(TV) == 8 ? SPMM_UNROLL_F64 : SPMM_UNROLL_F32;
         constexpr int64_t S = (int64_t)NWARP * G;
         for (int64_t e = it.e0 + warp * G + gi; e < it.e1; e += U * S) {
             int ca[U];

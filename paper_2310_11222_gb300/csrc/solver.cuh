@@ -434,15 +434,18 @@ struct TileIO {
     void *z;              // device or NULL
     int32_t idx = 0;      // 1: x, y are node ids (indicator pairs)
     const void *z0 = nullptr;  // device [kc][n] of the x type: warm start (FP64 mode), else NULL
+    bool owners = false;  // FP64/FP32: the Ctx already holds an owners table (batched graphs)
 };
 
 // FP64 / FP32 PCG on one tile.  Results stay in the Ctx state (d2, rr, ...).
 template <class TV, class TW, class TA, int KT, class TX>
 int tile_pcg(nvd_graph_s *g, Ctx c, SolveWs &w, const nvd_solve_opts &o, const TileIO &io,
              cudaStream_t s) {
-    c.own0 = Owner{io.x, io.y, io.z, 0, g->n, io.kc, 0, g->nseg, io.idx};
-    c.owners = nullptr;
-    c.n_owner = 1;
+    if (!io.owners) {
+        c.own0 = Owner{io.x, io.y, io.z, 0, g->n, io.kc, 0, g->nseg, io.idx};
+        c.owners = nullptr;
+        c.n_owner = 1;
+    }
     c.rtol2 = o.rtol * o.rtol;
     c.d2stop = (o.flags & NVD_SOLVE_D2_STOP) ? o.d2_rtol : 0.0;
     c.max_iter = o.max_iter;

@@ -1,5 +1,6 @@
-"""Batched persistent solve (many graphs, one cooperative launch in a CUDA graph) and
-the persistent single-graph solve, against the oracle and the host-driven path."""
+"""Batched solve (many graphs as one block-diagonal Laplacian: host-driven launches over
+all graphs by default, or one persistent cooperative launch in a CUDA graph) and the
+persistent single-graph solve, against the oracle and the host-driven path."""
 import numpy as np
 import pytest
 
@@ -42,22 +43,38 @@ def small_batch():
     return graphs, pairs, want
 
 
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("mode,rtol,tol", [(0, 1e-10, 1e-8), (1, 1e-6, 1e-4)])
-def test_batched_matches_oracle(nvd, small_batch, mode, rtol, tol):
+def test_batched_matches_oracle(nvd, small_batch, mode, rtol, tol, persistent):
     graphs, pairs, want = small_batch
     G = [nvd.Graph.from_csr(g) for g in graphs]
     xs = [on(X) for X, _ in pairs]
     ys = [on(Y) for _, Y in pairs]
-    d2, st = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, return_stats=True)
+    d2, st = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, return_stats=True, persistent=persistent)
     d2 = d2.numpy()
     off = 0
     for w in want:
         assert rel(d2[off:off + len(w)], w) < tol
         off += len(w)
     assert all(s["status"] == 0 for s in st)
-    # replaying the captured launch gives the identical answer
-    d2b = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol).numpy()
+    # a second call (the persistent form replays its captured launch) gives the identical answer
+    d2b = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, persistent=persistent).numpy()
     assert np.array_equal(d2, d2b)
+
+
+@pytest.mark.parametrize("mode,tol_p", [(0, 1e-12), (1, 1e-6)])
+def test_batched_host_loop_agrees_with_persistent(nvd, small_batch, mode, tol_p):
+    """The host-driven launches and the persistent kernel run the same phases over the
+    union graph; their results agree to rounding, with the same iteration counts."""
+    graphs, pairs, _ = small_batch
+    G = [nvd.Graph.from_csr(g) for g in graphs]
+    xs = [on(X) for X, _ in pairs]
+    ys = [on(Y) for _, Y in pairs]
+    rtol = 1e-10 if mode == 0 else 1e-6
+    h, sh = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, return_stats=True)
+    p, sp_ = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, return_stats=True, persistent=True)
+    assert rel(h.numpy(), p.numpy()) < tol_p
+    assert [s["iters"] for s in sh] == [s["iters"] for s in sp_]
 
 
 def test_batched_equals_independent_solves(nvd, small_batch):
@@ -119,9 +136,11 @@ def test_batched_folded_direction_matches_three_kernel_iteration(nvd, small_batc
     xs = [on(X) for X, _ in pairs]
     ys = [on(Y) for _, Y in pairs]
     rtol = 1e-10 if mode == 0 else 1e-6
-    a = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol).numpy()
-    b = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, fold_direction=True).numpy()
-    assert rel(a, b) < tol
+    for persistent in (False, True):
+        a = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, persistent=persistent).numpy()
+        b = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, fold_direction=True,
+                                    persistent=persistent).numpy()
+        assert rel(a, b) < tol
 
 
 @pytest.fixture(scope="module")
@@ -139,16 +158,17 @@ def full_batch():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("mode,rtol,tol", [(1, 1e-6, 1e-4), (0, 1e-11, 1e-8)])
-def test_batched_full_size_all_graphs(nvd, full_batch, mode, rtol, tol):
-    """All 2,048 pairs of the full batch in one persistent launch per tile against the
-    oracle: FP32 vectors with FP64 reductions at the unrefined-FP32 tolerance 1e-4,
-    and FP64 at 1e-8."""
+def test_batched_full_size_all_graphs(nvd, full_batch, mode, rtol, tol, persistent):
+    """All 2,048 pairs of the full batch (the host-driven launches, or one persistent
+    launch per tile) against the oracle: FP32 vectors with FP64 reductions at the
+    unrefined-FP32 tolerance 1e-4, and FP64 at 1e-8."""
     wl, X, Y, want = full_batch
     G = [nvd.Graph.from_csr(g) for g in wl.graphs]
     xs = [on(x) for x in X]
     ys = [on(y) for y in Y]
-    d2, st = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, return_stats=True)
+    d2, st = nvd.ge_distance_batched(G, xs, ys, mode=mode, rtol=rtol, return_stats=True, persistent=persistent)
     d2 = d2.numpy()
     assert np.all(np.isfinite(d2)) and np.all(d2 > 0)
     assert all(s["status"] == 0 for s in st)
@@ -178,7 +198,9 @@ def test_batched_more_owner_columns_than_the_grid_has_threads(nvd, mode, rtol, t
         want.append(dense.ge_d2_eig(g.n, g.rowptr, g.colidx, g.w, X, Y))
     want = np.concatenate(want)
     G = [nvd.Graph.from_csr(g) for g in graphs]
-    d2 = nvd.ge_distance_batched(G, [on(x) for x in xs], [on(y) for y in ys], mode=mode, rtol=rtol).numpy()
-    pos = want > 1e-12
-    assert rel(d2[pos], want[pos]) < tol
-    assert np.all(np.abs(d2[~pos]) < 1e-9)
+    for persistent in (True, False):
+        d2 = nvd.ge_distance_batched(G, [on(x) for x in xs], [on(y) for y in ys], mode=mode, rtol=rtol,
+                                     persistent=persistent).numpy()
+        pos = want > 1e-12
+        assert rel(d2[pos], want[pos]) < tol
+        assert np.all(np.abs(d2[~pos]) < 1e-9)
