@@ -551,11 +551,12 @@ int tile_mixed(nvd_graph_s *g, Ctx c, const Plan *pl64, SolveWs &w, const nvd_so
         // The first inner solve goes to opts.rtol.  A later one solves for the
         // correction L c = r of the current z; its d^2 change r^T c is what decides
         // convergence and the variational d^2 error after it is quadratic in its
-        // residual, so a relative residual of 1e-1 (or opts.rtol if looser) suffices: it
-        // measures the remaining d^2 error to about 1% and leaves about 1% of it.  z
-        // itself is only linearly accurate in that residual, so when z is returned the
-        // corrections go to 1e-2.
-        const double rtol_step = step == 0 ? o.rtol : std::max(o.rtol, io.z ? 1e-2 : 1e-1);
+        // residual, so a relative residual of 0.3 (or opts.rtol if looser) suffices: it
+        // measures the remaining d^2 error to about 10% and leaves about 10% of it (on
+        // the power-law workload 1e-1 took 9% longer for d^2 errors of 2e-11 instead
+        // of 1.5e-10, both far inside a 1e-8 target).  z itself is only linearly
+        // accurate in that residual, so when z is returned the corrections go to 1e-2.
+        const double rtol_step = step == 0 ? o.rtol : std::max(o.rtol, io.z ? 1e-2 : 3e-1);
         ci.rtol2 = rtol_step * rtol_step;
         NVD_TRY_CUDA(cudaMemsetAsync(c.n_active, 0, 4, s));
         dev::OpInit<float, KT> oi;
