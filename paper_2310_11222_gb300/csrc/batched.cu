@@ -284,26 +284,12 @@ int batched_impl(const nvd_graph_t *gs, int32_t G, const int32_t *k_per, const v
     for (int i = 0; i < G; ++i) out_off[i + 1] = out_off[i] + k_per[i];
     for (int c0 = 0; c0 < kmax; c0 += KT) {
         std::vector<Owner> own(G);
-        std::vector<uint64_t> key = {(uint64_t)KT, (uint64_t)o.mode, (uint64_t)xdt, (uint64_t)c0,
-                                     (uint64_t)o.max_iter, (uint64_t)pl->n_sblk, (uint64_t)a.fold};
-        uint64_t rbits;
-        memcpy(&rbits, &o.rtol, 8);
-        key.push_back(rbits);
-        // the captured launch holds workspace addresses: a regrown workspace is a new key
-        for (const void *ptr : {(const void *)w.part, (const void *)w.gpart, (const void *)w.gcount, (const void *)w.x, (const void *)w.r, (const void *)w.p,
-                                (const void *)w.q, (const void *)a.u, (const void *)w.delta, (const void *)w.res,
-                                (const void *)c.active,
-                                (const void *)w.hsum, (const void *)c.rho, (const void *)bar, (const void *)d_own})
-            key.push_back((uint64_t)(uintptr_t)ptr);
         for (int i = 0; i < G; ++i) {
             const int kc = std::max(0, std::min(KT, k_per[i] - c0));
             const int64_t ng = gs[i]->n;
             own[i] = Owner{kc ? (const char *)x[i] + (size_t)c0 * ng * xsz : nullptr,
                            kc ? (const char *)y[i] + (size_t)c0 * ng * xsz : nullptr, nullptr, u->node_off[i], ng,
                            kc, u->seg_off[i], u->seg_off[i + 1], 0};
-            key.push_back((uint64_t)(uintptr_t)own[i].x);
-            key.push_back((uint64_t)(uintptr_t)own[i].y);
-            key.push_back((uint64_t)kc);
         }
         if (!(o.flags & NVD_SOLVE_PERSISTENT)) {
             // the same phases as separate launches over the union graph, on the
@@ -321,57 +307,76 @@ int batched_impl(const nvd_graph_t *gs, int32_t G, const int32_t *k_per, const v
                                          s));
             NVD_TRY_CUDA(cudaStreamSynchronize(s));
         } else {
-        auto &cap = u->graphs[key];
-        // order the library stream after the caller's work
-        NVD_TRY_CUDA(cudaEventRecord(u->ev_in, s));
-        NVD_TRY_CUDA(cudaStreamWaitEvent(u->cs, u->ev_in, 0));
-        cudaStream_t cs = u->cs;
-        NVD_TRY_CUDA(cudaMemcpyAsync(d_own, own.data(), G * sizeof(Owner), cudaMemcpyHostToDevice, cs));
-        if (!cap) {
-            NVD_TRY_CUDA(cudaStreamSynchronize(cs));
-            std::unique_ptr<Captured> cp(new Captured());
-            cudaGraph_t graph = nullptr;
-            NVD_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            int rc = NVD_OK;
-            if (cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 8) * 4, cs) != cudaSuccess ||
-                cudaMemsetAsync(bar, 0, 16, cs) != cudaSuccess)
-                rc = NVD_ERR_CUDA;
-            if (rc == NVD_OK) rc = run_persistent(U, c, a, o.mode, KT, xdt, cs);
-            if (rc == NVD_OK &&
-                cudaMemcpyAsync(u->h_res, w.res, (size_t)G * KT * sizeof(ColResult), cudaMemcpyDeviceToHost, cs) !=
-                    cudaSuccess)
-                rc = NVD_ERR_CUDA;
-            const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
-            if (rc != NVD_OK || ec != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
-                cudaGetLastError();
-                u->graphs.erase(key);
-                if (rc == NVD_OK) {
-                    set_error("nvd_ge_distance_batched: graph capture failed: %s", cudaGetErrorString(ec));
+            // one persistent launch, captured with its resets and result copy; the
+            // key holds everything the captured launch depends on
+            std::vector<uint64_t> key = {(uint64_t)KT, (uint64_t)o.mode, (uint64_t)xdt, (uint64_t)c0,
+                                         (uint64_t)o.max_iter, (uint64_t)pl->n_sblk, (uint64_t)a.fold};
+            uint64_t rbits;
+            memcpy(&rbits, &o.rtol, 8);
+            key.push_back(rbits);
+            // workspace addresses: a regrown workspace is a new key
+            for (const void *ptr : {(const void *)w.part, (const void *)w.gpart, (const void *)w.gcount,
+                                    (const void *)w.x, (const void *)w.r, (const void *)w.p, (const void *)w.q,
+                                    (const void *)a.u, (const void *)w.delta, (const void *)w.res,
+                                    (const void *)c.active, (const void *)w.hsum, (const void *)c.rho,
+                                    (const void *)bar, (const void *)d_own})
+                key.push_back((uint64_t)(uintptr_t)ptr);
+            for (int i = 0; i < G; ++i) {
+                key.push_back((uint64_t)(uintptr_t)own[i].x);
+                key.push_back((uint64_t)(uintptr_t)own[i].y);
+                key.push_back((uint64_t)own[i].kc);
+            }
+            auto &cap = u->graphs[key];
+            // order the library stream after the caller's work
+            NVD_TRY_CUDA(cudaEventRecord(u->ev_in, s));
+            NVD_TRY_CUDA(cudaStreamWaitEvent(u->cs, u->ev_in, 0));
+            cudaStream_t cs = u->cs;
+            NVD_TRY_CUDA(cudaMemcpyAsync(d_own, own.data(), G * sizeof(Owner), cudaMemcpyHostToDevice, cs));
+            if (!cap) {
+                NVD_TRY_CUDA(cudaStreamSynchronize(cs));
+                std::unique_ptr<Captured> cp(new Captured());
+                cudaGraph_t graph = nullptr;
+                NVD_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+                int rc = NVD_OK;
+                if (cudaMemsetAsync(c.active, 0, (size_t)(3 * sk + 8) * 4, cs) != cudaSuccess ||
+                    cudaMemsetAsync(bar, 0, 16, cs) != cudaSuccess)
                     rc = NVD_ERR_CUDA;
+                if (rc == NVD_OK) rc = run_persistent(U, c, a, o.mode, KT, xdt, cs);
+                if (rc == NVD_OK &&
+                    cudaMemcpyAsync(u->h_res, w.res, (size_t)G * KT * sizeof(ColResult), cudaMemcpyDeviceToHost, cs) !=
+                        cudaSuccess)
+                    rc = NVD_ERR_CUDA;
+                const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+                if (rc != NVD_OK || ec != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    cudaGetLastError();
+                    u->graphs.erase(key);
+                    if (rc == NVD_OK) {
+                        set_error("nvd_ge_distance_batched: graph capture failed: %s", cudaGetErrorString(ec));
+                        rc = NVD_ERR_CUDA;
+                    }
+                    return rc;
                 }
-                return rc;
+                const cudaError_t ei = cudaGraphInstantiate(&cp->exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ei != cudaSuccess) {
+                    cudaGetLastError();
+                    u->graphs.erase(key);
+                    set_error("nvd_ge_distance_batched: graph instantiate failed: %s", cudaGetErrorString(ei));
+                    return NVD_ERR_CUDA;
+                }
+                cap = std::move(cp);
             }
-            const cudaError_t ei = cudaGraphInstantiate(&cp->exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ei != cudaSuccess) {
-                cudaGetLastError();
-                u->graphs.erase(key);
-                set_error("nvd_ge_distance_batched: graph instantiate failed: %s", cudaGetErrorString(ei));
-                return NVD_ERR_CUDA;
-            }
-            cap = std::move(cp);
-        }
-        NVD_TRY_CUDA(cudaGraphLaunch(cap->exec, cs));
-        note_launch();
-        NVD_TRY_CUDA(cudaEventRecord(u->ev_out, cs));
-        NVD_TRY_CUDA(cudaStreamWaitEvent(s, u->ev_out, 0));
-        NVD_TRY_CUDA(cudaStreamSynchronize(cs));
+            NVD_TRY_CUDA(cudaGraphLaunch(cap->exec, cs));
+            note_launch();
+            NVD_TRY_CUDA(cudaEventRecord(u->ev_out, cs));
+            NVD_TRY_CUDA(cudaStreamWaitEvent(s, u->ev_out, 0));
+            NVD_TRY_CUDA(cudaStreamSynchronize(cs));
         }
         int err = 0;
         NVD_TRY_CUDA(cudaMemcpy(&err, c.err, 4, cudaMemcpyDeviceToHost));
         if (err) {
-            set_error("nvd_ge_distance_batched: device barrier gave up (status %d)", err);
+            set_error("nvd_ge_distance_batched: a bounded device wait gave up (status %d)", err);
             return err;
         }
         for (int i = 0; i < G; ++i) {
