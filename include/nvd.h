@@ -463,6 +463,21 @@ int nvd_laplacian_apply(nvd_graph_t g, int32_t k, const void *x, void *y, int32_
                         nvd_stream_t stream);
 
 /*
+ * nvd_dot_f32 -- sum_i a_i b_i of two FP32 device vectors of length n into *out
+ * (one device double), with the reduction the FP32-mode PCG uses for its inner
+ * products (Section 3.2 solver, FP32 vectors): each thread accumulates the exact
+ * products a_i b_i (a float product fits a double-float pair) in a double-float
+ * pair, the per-thread values are added in FP64 within each block and the block
+ * totals in block order, so the result does not depend on timing.  Its error is
+ * about 1e-13 * sum_i |a_i b_i| (FP64 sums of at most 1,280 partials), where an
+ * FP32 accumulation would give about 1e-7 times that.  Stream-ordered on `stream`
+ * (8 KB of scratch from the stream-ordered allocator).
+ * Errors: NVD_ERR_INVALID_ARG (n < 0, NULL out, NULL a or b with n > 0),
+ * NVD_ERR_CUDA.
+ */
+int nvd_dot_f32(const float *a, const float *b, int64_t n, double *out, nvd_stream_t stream);
+
+/*
  * nvd_laplacian_quadform_noalloc -- y_j = L x_j and q_j = x_j^T L x_j for j < k,
  * without allocating any memory.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory when they call, e.g. a

@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "Graph", "SolveOpts", "SolveStats", "ge_distance", "effective_resistance", "resistance_matrix",
     "network_variance", "ge_distance_batched", "ge_grad",
-    "laplacian_apply", "GEDistance", "ge_distance_autograd", "profile_enable", "profile_read",
+    "laplacian_apply", "dot_f32", "GEDistance", "ge_distance_autograd", "profile_enable", "profile_read",
     "library_path", "load_library", "NvdError", "MODE_FP64", "MODE_FP32", "MODE_MIXED",
 ]
 
@@ -132,6 +132,8 @@ _SIGS = {
                                             ctypes.POINTER(SolveOpts), ctypes.c_void_p, ctypes.c_void_p]),
     "nvd_laplacian_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.c_void_p]),
+    "nvd_dot_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
     "nvd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "nvd_last_error": (ctypes.c_char_p, []),
     "nvd_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
@@ -568,6 +570,22 @@ def ge_grad(graph: Graph, z, gbar, *, want_w: bool = True, want_x: bool = True):
                              None if gy is None else gy.data_ptr(), _stream_ptr(Z.device))
     _check(rc, "nvd_ge_grad")
     return gw, gx, gy
+
+
+def dot_f32(a, b) -> float:
+    """sum a_i b_i of two FP32 CUDA vectors with the FP32-mode solver's inner-product
+    reduction (``nvd_dot_f32``: exact products in double-float, FP64 sums)."""
+    torch = _torch()
+    lib = load_library()
+    A = a.contiguous().reshape(-1)
+    B = b.contiguous().reshape(-1)
+    if A.dtype != torch.float32 or B.dtype != torch.float32 or A.numel() != B.numel():
+        raise ValueError("dot_f32: two FP32 tensors of the same length")
+    out = torch.empty(1, dtype=torch.float64, device=A.device)
+    with torch.cuda.device(A.device):
+        rc = lib.nvd_dot_f32(A.data_ptr(), B.data_ptr(), A.numel(), out.data_ptr(), _stream_ptr(A.device))
+    _check(rc, "nvd_dot_f32")
+    return float(out.item())
 
 
 def laplacian_apply(graph: Graph, x):

@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["nvd_graph_create", "nvd_graph_destroy", "nvd_graph_info", "nvd_ge_distance",
                  "nvd_ge_distance_batched", "nvd_ge_grad", "nvd_status_string", "nvd_laplacian_apply",
-                 "nvd_effective_resistance", "nvd_graph_set_weights"]:
+                 "nvd_effective_resistance", "nvd_graph_set_weights", "nvd_dot_f32"]:
         assert must in names
 
 
@@ -69,6 +69,7 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert lib.nvd_network_variance(None, 1, None, None, None, None, None) == 1
     assert lib.nvd_ge_distance_warm(None, 1, None, None, 1, None, None, None, None, None, None) == 1
     assert lib.nvd_graph_set_tuning(None, 0, None) == 1
+    assert lib.nvd_dot_f32(None, None, -1, None, None) == 1
     assert lib.nvd_graph_destroy(None) == 0
     assert lib.nvd_profile_read(3, None, None, None) == 1
 

@@ -1,4 +1,4 @@
-"""Cross-block sums in grouped form.  A pass with many partial-sum slots (blocks and
+"""Cross-block sums in grouped form, and the FP32-mode inner product.  A pass with many partial-sum slots (blocks and
 split heavy rows) adds them in two levels: groups of consecutive slots, then the
 group sums (each in a fixed order).  A power-law graph of 4e5 nodes with hubs of
 degree up to 1e4, cut into small blocks, makes every multi-column pass take that
@@ -64,3 +64,28 @@ def test_grouped_sums_repeat_and_match_the_oracle(nvd, case, mode, kt):
     run(yt.flip(0), xt)                                      # another solve in between
     c, ic = run(xt, yt)
     assert torch.equal(a, c) and ia == ic
+
+
+@pytest.mark.parametrize("n", [1, 1000, 1 << 20, 3_000_017])
+def test_fp32_mode_inner_product_on_cancelling_vectors(nvd, n):
+    """nvd_dot_f32 runs the reduction of the FP32-mode PCG (exact float products in
+    double-float, FP64 block and cross-block sums).  Vectors whose terms cancel
+    (pairs +-1e4 (1 + noise)) around a small remainder: its error stays below
+    1e-12 * sum |a_i b_i| of the exact sum (math.fsum of the FP64 products, which
+    are exact), where an FP32 accumulation misses by orders of magnitude more."""
+    import math
+    rng = np.random.default_rng(n)
+    big = (1e4 * (1.0 + rng.random(n))).astype(np.float32)
+    sign = np.where(np.arange(n) % 2 == 0, 1.0, -1.0).astype(np.float32)
+    a = (sign * big + rng.normal(0.0, 1e-3, n)).astype(np.float32)
+    b = (1.0 + 1e-3 * rng.random(n)).astype(np.float32)
+    prod = a.astype(np.float64) * b.astype(np.float64)
+    exact = math.fsum(prod.tolist())
+    scale = float(np.sum(np.abs(prod)))
+    got = nvd.dot_f32(torch.as_tensor(a, device=DEV), torch.as_tensor(b, device=DEV))
+    assert abs(got - exact) <= 1e-12 * scale
+    again = nvd.dot_f32(torch.as_tensor(a, device=DEV), torch.as_tensor(b, device=DEV))
+    assert got == again                                        # fixed order: repeatable
+    if n >= 1 << 20:
+        naive = float(torch.sum(torch.as_tensor(a * b, device=DEV)).item())   # FP32 products and sums
+        assert abs(naive - exact) > 1e3 * abs(got - exact)
