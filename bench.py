@@ -711,6 +711,10 @@ def run_powerlaw(args, nvd, synth, torch, np, rank, world, local, dist):
                      "kernel": kname, "launches": n_spmm,
                      "avg_launch_us": 1e3 * spmm_ms / n_spmm if n_spmm else None,
                      "algorithmic_bytes_per_launch": spmm_bytes / n_spmm if n_spmm else None,
+                     # the DRAM bytes the ncu summary counted per launch over the live launch
+                     # time: the bandwidth the kernel sustains on its real (gather-heavy) traffic
+                     "traffic_gbs": traffic / (spmm_ms / n_spmm / 1e3) / 1e9 if traffic and n_spmm else None,
+                     "traffic_frac": traffic / (spmm_ms / n_spmm / 1e3) / 1e9 / peak if traffic and n_spmm else None,
                      "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy) of MEASURED_PEAKS.json"},
         "solver": {"inner_iters_per_pair": [s_["iters"] for s_ in stats],
                    "refine_steps": sorted({s_["refine_steps"] for s_ in stats}),
