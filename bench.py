@@ -693,8 +693,9 @@ def run_powerlaw(args, nvd, synth, torch, np, rank, world, local, dist):
     folded = bool(tuning and tuning.get("fold_direction"))
     kt = (tuning or {}).get("kt") or 32
     kbase = {0: "k_spmm", 1: "k_spmm_stream", 2: "k_spmm_tma"}[gather]
+    # the committed DRAM count is of one full-size launch of this decomposition
     traffic = (ncu_traffic(f"spmm_powerlaw_kt{kt}_g{gather}_traffic.txt", SPMM_STREAM_SOURCES)
-               if not folded else None)
+               if not folded and args.scale == 1.0 and not args.eliminate else None)
     kname = (f"{kbase}<float,float,float,{kt},{'EpiLapDir' if folded else 'EpiLap'}> (FP32 multi-column "
              f"Laplacian SpMM, {['register loads per slice', 'register loads over each warp stream', 'TMA gathers over each warp stream'][gather]}, fused p^T q)")
     line = {
