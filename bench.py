@@ -44,7 +44,7 @@ if ROOT not in sys.path:
 METRIC = "GE distances/s on 1 GB300 at d² rel.err≤1e-6; SpMV HBM GB/s vs peak"
 UNIT = "distances/s"
 PL_PAIRS = 128         # power-law workload: pairs per step (per rank)
-PL_RTOL_IN = 3e-5      # its inner FP32 solve tolerance
+PL_RTOL_IN = 5e-5      # its inner FP32 solve tolerance
 PL_D2_RTOL = 1e-8      # its refinement stop (relative change of d^2)
 PL_ORACLE_PAIRS = 2    # pairs the oracle solves for the CPU baseline and the error check
 PAIRS_PER_STEP = 8
